@@ -1,0 +1,176 @@
+"""FP64 CPU oracle for the cell-list pair map (CellListMap.jl, arXiv 2202.06427).
+
+TEST INFRASTRUCTURE. Only the tests, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` import this package. It shares no code with the
+CUDA library and the library never calls it.
+
+Every function takes positions ``x`` as an (n, dim) float64 array and the
+lattice matrix ``h`` as a (dim, dim) array whose ROWS are the lattice vectors.
+Indices are 0-based. ``band`` is the relative half-width of the band around
+the cutoff and the histogram bin edges inside which a pair may be classified
+either way by a correct FP32 implementation (Sec. 2.3 leaves "within the
+cutoff" at the edge unspecified; the library reads it as strict r < rc).
+
+Functions and the passages they follow:
+  pair_map      -- Sec. 2.3 (Code 2), 2.6, 2.8: every pair-image within rc, with
+                   count, sum 1/r (Code 5), shifted-force energy, forces (Code 7
+                   pattern), virial, dE/dH, histogram (Code 10 pattern).
+  pairlist      -- Sec. 4.1 neighbour list, i<j, sorted by (i, j).
+  particles     -- force and half pair energy of chosen particles, one by one.
+  brute_map / brute_pairlist -- O(n^2 * images) definitions used to pin the above.
+  geom_info     -- widths between lattice faces and the cell grid for lcell.
+  closed_form   -- see oracle.closed_form (perfect-lattice sums).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+ERRORS = {0: "ok", -1: "invalid argument", -2: "singular box", -3: "pair with two images in cutoff",
+          -4: "capacity", -5: "out of memory"}
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        ll, i32, dbl = ctypes.c_longlong, ctypes.c_int, ctypes.c_double
+        lib.or_geom_info.argtypes = [i32, P, dbl, i32, P, P, P]
+        lib.or_map.argtypes = [i32, ll, P, P, dbl, dbl, ll, ll, i32, dbl, P, P, P, P, P, P, P]
+        lib.or_brute_map.argtypes = [i32, ll, P, P, dbl, dbl, i32, dbl, P, P, P, P, P, P, P]
+        lib.or_pairlist.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
+        lib.or_brute_pairlist.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
+        lib.or_particles.argtypes = [i32, ll, P, P, dbl, P, ll, P, P]
+        for f in (lib.or_geom_info, lib.or_map, lib.or_brute_map, lib.or_pairlist,
+                  lib.or_brute_pairlist, lib.or_particles):
+            f.restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc):
+    if rc != 0:
+        raise OracleError(ERRORS.get(rc, str(rc)))
+
+
+def _prep(x, h):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    dim = h.shape[0]
+    if h.shape != (dim, dim) or dim not in (2, 3) or x.ndim != 2 or x.shape[1] != dim:
+        raise OracleError("shapes: x (n, dim), h (dim, dim), dim in (2, 3)")
+    return x, h, dim
+
+
+def geom_info(h, rc, lcell=1):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    dim = h.shape[0]
+    w = np.zeros(3)
+    n = np.zeros(3, dtype=np.int32)
+    m = np.zeros(3, dtype=np.int32)
+    _check(_lib().or_geom_info(dim, _p(h), rc, lcell, _p(w), _p(n), _p(m)))
+    return {"w": w[:dim].copy(), "n": n[:dim].copy(), "m": m[:dim].copy()}
+
+
+def _result(dim, n, nbins, counts, sums, forces, virial, dedh, hc, hm):
+    out = {"count": int(counts[0]), "band_in": int(counts[1]), "band_out": int(counts[2]),
+           "suminvr": float(sums[0]), "energy": float(sums[1]),
+           "virial": virial.reshape(dim, dim), "dedh": dedh.reshape(dim, dim)}
+    if forces is not None:
+        out["forces"] = forces.reshape(n, dim)
+    if nbins > 0:
+        out["hist_core"] = hc
+        out["hist_maybe"] = hm
+    return out
+
+
+def pair_map(x, h, rc, band=1e-6, nbins=0, rmax=None, forces=True, i_range=None):
+    """All reductions over the pair-images within rc (restricted to pairs whose
+    smaller index lies in ``i_range`` when given)."""
+    x, h, dim = _prep(x, h)
+    n = x.shape[0]
+    lo, hi = (0, n) if i_range is None else i_range
+    counts = np.zeros(3, dtype=np.int64)
+    sums = np.zeros(2)
+    f = np.zeros((n, dim)) if forces else None
+    vir = np.zeros(dim * dim)
+    dedh = np.zeros(dim * dim)
+    hc = np.zeros(max(nbins, 1), dtype=np.int64)
+    hm = np.zeros(max(nbins, 1), dtype=np.int64)
+    _check(_lib().or_map(dim, n, _p(x), _p(h), rc, band, lo, hi, nbins, rmax or rc,
+                         _p(counts), _p(sums), _p(f), _p(vir), _p(dedh),
+                         _p(hc) if nbins else None, _p(hm) if nbins else None))
+    return _result(dim, n, nbins, counts, sums, f, vir, dedh, hc[:nbins], hm[:nbins])
+
+
+def brute_map(x, h, rc, band=1e-6, nbins=0, rmax=None):
+    x, h, dim = _prep(x, h)
+    n = x.shape[0]
+    counts = np.zeros(3, dtype=np.int64)
+    sums = np.zeros(2)
+    f = np.zeros((n, dim))
+    vir = np.zeros(dim * dim)
+    dedh = np.zeros(dim * dim)
+    hc = np.zeros(max(nbins, 1), dtype=np.int64)
+    hm = np.zeros(max(nbins, 1), dtype=np.int64)
+    _check(_lib().or_brute_map(dim, n, _p(x), _p(h), rc, band, nbins, rmax or rc,
+                               _p(counts), _p(sums), _p(f), _p(vir), _p(dedh),
+                               _p(hc) if nbins else None, _p(hm) if nbins else None))
+    return _result(dim, n, nbins, counts, sums, f, vir, dedh, hc[:nbins], hm[:nbins])
+
+
+def _pairlist(fn, x, h, rc, band, cap):
+    x, h, dim = _prep(x, h)
+    n = x.shape[0]
+    while True:
+        pi = np.zeros(cap, dtype=np.int64)
+        pj = np.zeros(cap, dtype=np.int64)
+        pd = np.zeros(cap)
+        pb = np.zeros(cap, dtype=np.int8)
+        npairs = np.zeros(1, dtype=np.int64)
+        rc_ = fn(dim, n, _p(x), _p(h), rc, band, cap, _p(pi), _p(pj), _p(pd), _p(pb), _p(npairs))
+        if rc_ == -4:
+            cap *= 4
+            continue
+        _check(rc_)
+        k = int(npairs[0])
+        return {"i": pi[:k], "j": pj[:k], "d": pd[:k], "band": pb[:k].astype(bool)}
+
+
+def pairlist(x, h, rc, band=1e-6, cap=1 << 20):
+    """Sorted i<j list of pairs with r < rc(1 + 4 band); ``band`` flags the
+    pairs with |r - rc| <= band*rc."""
+    return _pairlist(_lib().or_pairlist, x, h, rc, band, cap)
+
+
+def brute_pairlist(x, h, rc, band=1e-6, cap=1 << 16):
+    return _pairlist(_lib().or_brute_pairlist, x, h, rc, band, cap)
+
+
+def particles(x, h, rc, idx):
+    """Force (-dE/dx) and half pair energy of each particle in ``idx``."""
+    x, h, dim = _prep(x, h)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    f = np.zeros((idx.shape[0], dim))
+    e = np.zeros(idx.shape[0])
+    _check(_lib().or_particles(dim, x.shape[0], _p(x), _p(h), rc, _p(idx), idx.shape[0], _p(f), _p(e)))
+    return f, e
+
+
+def energy(x, h, rc):
+    """Shifted-force energy alone (no forces)."""
+    return pair_map(x, h, rc, forces=False)["energy"]
