@@ -71,5 +71,7 @@ def lattice_sums(b, rc, nsites, nbins=0, rmax=None, band=1e-6):
         np.add.at(hist, k[ok], 1)
         out["hist"] = (hist * nsites) // 2
         edges += [rmax * e / nbins for e in range(1, nbins + 1)]
-    out["min_edge_gap"] = float(min(np.min(np.abs(r - e)) for e in edges)) / rc
+    vw = lattice_vectors(b, rc * 1.01)  # shells just outside rc count for the gap too
+    rw = np.sqrt((vw * vw).sum(axis=1))
+    out["min_edge_gap"] = float(min(np.min(np.abs(rw - e)) for e in edges)) / rc
     return out
