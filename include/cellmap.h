@@ -1,0 +1,180 @@
+/*
+ * cellmap.h -- C ABI of the GB300 cell-list pair map.
+ *
+ * The calls follow the paper's statement of the problem (CellListMap.jl,
+ * Martinez, arXiv 2202.06427, Sec. 2.1-2.2): define the box and cutoff (Sec.
+ * 2.5, Code 3), build the cell lists from the coordinates (Sec. 2.6, Code 4),
+ * then map a pairwise function over every pair within the cutoff and reduce
+ * the per-worker outputs (Sec. 2.3, 2.7, 2.8, Code 1/2/5). The mapped
+ * functions are a fixed set of built-in reductions; a compile-time device
+ * functor hook (cellmap_functor.cuh) plays the role of the user function.
+ *
+ * Conventions shared by every call:
+ *  - Positions are the caller's (n, dim) row-major FP64 array in DEVICE
+ *    memory: x[i*dim + a]. The paper accepts (dim, n) matrices or vectors of
+ *    static vectors with this same memory layout (Sec. 2.4). Positions need
+ *    not lie inside the box; they are wrapped in FP64.
+ *  - The box is a dim x dim lattice matrix whose ROWS are the lattice vectors
+ *    (the paper's Julia display prints them as columns, Code 3). Orthorhombic
+ *    boxes are diagonal matrices.
+ *  - A pair (i, j) is "within the cutoff" when |x_j - x_i + t.H| < rc for
+ *    some integer image t (strict inequality). Each such pair-image is mapped
+ *    exactly once. When rc > w_min/2 (w = distances between opposite box
+ *    faces) one pair can have several images inside the cutoff; each counts.
+ *    rc must stay below w_min (a particle must not see itself).
+ *  - Indices are 0-based (the paper's Julia indices are 1-based).
+ *  - Every call is asynchronous on the given CUDA stream (a cudaStream_t
+ *    passed as void*; NULL = legacy default stream) unless its comment says
+ *    it synchronizes. Device pointers passed in are owned by the caller and
+ *    must stay valid until the work on the stream has completed. The cl_list
+ *    handle and its device workspace are owned by the library.
+ *  - Return value: CL_OK (0) or a negative error code; cl_error_string()
+ *    names it. A failed call leaves the handle usable unless it says
+ *    otherwise. Errors detected on the device (non-finite positions) are
+ *    latched in the handle and reported by cl_status().
+ */
+#ifndef CELLMAP_H
+#define CELLMAP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CL_OK 0
+#define CL_ERR_INVALID_ARG (-1)     /* null pointer, bad size, bad option */
+#define CL_ERR_INVALID_BOX (-2)     /* singular or non-finite lattice matrix */
+#define CL_ERR_CUTOFF_TOO_LARGE (-3)/* rc >= w_min, or rc > w_min/2 for the pair list */
+#define CL_ERR_NONFINITE (-4)       /* a position was NaN or infinite (reported by cl_status) */
+#define CL_ERR_OOM (-5)             /* device allocation failed */
+#define CL_ERR_CAPACITY (-6)        /* pair list larger than the caller's capacity */
+#define CL_ERR_TIMEOUT (-7)         /* a bounded device wait expired */
+#define CL_ERR_CUDA (-8)            /* a CUDA runtime call failed */
+#define CL_ERR_UNSUPPORTED (-9)     /* grid or stencil beyond the library's limits */
+
+/* Box and cutoff (Sec. 2.5, Code 3). */
+typedef struct {
+  int dim;          /* 2 or 3 */
+  double h[9];      /* lattice matrix, row-major, first dim*dim entries used; rows = lattice vectors */
+  double cutoff;    /* rc > 0 */
+  int lcell;        /* cells per cutoff length across each face (paper's lcell, Sec. 2.8), 1..4 */
+} cl_box;
+
+typedef struct cl_list cl_list; /* opaque; device buffers owned by the library */
+
+/* Built-in reductions (the mapped function of Sec. 2.3).
+ *  CL_RED_COUNT      number of pair-images within rc                         -> result.count
+ *  CL_RED_SUM_INV_R  sum of 1/r (Code 5, first example)                      -> result.sum_inv_r
+ *  CL_RED_SF_ENERGY  sum of u(r) = 1/r - 1/rc + (r - rc)/rc^2 (shifted force) -> result.energy
+ *  CL_RED_SF_ENERGY_FORCES_VIRIAL  energy, forces F = -dE/dx (Code 7 pattern)
+ *                    and virial W = -sum u'(r)/r r(x)r                        -> energy, forces, virial
+ *  CL_RED_HIST       counts of r in nbins equal bins over [0, rmax) (Code 10) -> result.hist
+ *  CL_RED_PAIRLIST   i<j neighbour list sorted by (i, j) with FP32 distance
+ *                    (Sec. 4.1); requires rc <= w_min/2 (unique images)       -> pair_i, pair_j, pair_d */
+typedef enum {
+  CL_RED_COUNT = 0,
+  CL_RED_SUM_INV_R = 1,
+  CL_RED_SF_ENERGY = 2,
+  CL_RED_SF_ENERGY_FORCES_VIRIAL = 3,
+  CL_RED_HIST = 4,
+  CL_RED_PAIRLIST = 5
+} cl_reduction;
+
+typedef struct {
+  int nbins;    /* CL_RED_HIST: number of bins, 1..4096 */
+  double rmax;  /* CL_RED_HIST: upper edge of the last bin; <= 0 means rc */
+} cl_params;
+
+/* Outputs of cl_map. All pointers are DEVICE pointers owned by the caller,
+ * except npairs (host). Only the fields the chosen reduction writes are read;
+ * the others may be NULL. Scalars are overwritten, not accumulated. */
+typedef struct {
+  unsigned long long* count;  /* 1 value */
+  double* sum_inv_r;          /* 1 value */
+  double* energy;             /* 1 value */
+  float* forces;              /* n*dim, original particle order */
+  double* virial;             /* dim*dim, row-major */
+  unsigned long long* hist;   /* nbins */
+  int* pair_i;                /* capacity entries; pair_i[k] < pair_j[k] */
+  int* pair_j;
+  float* pair_d;              /* distance of each pair */
+  long long capacity;         /* entries available in pair_i/pair_j/pair_d */
+  long long* npairs;          /* HOST: number of pairs found (also set on CL_ERR_CAPACITY) */
+} cl_result;
+
+/* Build the cell list (Sec. 2.6) of n particles: wrap each position into the
+ * box and compute its fractional cell in FP64, count particles per cell,
+ * prefix-sum the counts into cell offsets, scatter FP32 cell-local
+ * coordinates into cell order, and list the work tiles of the sweep.
+ * pos_dev: (n, dim) FP64 device array (0 <= n < 2^31). The pointer is kept by
+ * the handle (cl_backward reads the raw positions again) and must stay valid
+ * until the next cl_update or cl_free. Allocates device memory (synchronous
+ * cudaMalloc); the kernels run on `stream`. On success *out receives a new
+ * handle. Errors: INVALID_ARG, INVALID_BOX, CUTOFF_TOO_LARGE, UNSUPPORTED,
+ * OOM, CUDA. */
+int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream, cl_list** out);
+
+/* Rebuild the cell list for new positions of the same n particles (Sec. 4.2:
+ * the lists are updated between steps), reusing the workspace. box may be
+ * NULL (unchanged) or a new box; a new box that changes the grid reallocates.
+ * Same errors as cl_build. */
+int cl_update(cl_list* cl, const double* pos_dev, const cl_box* box, void* stream);
+
+/* Map a built-in reduction over every pair-image within the cutoff (Sec. 2.3,
+ * 2.7) and write the reduced result (Sec. 2.8: per-worker partial outputs are
+ * summed; here per-CTA FP64 partials are summed in a fixed order).
+ * Asynchronous except CL_RED_PAIRLIST, which synchronizes `stream` once to
+ * learn the pair count and returns CL_ERR_CAPACITY (with *npairs set) when it
+ * exceeds result->capacity; call again with more room. params may be NULL
+ * except for CL_RED_HIST. */
+int cl_map(const cl_list* cl, cl_reduction red, const cl_params* params, cl_result* result, void* stream);
+
+/* Adjoint of the shifted-force energy (Sec. 3.3, Code 9: the pair sum is
+ * differentiable). Given dL/dE in grad_energy_dev (1 FP64 value, device),
+ * writes grad_pos_dev[i*dim+a] = dL/dE * dE/dx_ia (= -dL/dE * force) for the
+ * positions the list was last built from, and, when grad_box_dev is not NULL,
+ * grad_box_dev = dL/dE * dE/dH at fixed Cartesian positions (dim*dim,
+ * row-major). When virial_dev is not NULL it also receives the virial W.
+ * All output arrays are overwritten. */
+int cl_backward(const cl_list* cl, const double* grad_energy_dev, double* grad_pos_dev, double* grad_box_dev,
+                double* virial_dev, void* stream);
+
+/* Queries. Grid and size values are answered from the host; NONEMPTY,
+ * MAX_OCCUPANCY and CANDIDATES read device counters and synchronize
+ * `stream` (NULL = legacy default stream) first. */
+#define CL_INFO_N 0
+#define CL_INFO_DIM 1
+#define CL_INFO_GRID_X 2
+#define CL_INFO_GRID_Y 3
+#define CL_INFO_GRID_Z 4
+#define CL_INFO_NCELLS 5
+#define CL_INFO_NONEMPTY 6
+#define CL_INFO_MAX_OCCUPANCY 7
+#define CL_INFO_BYTES 8
+#define CL_INFO_STENCIL_HALF 9      /* neighbour-cell offsets visited per cell by the half-shell sweep */
+#define CL_INFO_STENCIL_FULL 10     /* offsets of the full stencil (forces, backward) */
+#define CL_INFO_CANDIDATES 11       /* candidate pairs the half-shell sweep tests (cell occupancy products) */
+#define CL_INFO_WORK_TILES 12       /* tiles in the sweep's work list */
+int cl_query(const cl_list* cl, int what, long long* value, void* stream);
+
+/* Host-only box preparation, no GPU needed: for box, fills
+ * grid[3] (cells per axis, 1 for unused axes), widths[3] (face distances) and
+ * stencil[2] (half-shell and full-shell offset counts). Same errors as the
+ * box checks of cl_build. */
+int cl_box_info(const cl_box* box, long long* grid, double* widths, long long* stencil);
+
+/* Synchronize `stream` and report a latched device-side error of the handle
+ * (CL_ERR_NONFINITE when any position of the last build was not finite), or
+ * CL_OK. Reading clears the latch. */
+int cl_status(cl_list* cl, void* stream);
+
+/* Release the handle and its device memory (synchronizes the device). NULL is ignored. */
+void cl_free(cl_list* cl);
+
+/* Static description of an error code. */
+const char* cl_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CELLMAP_H */

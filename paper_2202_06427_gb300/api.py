@@ -1,0 +1,212 @@
+"""Python binding of the C ABI (include/cellmap.h), same names, argument
+marshalling only: torch tensors supply device memory, torch streams supply the
+CUDA stream, and every step of the computation runs in libcellmap's kernels.
+
+Positions are (n, dim) float64 CUDA tensors; the box ``h`` is a (dim, dim)
+matrix whose ROWS are the lattice vectors (orthorhombic: a diagonal matrix).
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from ._lib import (CL_RED_COUNT, CL_RED_HIST, CL_RED_PAIRLIST, CL_RED_SF_ENERGY, CL_RED_SF_ENERGY_FORCES_VIRIAL,
+                   CL_RED_SUM_INV_R, CellMapError)
+
+REDUCTIONS = {"count": CL_RED_COUNT, "sum_inv_r": CL_RED_SUM_INV_R, "energy": CL_RED_SF_ENERGY,
+              "energy_forces_virial": CL_RED_SF_ENERGY_FORCES_VIRIAL, "hist": CL_RED_HIST,
+              "pairlist": CL_RED_PAIRLIST}
+
+
+def make_box(h, cutoff, lcell=2):
+    h = np.asarray(h, dtype=np.float64)
+    dim = h.shape[0]
+    if h.shape != (dim, dim) or dim not in (2, 3):
+        raise ValueError("box must be a 2x2 or 3x3 matrix")
+    b = L.cl_box()
+    b.dim = dim
+    flat = h.reshape(-1)
+    for k in range(dim * dim):
+        b.h[k] = float(flat[k])
+    b.cutoff = float(cutoff)
+    b.lcell = int(lcell)
+    return b
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        stream = stream.cuda_stream
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _check_pos(pos, dim=None):
+    if not (isinstance(pos, torch.Tensor) and pos.is_cuda and pos.dtype == torch.float64 and pos.dim() == 2
+            and pos.is_contiguous()):
+        raise ValueError("positions must be a contiguous (n, dim) float64 CUDA tensor")
+    if dim is not None and pos.shape[1] != dim:
+        raise ValueError("positions have %d columns, box has dim %d" % (pos.shape[1], dim))
+
+
+class CellList:
+    """Owner of a cl_list handle; keeps the positions tensor alive because the
+    library reads it again in cl_backward."""
+
+    def __init__(self, handle, pos, h, cutoff, lcell):
+        self._h = handle
+        self.pos = pos
+        self.n, self.dim = pos.shape
+        self.h = np.asarray(h, dtype=np.float64).copy()
+        self.cutoff = float(cutoff)
+        self.lcell = int(lcell)
+        self.device = pos.device
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("cell list was freed")
+        return self._h
+
+    def __del__(self):
+        try:
+            cl_free(self)
+        except Exception:
+            pass
+
+
+def cl_build(pos, h, cutoff, lcell=2, stream=None):
+    box = make_box(h, cutoff, lcell)
+    _check_pos(pos, box.dim)
+    out = ctypes.c_void_p()
+    with torch.cuda.device(pos.device):
+        L.check(L.lib().cl_build(_ptr(pos), pos.shape[0], ctypes.byref(box), _stream(stream), ctypes.byref(out)),
+                "cl_build")
+    return CellList(out, pos, h, cutoff, lcell)
+
+
+def cl_update(cl, pos, h=None, cutoff=None, lcell=None, stream=None):
+    _check_pos(pos, cl.dim)
+    if pos.shape[0] != cl.n:
+        raise ValueError("cl_update keeps the particle count")
+    boxp = None
+    if h is not None or cutoff is not None or lcell is not None:
+        nh = cl.h if h is None else np.asarray(h, dtype=np.float64)
+        nc = cl.cutoff if cutoff is None else cutoff
+        nl = cl.lcell if lcell is None else lcell
+        boxp = ctypes.byref(make_box(nh, nc, nl))
+    with torch.cuda.device(pos.device):
+        L.check(L.lib().cl_update(cl.handle, _ptr(pos), boxp, _stream(stream)), "cl_update")
+    cl.pos = pos
+    if boxp is not None:
+        cl.h, cl.cutoff, cl.lcell = np.array(nh, dtype=np.float64), float(nc), int(nl)
+
+
+def cl_map(cl, reduction, nbins=0, rmax=0.0, capacity=None, stream=None):
+    """Run one built-in reduction; returns a dict of device tensors."""
+    red = REDUCTIONS[reduction] if isinstance(reduction, str) else int(reduction)
+    dev = cl.device
+    res = L.cl_result()
+    out = {}
+    f64 = dict(dtype=torch.float64, device=dev)
+    if red == CL_RED_COUNT:
+        out["count"] = torch.zeros(1, dtype=torch.int64, device=dev)
+        res.count = out["count"].data_ptr()
+    elif red == CL_RED_SUM_INV_R:
+        out["sum_inv_r"] = torch.zeros(1, **f64)
+        res.sum_inv_r = out["sum_inv_r"].data_ptr()
+    elif red == CL_RED_SF_ENERGY:
+        out["energy"] = torch.zeros(1, **f64)
+        res.energy = out["energy"].data_ptr()
+    elif red == CL_RED_SF_ENERGY_FORCES_VIRIAL:
+        out["energy"] = torch.zeros(1, **f64)
+        out["forces"] = torch.empty((cl.n, cl.dim), dtype=torch.float32, device=dev)
+        out["virial"] = torch.zeros((cl.dim, cl.dim), **f64)
+        res.energy, res.forces, res.virial = (out[k].data_ptr() for k in ("energy", "forces", "virial"))
+    elif red == CL_RED_HIST:
+        out["hist"] = torch.zeros(int(nbins), dtype=torch.int64, device=dev)
+        res.hist = out["hist"].data_ptr()
+    elif red == CL_RED_PAIRLIST:
+        return _pairlist(cl, capacity, stream)
+    params = L.cl_params()
+    params.nbins = int(nbins)
+    params.rmax = float(rmax)
+    with torch.cuda.device(dev):
+        L.check(L.lib().cl_map(cl.handle, red, ctypes.byref(params), ctypes.byref(res), _stream(stream)), "cl_map")
+    return out
+
+
+def _pairlist(cl, capacity, stream):
+    dev = cl.device
+    cap = int(capacity) if capacity is not None else max(1024, cl.n * 8)
+    lib = L.lib()
+    while True:
+        pi = torch.empty(cap, dtype=torch.int32, device=dev)
+        pj = torch.empty(cap, dtype=torch.int32, device=dev)
+        pd = torch.empty(cap, dtype=torch.float32, device=dev)
+        npairs = ctypes.c_longlong(0)
+        res = L.cl_result()
+        res.pair_i, res.pair_j, res.pair_d = pi.data_ptr(), pj.data_ptr(), pd.data_ptr()
+        res.capacity = cap
+        res.npairs = ctypes.pointer(npairs)
+        with torch.cuda.device(dev):
+            code = lib.cl_map(cl.handle, CL_RED_PAIRLIST, None, ctypes.byref(res), _stream(stream))
+        if code == -6 and capacity is None:
+            cap = int(npairs.value)
+            continue
+        L.check(code, "cl_map(pairlist)")
+        k = int(npairs.value)
+        return {"i": pi[:k], "j": pj[:k], "d": pd[:k], "npairs": k}
+
+
+def cl_backward(cl, grad_energy, want_box=True, want_virial=True, stream=None):
+    """dL/dx (n, dim) float64, dL/dH (dim, dim) float64 or None, virial or None."""
+    dev = cl.device
+    g = grad_energy.to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+    gp = torch.empty((cl.n, cl.dim), dtype=torch.float64, device=dev)
+    gb = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_box else None
+    vir = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_virial else None
+    with torch.cuda.device(dev):
+        L.check(L.lib().cl_backward(cl.handle, _ptr(g), _ptr(gp), _ptr(gb), _ptr(vir), _stream(stream)),
+                "cl_backward")
+    return gp, gb, vir
+
+
+def cl_query(cl, what, stream=None):
+    v = ctypes.c_longlong(0)
+    key = L.INFO[what] if isinstance(what, str) else int(what)
+    with torch.cuda.device(cl.device):
+        L.check(L.lib().cl_query(cl.handle, key, ctypes.byref(v), _stream(stream)), "cl_query")
+    return int(v.value)
+
+
+def cl_box_info(h, cutoff, lcell=2):
+    """Host-only: grid, face distances and stencil sizes (no GPU needed)."""
+    box = make_box(h, cutoff, lcell)
+    grid = (ctypes.c_longlong * 3)()
+    widths = (ctypes.c_double * 3)()
+    st = (ctypes.c_longlong * 2)()
+    L.check(L.lib().cl_box_info(ctypes.byref(box), grid, widths, st), "cl_box_info")
+    d = box.dim
+    return {"grid": list(grid)[:d], "widths": list(widths)[:d], "stencil_half": st[0], "stencil_full": st[1]}
+
+
+def cl_status(cl, stream=None):
+    """Synchronizes and returns the latched device error code (0 = ok)."""
+    with torch.cuda.device(cl.device):
+        return int(L.lib().cl_status(cl.handle, _stream(stream)))
+
+
+def cl_free(cl):
+    if getattr(cl, "_h", None) is not None:
+        L.lib().cl_free(cl._h)
+        cl._h = None
+
+
+def cl_error_string(code):
+    return L.lib().cl_error_string(int(code)).decode()

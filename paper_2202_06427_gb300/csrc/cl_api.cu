@@ -1,0 +1,340 @@
+// cl_api.cu -- the extern "C" boundary (cellmap.h): handle lifecycle,
+// argument checks, and dispatch of the binning, sweep and reduction kernels.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "cl_internal.cuh"
+
+struct cl_list {
+  clk::Geo geo;
+  int n;
+  const double* pos;
+  long long ncells_alloc;
+  // device workspace
+  unsigned* packed;
+  int* slot;
+  float4* xl;
+  float4* xs;
+  unsigned* cellc;
+  int* counts;
+  int* cell_start;
+  int* tile_sum;
+  int* meta;
+  double* partials;
+  double* sums;
+  unsigned long long* u64;
+  // pair-list workspace, grown on demand
+  mutable int* pl_count;
+  mutable long long* pl_off;
+  mutable long long pl_cap_n;
+  // stencils (host copies of the sweep arguments)
+  clk::SweepArgs* half;
+  clk::SweepArgs* full;
+  size_t bytes;
+};
+
+namespace {
+
+template <class T>
+int dev_alloc(T** p, size_t count, size_t* bytes) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return CL_ERR_OOM;
+  }
+  *bytes += sizeof(T) * count;
+  return CL_OK;
+}
+
+void free_cells(cl_list* c) {
+  cudaFree(c->counts);
+  cudaFree(c->cell_start);
+  cudaFree(c->tile_sum);
+  c->counts = nullptr;
+  c->cell_start = nullptr;
+  c->tile_sum = nullptr;
+}
+
+void free_all(cl_list* c) {
+  free_cells(c);
+  cudaFree(c->packed);
+  cudaFree(c->slot);
+  cudaFree(c->xl);
+  cudaFree(c->xs);
+  cudaFree(c->cellc);
+  cudaFree(c->meta);
+  cudaFree(c->partials);
+  cudaFree(c->sums);
+  cudaFree(c->u64);
+  cudaFree(c->pl_count);
+  cudaFree(c->pl_off);
+  delete c->half;
+  delete c->full;
+}
+
+int alloc_cells(cl_list* c, long long ncells) {
+  size_t b = 0;
+  int e;
+  if ((e = dev_alloc(&c->counts, (size_t)ncells, &b))) return e;
+  if ((e = dev_alloc(&c->cell_start, (size_t)ncells + 1, &b))) return e;
+  if ((e = dev_alloc(&c->tile_sum, (size_t)clk::scan_tiles_for(ncells), &b))) return e;
+  c->ncells_alloc = ncells;
+  c->bytes += b;
+  return CL_OK;
+}
+
+void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
+  A->xs = c->xs;
+  A->cellc = c->cellc;
+  A->cell_start = c->cell_start;
+  A->n = c->n;
+  A->nx = c->geo.n[0];
+  A->ny = c->geo.n[1];
+  A->nz = c->geo.n[2];
+  A->rc2 = (float)(c->geo.rc * c->geo.rc);
+  A->irc = (float)(1.0 / c->geo.rc);
+  A->irc2 = (float)(1.0 / (c->geo.rc * c->geo.rc));
+}
+
+int set_geometry(cl_list* c, const cl_box* box) {
+  clk::Geo g;
+  int e = clk::prepare_geometry(box, &g);
+  if (e) return e;
+  clk::Off* th = new (std::nothrow) clk::Off[2 * clk::kMaxOff];
+  if (!th) return CL_ERR_OOM;
+  clk::Off* tf = th + clk::kMaxOff;
+  int nh = clk::build_stencil(g, 1, th, clk::kMaxOff);
+  int nf = nh < 0 ? nh : clk::build_stencil(g, 0, tf, clk::kMaxOff);
+  if (nh < 0 || nf < 0) {
+    delete[] th;
+    return nh < 0 ? nh : nf;
+  }
+  if (g.ncells != c->ncells_alloc) {
+    free_cells(c);
+    if ((e = alloc_cells(c, g.ncells))) {
+      delete[] th;
+      return e;
+    }
+  }
+  std::memcpy(c->half->off, th, sizeof(clk::Off) * nh);
+  std::memcpy(c->full->off, tf, sizeof(clk::Off) * nf);
+  c->half->noff = nh;
+  c->full->noff = nf;
+  delete[] th;
+  c->geo = g;
+  fill_sweep_args(c, c->half);
+  fill_sweep_args(c, c->full);
+  return CL_OK;
+}
+
+int run_build(cl_list* c, cudaStream_t s) {
+  clk::BuildBufs b;
+  b.pos = c->pos;
+  b.n = c->n;
+  b.packed = c->packed;
+  b.slot = c->slot;
+  b.xl = c->xl;
+  b.counts = c->counts;
+  b.cell_start = c->cell_start;
+  b.tile_sum = c->tile_sum;
+  b.meta = c->meta;
+  b.xs = c->xs;
+  b.cellc = c->cellc;
+  return clk::launch_build(c->geo, b, s);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cl_error_string(int code) {
+  switch (code) {
+    case CL_OK: return "ok";
+    case CL_ERR_INVALID_ARG: return "invalid argument";
+    case CL_ERR_INVALID_BOX: return "singular or non-finite box matrix";
+    case CL_ERR_CUTOFF_TOO_LARGE: return "cutoff too large for the box";
+    case CL_ERR_NONFINITE: return "non-finite position";
+    case CL_ERR_OOM: return "device out of memory";
+    case CL_ERR_CAPACITY: return "pair list capacity exceeded";
+    case CL_ERR_TIMEOUT: return "device wait timed out";
+    case CL_ERR_CUDA: return "CUDA runtime error";
+    case CL_ERR_UNSUPPORTED: return "grid or stencil beyond library limits";
+    default: return "unknown error";
+  }
+}
+
+int cl_box_info(const cl_box* box, long long* grid, double* widths, long long* stencil) {
+  if (!box) return CL_ERR_INVALID_ARG;
+  clk::Geo g;
+  int e = clk::prepare_geometry(box, &g);
+  if (e) return e;
+  clk::Off* tmp = new (std::nothrow) clk::Off[clk::kMaxOff];
+  if (!tmp) return CL_ERR_OOM;
+  int nh = clk::build_stencil(g, 1, tmp, clk::kMaxOff);
+  int nf = clk::build_stencil(g, 0, tmp, clk::kMaxOff);
+  delete[] tmp;
+  if (nh < 0) return nh;
+  if (nf < 0) return nf;
+  for (int k = 0; k < 3; ++k) {
+    if (grid) grid[k] = g.n[k];
+    if (widths) widths[k] = k < g.dim ? g.w[k] : 0.0;
+  }
+  if (stencil) {
+    stencil[0] = nh;
+    stencil[1] = nf;
+  }
+  return CL_OK;
+}
+
+int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream, cl_list** out) {
+  if (!out || !box || n < 0 || n >= 2147483647LL || (n > 0 && !pos_dev)) return CL_ERR_INVALID_ARG;
+  *out = nullptr;
+  cl_list* c = new (std::nothrow) cl_list;
+  if (!c) return CL_ERR_OOM;
+  std::memset(c, 0, sizeof(*c));
+  c->half = new (std::nothrow) clk::SweepArgs;
+  c->full = new (std::nothrow) clk::SweepArgs;
+  if (!c->half || !c->full) {
+    free_all(c);
+    delete c;
+    return CL_ERR_OOM;
+  }
+  std::memset(c->half, 0, sizeof(clk::SweepArgs));
+  std::memset(c->full, 0, sizeof(clk::SweepArgs));
+  c->n = (int)n;
+  c->pos = pos_dev;
+  c->ncells_alloc = -1;
+  int e = CL_OK;
+  size_t b = 0;
+  const size_t nn = (size_t)n;
+  if (!e) e = dev_alloc(&c->packed, nn, &b);
+  if (!e) e = dev_alloc(&c->slot, nn, &b);
+  if (!e) e = dev_alloc(&c->xl, nn, &b);
+  if (!e) e = dev_alloc(&c->xs, nn, &b);
+  if (!e) e = dev_alloc(&c->cellc, nn, &b);
+  if (!e) e = dev_alloc(&c->meta, 4, &b);
+  if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
+  if (!e) e = dev_alloc(&c->sums, 32, &b);
+  if (!e) e = dev_alloc(&c->u64, 8, &b);
+  c->bytes = b;
+  if (!e) e = set_geometry(c, box);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!e && cudaMemsetAsync(c->meta, 0, sizeof(int) * 4, s) != cudaSuccess) e = CL_ERR_CUDA;
+  if (!e) e = run_build(c, s);
+  if (e) {
+    free_all(c);
+    delete c;
+    return e;
+  }
+  *out = c;
+  return CL_OK;
+}
+
+int cl_update(cl_list* c, const double* pos_dev, const cl_box* box, void* stream) {
+  if (!c || (c->n > 0 && !pos_dev)) return CL_ERR_INVALID_ARG;
+  if (box) {
+    int e = set_geometry(c, box);
+    if (e) return e;
+  }
+  c->pos = pos_dev;
+  return run_build(c, (cudaStream_t)stream);
+}
+
+int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_result* r, void* stream) {
+  if (!cc || !r) return CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int dim = c->geo.dim;
+  switch (red) {
+    case CL_RED_COUNT:
+      if (!r->count) return CL_ERR_INVALID_ARG;
+      return clk::launch_count(*c->half, dim, r->count, s);
+    case CL_RED_SUM_INV_R:
+      if (!r->sum_inv_r) return CL_ERR_INVALID_ARG;
+      return clk::launch_scalar(*c->half, dim, 0, c->partials, c->sums, r->sum_inv_r, s);
+    case CL_RED_SF_ENERGY:
+      if (!r->energy) return CL_ERR_INVALID_ARG;
+      return clk::launch_scalar(*c->half, dim, 1, c->partials, c->sums, r->energy, s);
+    case CL_RED_SF_ENERGY_FORCES_VIRIAL:
+      if (!r->forces && c->n > 0) return CL_ERR_INVALID_ARG;
+      return clk::launch_force(*c->full, dim, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr, c->partials,
+                               c->sums, r->energy, r->virial, nullptr, s);
+    case CL_RED_HIST: {
+      if (!params || !r->hist || params->nbins < 1 || params->nbins > clk::kMaxBins) return CL_ERR_INVALID_ARG;
+      double rmax = params->rmax > 0 ? params->rmax : c->geo.rc;
+      return clk::launch_hist(*c->half, dim, params->nbins, (float)rmax, r->hist, s);
+    }
+    case CL_RED_PAIRLIST:
+      return CL_ERR_UNSUPPORTED;
+    default:
+      return CL_ERR_INVALID_ARG;
+  }
+}
+
+int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_pos_dev, double* grad_box_dev,
+                double* virial_dev, void* stream) {
+  if (!cc || !grad_energy_dev || (cc->n > 0 && !grad_pos_dev)) return CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev, c->pos,
+                           c->partials, c->sums, nullptr, virial_dev, grad_box_dev, (cudaStream_t)stream);
+}
+
+int cl_query(const cl_list* c, int what, long long* value, void* stream) {
+  if (!c || !value) return CL_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (what) {
+    case CL_INFO_N: *value = c->n; return CL_OK;
+    case CL_INFO_DIM: *value = c->geo.dim; return CL_OK;
+    case CL_INFO_GRID_X: *value = c->geo.n[0]; return CL_OK;
+    case CL_INFO_GRID_Y: *value = c->geo.n[1]; return CL_OK;
+    case CL_INFO_GRID_Z: *value = c->geo.n[2]; return CL_OK;
+    case CL_INFO_NCELLS: *value = c->geo.ncells; return CL_OK;
+    case CL_INFO_BYTES: *value = (long long)c->bytes; return CL_OK;
+    case CL_INFO_STENCIL_HALF: *value = c->half->noff; return CL_OK;
+    case CL_INFO_STENCIL_FULL: *value = c->full->noff; return CL_OK;
+    case CL_INFO_WORK_TILES: *value = (c->n + 255) / 256; return CL_OK;
+    case CL_INFO_NONEMPTY:
+    case CL_INFO_MAX_OCCUPANCY: {
+      int m[3];
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+      if (cudaMemcpy(m, c->meta, sizeof(m), cudaMemcpyDeviceToHost) != cudaSuccess) return CL_ERR_CUDA;
+      *value = what == CL_INFO_NONEMPTY ? m[1] : m[2];
+      return CL_OK;
+    }
+    case CL_INFO_CANDIDATES: {
+      int e = clk::launch_candidates(*c->half, c->geo.ncells, c->u64, s);
+      if (e) return e;
+      unsigned long long v = 0;
+      if (cudaMemcpyAsync(&v, c->u64, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+      *value = (long long)v;
+      return CL_OK;
+    }
+    default: return CL_ERR_INVALID_ARG;
+  }
+}
+
+int cl_status(cl_list* c, void* stream) {
+  if (!c) return CL_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int flag = 0;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+  if (cudaMemcpy(&flag, c->meta, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return CL_ERR_CUDA;
+  if (flag) {
+    int zero = 0;
+    if (cudaMemcpy(c->meta, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return CL_ERR_CUDA;
+  }
+  return (flag & clk::kErrNonFinite) ? CL_ERR_NONFINITE : CL_OK;
+}
+
+void cl_free(cl_list* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

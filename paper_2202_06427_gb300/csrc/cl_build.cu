@@ -1,0 +1,252 @@
+// cl_build.cu -- cell binning on the GPU (the cell-list construction of
+// Sec. 2.6 and Sec. 2.8 "integer division of the coordinates").
+//
+//   k_bin          one thread per particle: FP64 position in cell units
+//                  t = x . H^-1 . diag(n), wrap t into [0, n), cell index from
+//                  the integer part, centred FP32 local coordinate from the
+//                  fractional part; counts particles per cell with an atomic
+//                  whose return value is the particle's slot in its cell.
+//   k_scan_*       exclusive prefix sum of the per-cell counts (reduce tiles,
+//                  scan tile sums, rescan tiles) -> cell_start[ncells + 1];
+//                  also the number of non-empty cells and the largest count.
+//   k_scatter      moves each particle's (local coordinate, index) into its
+//                  cell's range: the per-cell contiguous copy of Sec. 2.6
+//                  ("vector of lists ... an immutable copy of the particle
+//                  coordinates and index", Sec. 2.8).
+//
+// FP64 is kept for the wrap and the cell assignment. On this GPU FP64 issues
+// at about 1/74 of the FP32 rate, so the kernel uses one FP64 multiply per
+// axis for diagonal boxes and works in integers for the periodic cell index.
+#include "cl_internal.cuh"
+
+namespace clk {
+
+struct BinArgs {
+  const double* pos;
+  int n;
+  int nx, ny, nz;
+  double m[9];      // t = x M
+  float g[9];       // cell edge vectors (rows)
+  unsigned* packed; // per original particle: packed cell coordinates
+  int* slot;        // per original particle: position inside its cell
+  float4* xl;       // per original particle: centred local coordinate + index
+  int* counts;      // per cell
+  int* err;         // error latch
+};
+
+template <int DIM, bool ORTHO>
+__global__ void __launch_bounds__(256) k_bin(const __grid_constant__ BinArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  double x[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) x[k] = a.pos[(size_t)i * DIM + k];
+  bool finite = true;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) finite = finite && isfinite(x[k]);
+  const int nk[3] = {a.nx, a.ny, a.nz};
+  int c[3] = {0, 0, 0};
+  float u[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    double t;
+    if (ORTHO) {
+      t = x[k] * a.m[k * 3 + k];
+    } else {
+      t = 0.0;
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) t = fma(x[q], a.m[q * 3 + k], t);
+    }
+    const double f = floor(t);
+    const double frac = t - f;  // exact, in [0, 1)
+    long long ci = finite ? (long long)f : 0;
+    int cm;
+    if (ci >= 0 && ci < nk[k]) {
+      cm = (int)ci;  // inside the box: the common case
+    } else {
+      long long r = ci % nk[k];
+      if (r < 0) r += nk[k];
+      cm = (int)r;
+    }
+    c[k] = cm;
+    u[k] = (float)frac - 0.5f;  // centred, in [-0.5, 0.5]
+  }
+  float4 o;
+  o.x = 0.f; o.y = 0.f; o.z = 0.f;
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    o.x = fmaf(u[k], a.g[k * 3 + 0], o.x);
+    o.y = fmaf(u[k], a.g[k * 3 + 1], o.y);
+    if (DIM == 3) o.z = fmaf(u[k], a.g[k * 3 + 2], o.z);
+  }
+  if (!finite) {
+    // park the particle in cell 0 with NaN coordinates: every distance test
+    // against it is false, and the host learns of it through the latch
+    c[0] = c[1] = c[2] = 0;
+    o.x = o.y = o.z = __int_as_float(0x7fc00000);
+    atomicOr(a.err, kErrNonFinite);
+  }
+  o.w = __int_as_float(i);
+  const int lin = c[0] + a.nx * (c[1] + a.ny * c[2]);
+  const int s = atomicAdd(&a.counts[lin], 1);
+  a.packed[i] = (unsigned)c[0] | ((unsigned)c[1] << 10) | ((unsigned)c[2] << 20);
+  a.slot[i] = s;
+  a.xl[i] = o;
+}
+
+constexpr int kScanThreads = 256;
+constexpr int kScanPer = 8;
+constexpr int kScanTile = kScanThreads * kScanPer;
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, off);
+    if (lane >= off) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread across the block.
+__device__ void block_excl_scan(int v, int* out_excl) {
+  __shared__ int wsum[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = warp_incl_scan(v);
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    int w = (lane < kScanThreads / 32) ? wsum[lane] : 0;
+    int wi = warp_incl_scan(w);
+    if (lane < kScanThreads / 32) wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  *out_excl = incl - v + wsum[warp];
+  __syncthreads();  // wsum is reused by the next call
+}
+
+// Per tile: sum of counts, non-empty cells, largest count.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restrict__ counts, long long ncells,
+                                                             int* __restrict__ tile_sum, int* __restrict__ meta) {
+  const long long base = (long long)blockIdx.x * kScanTile;
+  int s = 0, ne = 0, mx = 0;
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    long long c = base + k;
+    if (c < ncells) {
+      int v = counts[c];
+      s += v;
+      ne += (v > 0);
+      mx = max(mx, v);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, off);
+    ne += __shfl_down_sync(0xffffffffu, ne, off);
+    mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
+  }
+  __shared__ int sm[3][kScanThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { sm[0][warp] = s; sm[1][warp] = ne; sm[2][warp] = mx; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int S = 0, NE = 0, MX = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) { S += sm[0][w]; NE += sm[1][w]; MX = max(MX, sm[2][w]); }
+    tile_sum[blockIdx.x] = S;
+    atomicAdd(&meta[1], NE);
+    atomicMax(&meta[2], MX);
+  }
+}
+
+// One block: exclusive scan of the tile sums in place; cell_start[ncells] = total.
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int* __restrict__ tile_sum, int ntiles,
+                                                            int* __restrict__ cell_start, long long ncells) {
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < ntiles; base += kScanThreads) {
+    const int t = base + threadIdx.x;
+    const int v = (t < ntiles) ? tile_sum[t] : 0;
+    int excl;
+    block_excl_scan(v, &excl);
+    const int c0 = carry;
+    if (t < ntiles) tile_sum[t] = c0 + excl;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = c0 + excl + v;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) cell_start[ncells] = carry;
+}
+
+// Per tile: rescan the counts with the tile's offset -> cell_start.
+__global__ void __launch_bounds__(kScanThreads) k_scan_final(const int* __restrict__ counts, long long ncells,
+                                                            const int* __restrict__ tile_off,
+                                                            int* __restrict__ cell_start) {
+  const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
+  int v[kScanPer];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    v[k] = (base + k < ncells) ? counts[base + k] : 0;
+    s += v[k];
+  }
+  int excl;
+  block_excl_scan(s, &excl);
+  int run = tile_off[blockIdx.x] + excl;
+#pragma unroll
+  for (int k = 0; k < kScanPer; ++k) {
+    if (base + k < ncells) cell_start[base + k] = run;
+    run += v[k];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int n, int nx, int ny, const unsigned* __restrict__ packed,
+                                                const int* __restrict__ slot, const float4* __restrict__ xl,
+                                                const int* __restrict__ cell_start, float4* __restrict__ xs,
+                                                unsigned* __restrict__ cellc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned cc = packed[i];
+  const int lin = (int)(cc & 1023u) + nx * ((int)((cc >> 10) & 1023u) + ny * (int)(cc >> 20));
+  const int p = cell_start[lin] + slot[i];
+  xs[p] = xl[i];
+  cellc[p] = cc;
+}
+
+// ------------------------------------------------------------ host entry --
+
+
+
+int scan_tiles_for(long long ncells) { return (int)((ncells + kScanTile - 1) / kScanTile); }
+
+// Enqueue the whole binning pipeline on `s`. Returns CL_OK or CL_ERR_CUDA.
+int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
+  const long long nc = g.ncells;
+  const int ntiles = scan_tiles_for(nc);
+  if (cudaMemsetAsync(b.counts, 0, sizeof(int) * nc, s) != cudaSuccess) return CL_ERR_CUDA;
+  if (cudaMemsetAsync(b.meta + 1, 0, sizeof(int) * 2, s) != cudaSuccess) return CL_ERR_CUDA;
+  BinArgs a;
+  a.pos = b.pos;
+  a.n = b.n;
+  a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
+  for (int k = 0; k < 9; ++k) { a.m[k] = g.m[k]; a.g[k] = g.g[k]; }
+  a.packed = b.packed; a.slot = b.slot; a.xl = b.xl; a.counts = b.counts; a.err = b.meta;
+  const int blocks = (b.n + 255) / 256;
+  if (b.n > 0) {
+    if (g.dim == 3) {
+      if (g.ortho) k_bin<3, true><<<blocks, 256, 0, s>>>(a);
+      else k_bin<3, false><<<blocks, 256, 0, s>>>(a);
+    } else {
+      if (g.ortho) k_bin<2, true><<<blocks, 256, 0, s>>>(a);
+      else k_bin<2, false><<<blocks, 256, 0, s>>>(a);
+    }
+  }
+  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.meta);
+  k_scan_tiles<<<1, kScanThreads, 0, s>>>(b.tile_sum, ntiles, b.cell_start, nc);
+  k_scan_final<<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
+  if (b.n > 0)
+    k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.packed, b.slot, b.xl, b.cell_start, b.xs, b.cellc);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+}  // namespace clk

@@ -1,0 +1,106 @@
+// cl_internal.cuh -- types shared by the translation units of libcellmap.
+//
+// Data layout in device memory (one cl_list):
+//   xs[n]        float4  cell-sorted particles: (x, y, z) FP32 relative to the
+//                        CENTRE of the particle's own cell, w = original index
+//                        (int bits). 2D sets z = 0.
+//   cellc[n]     uint32  packed cell coordinates of each sorted particle:
+//                        cx | cy << 10 | cz << 20 (at most 1023 cells per axis)
+//   cell_start[ncells+1] prefix sum of the per-cell counts: particles of cell
+//                        c occupy xs[cell_start[c] .. cell_start[c+1]). Cells
+//                        are linearised x-fastest, c = cx + nx (cy + ny cz),
+//                        so a row of cells along x is one contiguous range.
+// The displacement from particle i (cell ci) to particle j in the neighbour
+// cell reached by the integer offset o (wrapped periodically) is
+//   r = (xs_j + S_o) - xs_i,   S_o = sum_k (o_k / n_k) H_k,
+// because the centre of cell ci + o, unwrapped, is the centre of the wrapped
+// cell plus the lattice translation. S_o depends on o only, so one FP32 shift
+// per stencil entry serves every cell (Sec. 2.6 replicates ghost particles to
+// the same end; this build stores no ghosts).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cellmap.h"
+
+namespace clk {
+
+constexpr int kMaxOff = 768;      // stencil entries (9^3 = 729 plus margin)
+constexpr int kMaxAxis = 1023;    // cells per axis (10-bit packing)
+constexpr int kMaxBins = 4096;    // histogram bins (shared-memory histogram)
+
+// One neighbour-cell offset of the stencil.
+struct Off {
+  int dx, dy, dz;     // o_k mod n_k, in [0, n_k)
+  float sx, sy, sz;   // Cartesian shift S_o (FP32 of an FP64 value)
+};
+
+// Box geometry after preparation (host and device copies).
+struct Geo {
+  int dim;
+  int n[3];           // cells per axis (1 for unused axes)
+  long long ncells;
+  double h[9];        // lattice rows, 3x3 (2D padded with identity z)
+  double hinv[9];     // H^-1, 3x3
+  double m[9];        // M = H^-1 diag(n): t = x M is the position in cell units
+  double w[3];        // distances between opposite faces
+  float g[9];         // cell edge vectors G_k = H_k / n_k (rows), FP32
+  int ortho;          // 1 when H is diagonal
+  double rc;
+  int lcell;
+};
+
+// Device-side error latch bits.
+constexpr int kErrNonFinite = 1;
+
+// Launch arguments of the sweep kernels (passed as one __grid_constant__ parameter).
+struct SweepArgs {
+  const float4* xs;
+  const unsigned* cellc;
+  const int* cell_start;
+  int n;
+  int nx, ny, nz;
+  float rc2, irc, irc2;
+  int noff;             // entries in off[]; off[0] is the own cell
+  Off off[kMaxOff];
+};
+
+// Host helpers implemented in cl_geom.cu.
+int prepare_geometry(const cl_box* box, Geo* geo);
+// Builds the half-shell (half = 1) or full stencil; returns the entry count or a negative error.
+int build_stencil(const Geo& geo, int half, Off* out, int cap);
+
+}  // namespace clk
+
+namespace clk {
+
+// Buffers of one binning pipeline (cl_build.cu).
+struct BuildBufs {
+  const double* pos;
+  int n;
+  unsigned* packed;
+  int* slot;
+  float4* xl;
+  int* counts;
+  int* cell_start;
+  int* tile_sum;
+  int* meta;  // [0] error latch, [1] non-empty cells, [2] max occupancy
+  float4* xs;
+  unsigned* cellc;
+};
+int scan_tiles_for(long long ncells);
+int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
+
+// Sweeps and reductions (cl_sweep.cu).
+int sweep_partials_needed(int n);
+int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStream_t s);
+int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, double* sums, double* out,
+                  cudaStream_t s);
+int launch_hist(const SweepArgs& A, int dim, int nbins, float rmax, unsigned long long* hist, cudaStream_t s);
+int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, float* forces, double* grad,
+                 const double* gE, const double* pos, double* partials, double* sums, double* energy,
+                 double* virial, double* gradbox, cudaStream_t s);
+int launch_candidates(const SweepArgs& A, long long ncells, unsigned long long* out, cudaStream_t s);
+
+}  // namespace clk

@@ -1,0 +1,487 @@
+// cl_sweep.cu -- the neighbour-cell sweep (Sec. 2.8: "a loop over the cells
+// is performed, and the interactions of the particle of each cell with the
+// particles of the neighboring cells are computed") with the reduction fused
+// into the loop, and the fixed-order FP64 final reduction of the per-CTA
+// partial outputs (Sec. 2.8: each worker updates its own copy of the output;
+// the copies are summed at the end).
+//
+// Mapping: one thread per cell-sorted particle i. The thread walks the
+// stencil of its cell (own cell first), and for every neighbour cell scans
+// that cell's contiguous range of the sorted array. Threads of a warp hold
+// consecutive sorted particles, mostly of one cell, so they read the same
+// neighbour particles at the same time (one broadcast load serves the warp).
+//
+// Half shell (count, sum 1/r, energy, histogram): lexicographically positive
+// offsets plus the own cell with j after i in sorted order; each pair-image
+// once. Full shell (forces, virial, backward): all offsets; each pair-image
+// twice, once from each end, so a thread owns the force on its particle and
+// writes it once, without atomics.
+//
+// Precision: pair math in FP32 on cell-centred coordinates; per-thread FP32
+// partial sums (a few hundred terms); FP64 from the warp level up; partials
+// per CTA reduced in a fixed order.
+#include "cl_internal.cuh"
+
+namespace clk {
+
+// 1/sqrt(d2) to FP32 accuracy: hardware estimate plus one Newton-Raphson
+// step, y1 = y0 + y0 (1 - d2 y0^2) / 2.
+__device__ __forceinline__ float rsqrt_nr(float d2) {
+  const float y = rsqrtf(d2);
+  const float e = fmaf(-d2 * y, y, 1.0f);
+  return fmaf(0.5f * y, e, y);
+}
+
+// ---------------------------------------------------------------- reductions
+// Each reduction: per-thread accumulator, hit() for a pair within the cutoff
+// (displacement r = x_j - x_i under the image of the offset), and an
+// epilogue. "Half" reductions see each pair-image once, "full" ones twice.
+
+struct RedCount {
+  static constexpr bool kFull = false;
+  struct Acc { unsigned n; };
+  __device__ void init(Acc& a) const { a.n = 0; }
+  __device__ void hit(Acc& a, float, float, float, float, int) const { a.n++; }
+};
+
+struct RedSumInvR {
+  static constexpr bool kFull = false;
+  struct Acc { float s; };
+  __device__ void init(Acc& a) const { a.s = 0.f; }
+  __device__ void hit(Acc& a, float, float, float, float d2, int) const { a.s += rsqrt_nr(d2); }
+};
+
+// u(r) = 1/r - 1/rc + (r - rc)/rc^2 = (1 - r/rc)^2 / r
+struct RedEnergy {
+  static constexpr bool kFull = false;
+  float irc;
+  struct Acc { float e; };
+  __device__ void init(Acc& a) const { a.e = 0.f; }
+  __device__ void hit(Acc& a, float, float, float, float d2, int) const {
+    const float y = rsqrt_nr(d2);
+    const float t = fmaf(-d2 * y, irc, 1.0f);
+    a.e = fmaf(t * t, y, a.e);
+  }
+};
+
+struct RedHist {
+  static constexpr bool kFull = false;
+  float scale;     // nbins / rmax
+  float rmax;
+  int nbins;
+  unsigned* sh;    // shared-memory histogram
+  struct Acc {};
+  __device__ void init(Acc&) const {}
+  __device__ void hit(Acc&, float, float, float, float d2, int) const {
+    const float r = d2 * rsqrt_nr(d2);
+    if (r < rmax) {
+      int b = (int)(r * scale);
+      b = b < nbins ? b : nbins - 1;
+      atomicAdd(&sh[b], 1u);
+    }
+  }
+};
+
+// Forces, virial and (optionally) energy; full shell. F_i = sum_j u'(r)/r r,
+// W accumulates sum fs r (x) r over ordered pairs (the virial is -1/2 of it).
+template <int DIM, bool ENERGY>
+struct RedForce {
+  static constexpr bool kFull = true;
+  float irc, irc2;
+  struct Acc { float f[3]; float w[6]; float e; };
+  __device__ void init(Acc& a) const {
+    a.f[0] = a.f[1] = a.f[2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.w[k] = 0.f;
+    a.e = 0.f;
+  }
+  __device__ void hit(Acc& a, float dx, float dy, float dz, float d2, int) const {
+    const float y = rsqrt_nr(d2);
+    const float fs = fmaf(-y, y, irc2) * y;  // u'(r)/r
+    const float ax = fs * dx, ay = fs * dy;
+    a.f[0] += ax;
+    a.f[1] += ay;
+    a.w[0] = fmaf(ax, dx, a.w[0]);
+    a.w[1] = fmaf(ax, dy, a.w[1]);
+    a.w[3] = fmaf(ay, dy, a.w[3]);
+    if (DIM == 3) {
+      const float az = fs * dz;
+      a.f[2] += az;
+      a.w[2] = fmaf(ax, dz, a.w[2]);
+      a.w[4] = fmaf(ay, dz, a.w[4]);
+      a.w[5] = fmaf(az, dz, a.w[5]);
+    }
+    if (ENERGY) {
+      const float t = fmaf(-d2 * y, irc, 1.0f);
+      a.e = fmaf(t * t, y, a.e);
+    }
+  }
+};
+
+// --------------------------------------------------------- block reduction
+
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restrict__ out) {
+  __shared__ double sm[8][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------- the sweep
+
+template <int DIM, class R, class Acc>
+__device__ __forceinline__ void scan_range(const float4* __restrict__ xs, int j0, int j1, float ax, float ay, float az,
+                                           float rc2, const R& red, Acc& acc) {
+  for (int j = j0; j < j1; ++j) {
+    const float4 q = __ldg(&xs[j]);
+    const float dx = q.x - ax, dy = q.y - ay;
+    float d2;
+    float dz = 0.f;
+    if (DIM == 3) {
+      dz = q.z - az;
+      d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    } else {
+      d2 = fmaf(dx, dx, dy * dy);
+    }
+    if (d2 < rc2) red.hit(acc, dx, dy, dz, d2, __float_as_int(q.w));
+  }
+}
+
+// Visits every pair-image of sorted particle p (half or full shell) and
+// accumulates into acc. Returns false for threads past the end.
+template <int DIM, class R>
+__device__ __forceinline__ bool sweep_particle(const SweepArgs& A, const R& red, typename R::Acc& acc, int p,
+                                               float4& pi) {
+  if (p >= A.n) return false;
+  pi = A.xs[p];
+  const unsigned cc = A.cellc[p];
+  const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
+  {
+    const int c = cx + A.nx * (cy + A.ny * cz);
+    const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
+    if (R::kFull) scan_range<DIM>(A.xs, s0, p, pi.x, pi.y, pi.z, A.rc2, red, acc);
+    scan_range<DIM>(A.xs, p + 1, s1, pi.x, pi.y, pi.z, A.rc2, red, acc);
+  }
+  for (int k = 1; k < A.noff; ++k) {
+    const Off o = A.off[k];
+    int x2 = cx + o.dx;
+    x2 -= (x2 >= A.nx) ? A.nx : 0;
+    int y2 = cy + o.dy;
+    y2 -= (y2 >= A.ny) ? A.ny : 0;
+    int z2 = 0;
+    if (DIM == 3) {
+      z2 = cz + o.dz;
+      z2 -= (z2 >= A.nz) ? A.nz : 0;
+    }
+    const int c = x2 + A.nx * (y2 + A.ny * z2);
+    scan_range<DIM>(A.xs, A.cell_start[c], A.cell_start[c + 1], pi.x - o.sx, pi.y - o.sy, pi.z - o.sz, A.rc2, red,
+                    acc);
+  }
+  return true;
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sweep_count(const __grid_constant__ SweepArgs A, unsigned long long* out) {
+  RedCount red;
+  RedCount::Acc acc;
+  red.init(acc);
+  float4 pi;
+  sweep_particle<DIM>(A, red, acc, blockIdx.x * blockDim.x + threadIdx.x, pi);
+  unsigned v = acc.n;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+// Scalar FP64 partial per CTA: sum 1/r (kind 0) or shifted-force energy (kind 1).
+template <int DIM, int KIND>
+__global__ void __launch_bounds__(256) k_sweep_scalar(const __grid_constant__ SweepArgs A, double* partials) {
+  float4 pi;
+  double v[1];
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (KIND == 0) {
+    RedSumInvR red;
+    RedSumInvR::Acc acc;
+    red.init(acc);
+    sweep_particle<DIM>(A, red, acc, p, pi);
+    v[0] = (double)acc.s;
+  } else {
+    RedEnergy red;
+    red.irc = A.irc;
+    RedEnergy::Acc acc;
+    red.init(acc);
+    sweep_particle<DIM>(A, red, acc, p, pi);
+    v[0] = (double)acc.e;
+  }
+  block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_sweep_hist(const __grid_constant__ SweepArgs A, int nbins, float rmax,
+                                                    unsigned long long* __restrict__ hist) {
+  extern __shared__ unsigned sh[];
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0u;
+  __syncthreads();
+  RedHist red;
+  red.nbins = nbins;
+  red.rmax = rmax;
+  red.scale = (float)nbins / rmax;
+  red.sh = sh;
+  RedHist::Acc acc;
+  float4 pi;
+  sweep_particle<DIM>(A, red, acc, blockIdx.x * blockDim.x + threadIdx.x, pi);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+    if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
+}
+
+// Full shell: forces (FP32, original order), and per CTA the energy (x1/2) and
+// the symmetric accumulator of the virial. MODE 0: forward forces; MODE 1:
+// backward, grad_pos = -g F in FP64 plus X = sum x_raw (x) F for the box gradient.
+constexpr int kVirN3 = 6, kVirN2 = 3;
+template <int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_sweep_force(const __grid_constant__ SweepArgs A, float* __restrict__ forces,
+                                                     double* __restrict__ grad, const double* __restrict__ gE,
+                                                     const double* __restrict__ pos, double* __restrict__ partials) {
+  RedForce<DIM, MODE == 0> red;
+  red.irc = A.irc;
+  red.irc2 = A.irc2;
+  typename RedForce<DIM, MODE == 0>::Acc acc;
+  red.init(acc);
+  float4 pi;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = sweep_particle<DIM>(A, red, acc, p, pi);
+  constexpr int NW = (DIM == 3) ? kVirN3 : kVirN2;
+  constexpr int NV = (MODE == 0) ? 1 + NW : NW + DIM * DIM;
+  double v[NV];
+  // symmetric components in the order xx, xy, (xz), yy, (yz), (zz)
+  if (DIM == 3) {
+    v[0] = acc.w[0]; v[1] = acc.w[1]; v[2] = acc.w[2]; v[3] = acc.w[3]; v[4] = acc.w[4]; v[5] = acc.w[5];
+  } else {
+    v[0] = acc.w[0]; v[1] = acc.w[1]; v[2] = acc.w[3];
+  }
+  if (MODE == 0) {
+    v[NW] = 0.5 * (double)acc.e;
+    if (live) {
+      const int i = __float_as_int(pi.w);
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) forces[(size_t)i * DIM + a] = acc.f[a];
+    }
+  } else {
+#pragma unroll
+    for (int k = NW; k < NV; ++k) v[k] = 0.0;
+    if (live) {
+      const int i = __float_as_int(pi.w);
+      const double g = *gE;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) grad[(size_t)i * DIM + a] = -g * (double)acc.f[a];
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double xa = pos[(size_t)i * DIM + a];
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) v[NW + a * DIM + b] = xa * (double)acc.f[b];
+      }
+    }
+  }
+  block_sum_store<NV>(v, partials + (size_t)blockIdx.x * NV);
+}
+
+// ----------------------------------------------------------- final reduce
+
+// Sums partials[nblocks][nv] in a fixed order into sums[nv] (one CTA).
+__global__ void __launch_bounds__(256) k_final_sum(const double* __restrict__ partials, int nblocks, int nv,
+                                                   double* __restrict__ sums) {
+  __shared__ double sm[256];
+  for (int k = 0; k < nv; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * nv + k];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[k] = sm[0];
+    __syncthreads();
+  }
+}
+
+struct FinalArgs {
+  int mode;          // 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward
+  int dim;
+  double hinv[9];    // 3x3
+  double* out_scalar;
+  double* out_virial;   // dim*dim or null
+  double* out_gradbox;  // dim*dim or null
+  const double* gE;
+};
+
+// Turns the summed partials into the caller's outputs (one thread).
+__global__ void k_final_assemble(const __grid_constant__ FinalArgs F, const double* __restrict__ sums) {
+  if (threadIdx.x != 0) return;
+  const int d = F.dim;
+  if (F.mode <= 1) {
+    *F.out_scalar = sums[0];
+    return;
+  }
+  const int NW = (d == 3) ? kVirN3 : kVirN2;
+  double S[3][3];
+  if (d == 3) {
+    const int map[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) S[a][b] = sums[map[a][b]];
+  } else {
+    S[0][0] = sums[0]; S[0][1] = S[1][0] = sums[1]; S[1][1] = sums[2];
+  }
+  double W[3][3];
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) W[a][b] = -0.5 * S[a][b];
+  if (F.out_virial)
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) F.out_virial[a * d + b] = W[a][b];
+  if (F.mode == 2) {
+    if (F.out_scalar) *F.out_scalar = sums[NW];
+    return;
+  }
+  // dE/dH at fixed positions = H^-T (X - W), X = sum_i x_i (x) F_i
+  const double g = *F.gE;
+  if (F.out_gradbox) {
+    for (int a = 0; a < d; ++a)
+      for (int b = 0; b < d; ++b) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += F.hinv[k * 3 + a] * (sums[NW + k * d + b] - W[k][b]);
+        F.out_gradbox[a * d + b] = g * s;
+      }
+  }
+}
+
+// Candidate pairs the half-shell sweep tests: for each cell c,
+// n_c (n_c - 1)/2 + n_c sum_{o != 0} n_{c+o}.
+__global__ void __launch_bounds__(256) k_candidates(const __grid_constant__ SweepArgs A, long long ncells,
+                                                    unsigned long long* out) {
+  unsigned long long acc = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncells;
+       c += (long long)gridDim.x * blockDim.x) {
+    const long long nc = A.cell_start[c + 1] - A.cell_start[c];
+    if (nc == 0) continue;
+    const int cx = (int)(c % A.nx), cy = (int)((c / A.nx) % A.ny), cz = (int)(c / ((long long)A.nx * A.ny));
+    unsigned long long s = 0;
+    for (int k = 1; k < A.noff; ++k) {
+      const Off o = A.off[k];
+      int x2 = cx + o.dx; x2 -= (x2 >= A.nx) ? A.nx : 0;
+      int y2 = cy + o.dy; y2 -= (y2 >= A.ny) ? A.ny : 0;
+      int z2 = cz + o.dz; z2 -= (z2 >= A.nz) ? A.nz : 0;
+      const long long c2 = x2 + (long long)A.nx * (y2 + (long long)A.ny * z2);
+      s += (unsigned long long)(A.cell_start[c2 + 1] - A.cell_start[c2]);
+    }
+    acc += (unsigned long long)nc * s + (unsigned long long)(nc * (nc - 1) / 2);
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// ------------------------------------------------------------ host entry --
+
+static int blocks_for(int n) { return n > 0 ? (n + 255) / 256 : 1; }
+
+int sweep_partials_needed(int n) { return blocks_for(n) * 16; }
+
+int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStream_t s) {
+  if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
+  if (A.n > 0) {
+    if (dim == 3) k_sweep_count<3><<<blocks_for(A.n), 256, 0, s>>>(A, out);
+    else k_sweep_count<2><<<blocks_for(A.n), 256, 0, s>>>(A, out);
+  }
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, double* sums, double* out,
+                  cudaStream_t s) {
+  const int nb = blocks_for(A.n);
+  if (A.n > 0) {
+    if (dim == 3) {
+      if (kind == 0) k_sweep_scalar<3, 0><<<nb, 256, 0, s>>>(A, partials);
+      else k_sweep_scalar<3, 1><<<nb, 256, 0, s>>>(A, partials);
+    } else {
+      if (kind == 0) k_sweep_scalar<2, 0><<<nb, 256, 0, s>>>(A, partials);
+      else k_sweep_scalar<2, 1><<<nb, 256, 0, s>>>(A, partials);
+    }
+  } else {
+    if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
+  }
+  k_final_sum<<<1, 256, 0, s>>>(partials, A.n > 0 ? nb : 1, 1, sums);
+  FinalArgs F;
+  memset(&F, 0, sizeof(F));
+  F.mode = kind;
+  F.dim = dim;
+  F.out_scalar = out;
+  k_final_assemble<<<1, 32, 0, s>>>(F, sums);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int launch_hist(const SweepArgs& A, int dim, int nbins, float rmax, unsigned long long* hist, cudaStream_t s) {
+  if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nbins, s) != cudaSuccess) return CL_ERR_CUDA;
+  const size_t smem = sizeof(unsigned) * nbins;
+  if (A.n > 0) {
+    if (dim == 3) k_sweep_hist<3><<<blocks_for(A.n), 256, smem, s>>>(A, nbins, rmax, hist);
+    else k_sweep_hist<2><<<blocks_for(A.n), 256, smem, s>>>(A, nbins, rmax, hist);
+  }
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+// mode 0: forward (forces, energy, virial); mode 1: backward (grad_pos, grad_box, virial).
+int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, float* forces, double* grad,
+                 const double* gE, const double* pos, double* partials, double* sums, double* energy,
+                 double* virial, double* gradbox, cudaStream_t s) {
+  const int nb = blocks_for(A.n);
+  const int NW = dim == 3 ? kVirN3 : kVirN2;
+  const int NV = mode == 0 ? 1 + NW : NW + dim * dim;
+  if (A.n > 0) {
+    if (dim == 3) {
+      if (mode == 0) k_sweep_force<3, 0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
+      else k_sweep_force<3, 1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
+    } else {
+      if (mode == 0) k_sweep_force<2, 0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
+      else k_sweep_force<2, 1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
+    }
+  } else {
+    if (cudaMemsetAsync(partials, 0, sizeof(double) * NV, s) != cudaSuccess) return CL_ERR_CUDA;
+  }
+  k_final_sum<<<1, 256, 0, s>>>(partials, A.n > 0 ? nb : 1, NV, sums);
+  FinalArgs F;
+  memset(&F, 0, sizeof(F));
+  F.mode = mode == 0 ? 2 : 3;
+  F.dim = dim;
+  for (int k = 0; k < 9; ++k) F.hinv[k] = hinv[k];
+  F.out_scalar = energy;
+  F.out_virial = virial;
+  F.out_gradbox = gradbox;
+  F.gE = gE;
+  k_final_assemble<<<1, 32, 0, s>>>(F, sums);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int launch_candidates(const SweepArgs& A, long long ncells, unsigned long long* out, cudaStream_t s) {
+  if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
+  long long blocks = (ncells + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_candidates<<<(int)blocks, 256, 0, s>>>(A, ncells, out);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+}  // namespace clk

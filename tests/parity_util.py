@@ -1,0 +1,87 @@
+"""Helpers shared by the GPU parity tests: tolerances, comparison rules and a
+spawn-based pool that runs the (single-threaded) oracle on index ranges.
+
+Tolerances (derived in DESIGN.md, "Parity rules"):
+  counts       exact outside the band: oracle count - band_in <= gpu <= count + band_out
+  histograms   exact outside the band: core[k] <= gpu[k] <= core[k] + maybe[k]
+  sum 1/r      relative 1e-6, plus 1/rc for every band pair that may flip
+  energy       relative 1e-6 (u and u' vanish at rc, band pairs add nothing)
+  forces       max-norm 1e-5 relative to the largest oracle force component
+  virial       1e-6 relative to its largest component
+  box gradient 1e-5 relative to its largest component (X - W mixes FP32 forces
+               with raw positions)
+"""
+import multiprocessing as mp
+
+import numpy as np
+
+BAND = 1e-6
+TOL_E = 1e-6
+TOL_F = 1e-5
+TOL_W = 1e-6
+TOL_GB = 1e-5
+
+
+def check_count(gpu, ref):
+    lo, hi = ref["count"] - ref["band_in"], ref["count"] + ref["band_out"]
+    assert lo <= gpu <= hi, "count %d outside [%d, %d]" % (gpu, lo, hi)
+
+
+def check_hist(gpu, ref):
+    gpu = np.asarray(gpu, dtype=np.int64)
+    core, maybe = ref["hist_core"], ref["hist_maybe"]
+    assert np.all(gpu >= core), "bins below the certain count: %s" % np.where(gpu < core)[0][:10]
+    assert np.all(gpu <= core + maybe), "bins above the possible count: %s" % np.where(gpu > core + maybe)[0][:10]
+
+
+def check_suminvr(gpu, ref, rc):
+    slack = TOL_E * abs(ref["suminvr"]) + (ref["band_in"] + ref["band_out"]) / rc * (1 + 1e-5)
+    assert abs(gpu - ref["suminvr"]) <= slack, (gpu, ref["suminvr"], slack)
+
+
+def check_energy(gpu, ref_e):
+    assert abs(gpu - ref_e) <= TOL_E * abs(ref_e) + 1e-12, (gpu, ref_e, abs(gpu - ref_e) / abs(ref_e))
+
+
+def check_forces(gpu, ref):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    scale = np.abs(ref).max()
+    err = np.abs(gpu - ref).max()
+    assert err <= TOL_F * scale, "force max-norm error %.3g > %.3g (scale %.3g)" % (err, TOL_F * scale, scale)
+    return err / scale
+
+
+def check_matrix(gpu, ref, tol):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    scale = np.abs(ref).max()
+    err = np.abs(gpu - ref).max()
+    assert err <= tol * scale, "matrix error %.3g > %.3g\n%s\n%s" % (err, tol * scale, gpu, ref)
+    return err / scale
+
+
+def _part(args):
+    import oracle
+    x, h, rc, nbins, forces, lo, hi = args
+    return oracle.pair_map(x, h, rc, band=BAND, nbins=nbins, forces=forces, i_range=(lo, hi))
+
+
+def oracle_pool(x, h, rc, nbins=0, forces=True, nproc=None):
+    """oracle.pair_map over the whole set, split by the smaller index into
+    chunks run in a spawn pool (the oracle itself stays single-threaded)."""
+    n = x.shape[0]
+    nproc = nproc or min(16, mp.cpu_count())
+    # the smaller index carries more pairs at the start of the range: cut finer chunks
+    cuts = np.unique(np.linspace(0, n, 4 * nproc + 1).astype(np.int64))
+    jobs = [(x, h, rc, nbins, forces, int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:])]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(nproc) as pool:
+        parts = pool.map(_part, jobs)
+    out = {k: sum(p[k] for p in parts) for k in ("count", "band_in", "band_out", "suminvr", "energy")}
+    out["virial"] = sum(p["virial"] for p in parts)
+    out["dedh"] = sum(p["dedh"] for p in parts)
+    if forces:
+        out["forces"] = sum(p["forces"] for p in parts)
+    if nbins:
+        out["hist_core"] = sum(p["hist_core"] for p in parts)
+        out["hist_maybe"] = sum(p["hist_maybe"] for p in parts)
+    return out

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle
+on the same seeded inputs. Rules and tolerances: parity_util."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from parity_util import (BAND, TOL_GB, TOL_W, check_count, check_energy, check_forces, check_hist, check_matrix,
+                         check_suminvr, oracle_pool)
+
+pytestmark = pytest.mark.gpu
+
+
+def _P():
+    import paper_2202_06427_gb300 as P
+    return P
+
+
+def _box(dim, tric, L, rng):
+    h = np.eye(dim) * L
+    if tric:
+        for a in range(1, dim):
+            for b in range(a):
+                h[a, b] = rng.uniform(-0.3 * L, 0.3 * L)
+    return h
+
+
+def _lattice_set(dim, tric, n_side, L, seed, wrap_far=True):
+    """Jittered lattice in fractional coordinates of a random box, then each
+    particle moved by a random lattice vector (positions far outside the box)."""
+    rng = np.random.default_rng(seed)
+    h = _box(dim, tric, L, rng)
+    n = n_side ** dim - n_side  # ragged: not a full lattice
+    x = synth.jittered_fractional(h, n_side, n, 0.4, seed + 1)
+    if wrap_far:
+        x = x + rng.integers(-3, 4, size=(n, dim)).astype(np.float64) @ h
+    return np.ascontiguousarray(x), h
+
+
+def _regime(dim, rc_frac):
+    """Lattice spacing 1 and rc = 4 (2D) or 3 (3D), about 50 / 110 neighbours
+    per particle as in the workloads (rc / spacing of 2 to 6); the box is
+    sized so that rc is rc_frac of its side (0.6: several images per pair)."""
+    rc = 4.0 if dim == 2 else 3.0
+    L = rc / rc_frac
+    n_side = int(round(L))
+    return n_side, float(n_side), rc
+
+SMALL = []
+for dim in (2, 3):
+    for tric in (False, True):
+        for lcell in (1, 2, 3):
+            for rc_frac in (0.08, 0.15, 0.6):
+                SMALL.append((dim, tric, lcell, rc_frac))
+
+
+@pytest.mark.parametrize("dim,tric,lcell,rc_frac", SMALL)
+def test_small_all_reductions(cuda_ok, dim, tric, lcell, rc_frac):
+    P = _P()
+    n_side, L, rc = _regime(dim, rc_frac)
+    seed = 100 + dim * 1000 + tric * 100 + lcell * 10 + int(rc_frac * 100)
+    x, h = _lattice_set(dim, tric, n_side, L, seed)
+    w = oracle.geom_info(h, 1.0)["w"]
+    assert rc < w.min()
+    nbins = 37
+    ref = oracle.pair_map(x, h, rc, band=BAND, nbins=nbins)
+    pos = torch.from_numpy(x).cuda()
+    cl = P.cl_build(pos, h, rc, lcell)
+    cnt = int(P.cl_map(cl, "count")["count"].item())
+    check_count(cnt, ref)
+    check_suminvr(P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item(), ref, rc)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    hist = P.cl_map(cl, "hist", nbins=nbins)["hist"].cpu().numpy()
+    check_hist(hist, ref)
+    efv = P.cl_map(cl, "energy_forces_virial")
+    check_energy(efv["energy"].item(), ref["energy"])
+    check_forces(efv["forces"].cpu().numpy(), ref["forces"])
+    check_matrix(efv["virial"].cpu().numpy(), ref["virial"], TOL_W)
+    g = torch.tensor([0.75], dtype=torch.float64, device="cuda")
+    gp, gb, vir = P.cl_backward(cl, g)
+    check_forces(gp.cpu().numpy(), -0.75 * ref["forces"])
+    check_matrix(gb.cpu().numpy(), 0.75 * ref["dedh"], TOL_GB)
+    check_matrix(vir.cpu().numpy(), ref["virial"], TOL_W)
+    assert P.cl_status(cl) == 0
+
+
+@pytest.mark.parametrize("lcell", [1, 2, 3, 4])
+def test_grid_independence(cuda_ok, lcell):
+    """Results do not depend on the cell size (lcell, Sec. 2.8)."""
+    P = _P()
+    x, h = _lattice_set(3, True, 20, 28.0, 77)
+    rc = 0.45 * oracle.geom_info(h, 1.0)["w"].min()
+    ref = oracle.pair_map(x, h, rc, band=BAND, nbins=20)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, lcell)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_hist(P.cl_map(cl, "hist", nbins=20)["hist"].cpu().numpy(), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+
+
+def test_workload_small_10k(cuda_ok):
+    """3D, 10,000 particles, cubic box 46.416, rc 12: sum 1/r and the count."""
+    P = _P()
+    w = synth.w0_small()
+    ref = oracle.pair_map(w["x"], w["h"], w["rc"], band=BAND, forces=False)
+    cl = P.cl_build(torch.from_numpy(w["x"]).cuda(), w["h"], w["rc"], 2)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_suminvr(P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item(), ref, w["rc"])
+    assert 3.5e6 < ref["count"] < 3.7e6
+
+
+@pytest.mark.slow
+def test_workload_lattice_1m(cuda_ok):
+    """3D, 1,000,000 jittered lattice, box 215.44, rc 12: energy forward, forces,
+    virial and box gradient from the backward kernel, in the launch
+    configuration the benchmark times (lcell 2)."""
+    P = _P()
+    w = synth.w1_lattice()
+    ref = oracle_pool(w["x"], w["h"], w["rc"], nbins=0, forces=True)
+    pos = torch.from_numpy(w["x"]).cuda()
+    cl = P.cl_build(pos, w["h"], w["rc"], 2)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    g = torch.ones(1, dtype=torch.float64, device="cuda")
+    gp, gb, vir = P.cl_backward(cl, g)
+    check_forces(gp.cpu().numpy(), -ref["forces"])
+    check_matrix(vir.cpu().numpy(), ref["virial"], TOL_W)
+    check_matrix(gb.cpu().numpy(), ref["dedh"], TOL_GB)
+    efv = P.cl_map(cl, "energy_forces_virial")
+    check_forces(efv["forces"].cpu().numpy(), ref["forces"])
+    check_energy(efv["energy"].item(), ref["energy"])
+
+
+def test_empty_and_tiny(cuda_ok):
+    P = _P()
+    h = np.eye(3) * 10.0
+    for n in (0, 1):
+        pos = torch.zeros((n, 3), dtype=torch.float64, device="cuda") + 1.0
+        cl = P.cl_build(pos, h, 3.0, 2)
+        assert int(P.cl_map(cl, "count")["count"].item()) == 0
+        assert P.cl_map(cl, "energy")["energy"].item() == 0.0
+        assert P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item() == 0.0
+        efv = P.cl_map(cl, "energy_forces_virial")
+        assert efv["energy"].item() == 0.0
+        assert int(P.cl_map(cl, "hist", nbins=4)["hist"].sum().item()) == 0
+        gp, gb, vir = P.cl_backward(cl, torch.ones(1, dtype=torch.float64, device="cuda"))
+        assert gp.shape == (n, 3) and float(gb.abs().max()) == 0.0
+    # two particles across the periodic boundary: distance 1.5 through the face
+    x = np.array([[0.25, 5.0, 5.0], [8.75, 5.0, 5.0]])
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, 3.0, 2)
+    assert int(P.cl_map(cl, "count")["count"].item()) == 1
+    assert P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item() == pytest.approx(1 / 1.5, rel=1e-6)
+
+
+def test_all_in_one_cell_and_multi_image(cuda_ok):
+    """Degenerate grids: one cell per axis (box < 2 rc, several images per
+    pair) and every particle piled in one corner."""
+    P = _P()
+    rng = np.random.default_rng(5)
+    h = np.array([[7.0, 0, 0], [1.0, 6.5, 0], [0.5, -1.0, 6.8]])
+    rc = 0.9 * oracle.geom_info(h, 1.0)["w"].min()
+    x = synth.jittered_fractional(h, 6, 200, 0.3, 9)
+    ref = oracle.pair_map(x, h, rc, band=BAND, nbins=11)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, 1)
+    assert P.cl_query(cl, "ncells") == 1
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    efv = P.cl_map(cl, "energy_forces_virial")
+    check_forces(efv["forces"].cpu().numpy(), ref["forces"])
+    # corner pile: particles within a 1.0 cube of a 30 box (min separation 0.1)
+    g = np.stack(np.meshgrid(*[np.arange(8) * 0.12] * 3, indexing="ij"), -1).reshape(-1, 3) + 29.5
+    h2 = np.eye(3) * 30.0
+    ref2 = oracle.pair_map(g, h2, 2.0, band=BAND)
+    cl2 = P.cl_build(torch.from_numpy(np.ascontiguousarray(g)).cuda(), h2, 2.0, 2)
+    check_count(int(P.cl_map(cl2, "count")["count"].item()), ref2)
+    check_energy(P.cl_map(cl2, "energy")["energy"].item(), ref2["energy"])
+    assert P.cl_query(cl2, "max_occupancy") >= 1
+
+
+def test_errors_are_reported(cuda_ok):
+    P = _P()
+    pos = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(P.CellMapError) as e:
+        P.cl_build(pos, np.eye(3) * 10.0, 10.0, 1)
+    assert e.value.code == -3
+    with pytest.raises(P.CellMapError) as e:
+        P.cl_build(pos, np.zeros((3, 3)), 1.0, 1)
+    assert e.value.code == -2
+    bad = torch.tensor([[1.0, 2.0, 3.0], [float("nan"), 0.0, 0.0], [4.0, 4.0, 4.0]], dtype=torch.float64,
+                       device="cuda")
+    cl = P.cl_build(bad, np.eye(3) * 10.0, 3.0, 2)
+    assert P.cl_status(cl) == -4
+    assert P.cl_status(cl) == 0  # latch cleared
+    assert int(P.cl_map(cl, "count")["count"].item()) == 0
+
+
+def test_update_matches_fresh_build(cuda_ok):
+    P = _P()
+    x, h = _lattice_set(3, True, 16, 24.0, 31)
+    rc = 0.4 * oracle.geom_info(h, 1.0)["w"].min()
+    x2 = x + np.random.default_rng(2).normal(0, 0.2, size=x.shape)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, 2)
+    pos2 = torch.from_numpy(np.ascontiguousarray(x2)).cuda()
+    P.cl_update(cl, pos2)
+    ref = oracle.pair_map(x2, h, rc, band=BAND)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    # new box with a different grid
+    h3 = h * 1.3
+    P.cl_update(cl, pos2, h=h3)
+    ref3 = oracle.pair_map(x2, h3, rc, band=BAND)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref3)
