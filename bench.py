@@ -1,0 +1,331 @@
+"""Benchmark of the cell-list pair map on GB300: in-cutoff pairs per second at
+1M particles.
+
+One step is one pass of the whole hot path over the 1M jittered-lattice
+workload (3D, 100^3 sites at density 0.1, box 215.44, rc 12):
+  cell binning (FP64 wrap, fractional cell, counting sort, prefix sum, scatter)
+  -> half-shell sweep with the shifted-force energy fused in (forward)
+  -> full-shell backward sweep: forces (dE/dx) and virial / box gradient
+  -> fixed-order FP64 reduction of the per-CTA partials.
+value = pairs within the cutoff per step * ranks / time per step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+N > 1 runs under torchrun, one rank per GPU; each rank runs its own replica
+of the workload (the path has no exchange step: replicas only), and the step
+time is the maximum over ranks.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pairs-within-cutoff/sec at 1M particles"
+UNIT = "pairs/s"
+WORKLOAD = "w1_lattice_1m"
+LCELL = 2
+# FP32 arithmetic per pair test and per pair in the cutoff (FMA = 2 FLOP):
+FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j + S - x_i|^2
+FLOP_PER_HIT_BACKWARD = 27  # Newton-refined 1/r (6), u'(r)/r (3), force (6), virial (12)
+FLOP_PER_HIT_ENERGY = 12    # Newton-refined 1/r (6), (1 - r/rc)^2 / r accumulated (6)
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value, world, device=None):
+    """Maximum of a float over the ranks (identity when world == 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world <= 1:
+        return
+    import torch.distributed as dist
+    if device is not None and device.type == "cuda":
+        dist.barrier(device_ids=[device.index])
+    else:
+        dist.barrier()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def gpu_id(dev):
+    """nvidia-smi -i accepts the UUID, which survives CUDA_VISIBLE_DEVICES renumbering."""
+    import torch
+    uuid = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
+    if uuid is None:
+        return str(dev.index)
+    s = str(uuid)
+    return s if s.startswith("GPU-") else "GPU-" + s
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The FP64 oracle as it stands, single-threaded on the host, on a bounded
+    sample: pairs whose smaller index is below k (energy, forces, virial)."""
+    import oracle
+    x, h, rc = w["x"], w["h"], w["rc"]
+    k = 20_000
+    t0 = time.perf_counter()
+    r = oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
+    dt = time.perf_counter() - t0
+    if dt < budget_s / 4:
+        k = min(x.shape[0], int(k * budget_s / max(dt, 1e-3) * 0.8))
+        t0 = time.perf_counter()
+        r = oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
+        dt = time.perf_counter() - t0
+    return {"value": r["count"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "pairs (i<j) with i < %d of the 1M lattice: energy, forces, virial in FP64; %.1f s, %d pairs"
+                      % (k, dt, r["count"]), "seconds": dt, "pairs": r["count"]}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    if rank != 0:
+        return None
+    import synth
+    w = synth.w1_lattice()
+    import oracle
+    x, h, rc = w["x"], w["h"], w["rc"]
+    k = 2000
+    for _ in range(min(args.warmup, 2)):
+        oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
+    times, pairs = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
+        times.append(time.perf_counter() - t0)
+        pairs = r["count"]
+    ms = 1e3 * sum(times) / len(times)
+    value = pairs / (ms / 1e3)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "n": x.shape[0], "cutoff": rc,
+                       "sample": "each step: pairs (i<j) with i < %d" % k},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "pairs (i<j) with i < %d of the 1M lattice per step, FP64 energy, "
+                                       "forces, virial, single thread" % k},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_2202_06427_gb300 as P
+    import synth
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = synth.w1_lattice()
+    x = torch.from_numpy(w["x"]).to(dev)
+    h, rc = w["h"], w["rc"]
+    n = x.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    cl = P.cl_build(x, h, rc, LCELL)
+    pairs = int(P.cl_map(cl, "count")["count"].item())
+    cand_half = P.cl_query(cl, "candidates")
+    g = torch.ones(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def step(ev=None):
+        P.cl_update(cl, x)
+        P.cl_map(cl, "energy")
+        if ev is not None:
+            ev[0].record(stream)
+        P.cl_backward(cl, g)
+        if ev is not None:
+            ev[1].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_id(dev))
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.fill_(float(k))  # evict the inputs from L2 between steps (outside the timed events)
+        starts[k].record(stream)
+        step(kev[k])
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    ms = reduce_max(sum(step_ms) / len(step_ms), world, dev)
+    kms = sum(kern_ms) / len(kern_ms)
+    value = pairs * world / (ms / 1e3)
+
+    # roofline of the dominant kernel (full-shell backward sweep)
+    clocks = sampler.summary()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    max_mhz = clocks["sm_max_mhz"] or 2070.0
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
+    flop = 2 * cand_half * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_BACKWARD
+    achieved = flop / (kms / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_sweep_force<3,1> (cl_backward)",
+                "kernel_ms": kms, "flop_per_launch": flop,
+                "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (of max clock, not measured)" % (sms, max_mhz)}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "box": 215.443469, "cutoff": rc, "lcell": LCELL,
+                       "pairs_per_step": pairs, "candidates_half_shell": cand_half,
+                       "step": "binning + energy sweep (forward) + force/virial sweep (backward)",
+                       "l2": "flushed between steps by a 256 MB write outside the timed events",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gpu_launches": 11 * args.steps,
+            "clocks": clocks, "roofline": roofline}
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(P, cl, w, dev, stream, pairs, args, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    return line
+
+
+def e2e(P, cl, w, dev, stream, pairs, args, world):
+    """Same step through the public API with host buffers: pinned host
+    positions copied in, energy and gradients copied out, every step."""
+    import torch
+    host_x = torch.from_numpy(w["x"]).pin_memory()
+    x = torch.empty_like(host_x, device=dev)
+    out_g = torch.empty(host_x.shape, dtype=torch.float64).pin_memory()
+    out_e = torch.empty(1, dtype=torch.float64).pin_memory()
+    out_b = torch.empty((3, 3), dtype=torch.float64).pin_memory()
+    g = torch.ones(1, dtype=torch.float64, device=dev)
+    steps = max(3, min(args.steps, 50))
+
+    def one():
+        x.copy_(host_x, non_blocking=True)
+        P.cl_update(cl, x)
+        e = P.cl_map(cl, "energy")["energy"]
+        gp, gb, _ = P.cl_backward(cl, g, want_virial=False)
+        out_e.copy_(e, non_blocking=True)
+        out_g.copy_(gp, non_blocking=True)
+        out_b.copy_(gb, non_blocking=True)
+
+    for _ in range(3):
+        one()
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        one()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = reduce_max(a.elapsed_time(b) / steps, world, dev)
+    return {"value": pairs * world / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "h2d_bytes_per_step": host_x.numel() * 8,
+            "d2h_bytes_per_step": out_g.numel() * 8 + 8 + 72}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            import torch
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,58 @@
+"""The multi-rank path of bench.py (replicas, barrier, max of the step time
+over ranks) on CPU with the gloo backend, world size 2."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, _ = bench.dist_env()
+    bench.barrier(w)
+    m = bench.reduce_max(10.0 + 5.0 * rank, w)
+    out[rank] = (r, w, m)
+    dist.destroy_process_group()
+
+
+def test_reduce_max_over_two_gloo_ranks():
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(2, port, out), nprocs=2, join=True)
+    assert out[0] == (0, 2, 15.0)
+    assert out[1] == (1, 2, 15.0)
+
+
+def test_single_rank_is_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.reduce_max(3.5, 1) == 3.5
+    bench.barrier(1)
+
+
+def test_reference_arm_line_shape(monkeypatch):
+    """The reference arm (the FP64 oracle on the host) prints the same metric."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class A:
+        steps, warmup, gpus = 1, 0, 1
+    line = bench.run_reference(A, 0, 1)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert bench.run_reference(A, 1, 2) is None
