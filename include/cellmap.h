@@ -167,6 +167,29 @@ int cl_box_info(const cl_box* box, long long* grid, double* widths, long long* s
  * CL_OK. Reading clears the latch. */
 int cl_status(cl_list* cl, void* stream);
 
+/* Shifted-force energy of a small particle set WITHOUT allocating device
+ * memory (the paper has no counterpart; it exists for callers of this
+ * library). For applications that route all device memory through their own
+ * pool or framework allocator and may not call cudaMalloc/cudaFree, and for
+ * latency-critical loops that cannot afford them: cl_build allocates, this
+ * call does not. It bins the particles and runs the energy sweep exactly as
+ * cl_build + cl_map(CL_RED_SF_ENERGY) would, with every intermediate buffer in
+ * one fixed device array inside the library (3.44 MB, held by every GPU
+ * that loads the library until the process exits).
+ * pos_dev: (n, dim) FP64 device positions; energy_dev: 1 FP64 device value,
+ * overwritten. Limits: n <= CL_NOALLOC_MAX_N and at most
+ * CL_NOALLOC_MAX_CELLS cells in the grid the box and lcell give; larger
+ * inputs return CL_ERR_UNSUPPORTED and launch nothing. Other errors as for
+ * cl_build. A non-finite position never pairs and is not reported.
+ * The first call made with a given device current looks up the array's
+ * device address for that device; make that first call before any stream
+ * capture begins. All calls share the array: calls whose GPU work overlaps
+ * (different streams, or unordered host threads) race and give wrong results;
+ * calls ordered on one stream are safe. Asynchronous on `stream`. */
+#define CL_NOALLOC_MAX_N 65536
+#define CL_NOALLOC_MAX_CELLS 65536
+int cl_energy_noalloc(const double* pos_dev, long long n, const cl_box* box, double* energy_dev, void* stream);
+
 /* Release the handle and its device memory (synchronizes the device). NULL is ignored. */
 void cl_free(cl_list* cl);
 

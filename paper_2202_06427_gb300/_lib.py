@@ -63,6 +63,8 @@ def lib():
         L.cl_status.argtypes = [P, P]
         L.cl_free.argtypes = [P]
         L.cl_free.restype = None
+        L.cl_energy_noalloc.argtypes = [P, ll, ctypes.POINTER(cl_box), P, P]
+        L.cl_energy_noalloc.restype = ctypes.c_int
         L.cl_error_string.argtypes = [i32]
         L.cl_error_string.restype = ctypes.c_char_p
         for f in ("cl_build", "cl_update", "cl_map", "cl_backward", "cl_query", "cl_box_info", "cl_status"):

@@ -208,5 +208,20 @@ def cl_free(cl):
         cl._h = None
 
 
+def cl_energy_noalloc(pos, h, cutoff, lcell=2, out=None, stream=None):
+    """Shifted-force energy without any device allocation inside the library
+    (for callers that may not call cudaMalloc); n <= 65536. ``out`` is a
+    1-element float64 CUDA tensor the caller supplies (allocated here when
+    omitted, by torch, not by the library)."""
+    box = make_box(h, cutoff, lcell)
+    _check_pos(pos, box.dim)
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=pos.device)
+    with torch.cuda.device(pos.device):
+        L.check(L.lib().cl_energy_noalloc(_ptr(pos), pos.shape[0], ctypes.byref(box), _ptr(out), _stream(stream)),
+                "cl_energy_noalloc")
+    return out
+
+
 def cl_error_string(code):
     return L.lib().cl_error_string(int(code)).decode()
