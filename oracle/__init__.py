@@ -51,8 +51,9 @@ def _lib():
         lib.or_pairlist.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
         lib.or_brute_pairlist.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
         lib.or_particles.argtypes = [i32, ll, P, P, dbl, P, ll, P, P]
+        lib.or_neighbors.argtypes = [i32, ll, P, P, dbl, dbl, P, ll, ll, P, P, P, P]
         for f in (lib.or_geom_info, lib.or_map, lib.or_brute_map, lib.or_pairlist,
-                  lib.or_brute_pairlist, lib.or_particles):
+                  lib.or_brute_pairlist, lib.or_particles, lib.or_neighbors):
             f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -169,6 +170,28 @@ def particles(x, h, rc, idx):
     e = np.zeros(idx.shape[0])
     _check(_lib().or_particles(dim, x.shape[0], _p(x), _p(h), rc, _p(idx), idx.shape[0], _p(f), _p(e)))
     return f, e
+
+
+def neighbors(x, h, rc, idx, band=1e-6):
+    """For each a in idx: its j > a with r < rc(1 + 4 band), sorted by j.
+    Returns a list of dicts {"j", "d", "band"}."""
+    x, h, dim = _prep(x, h)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    k = idx.shape[0]
+    cap = max(1024, 512 * k)
+    while True:
+        offs = np.zeros(k + 1, dtype=np.int64)
+        oj = np.zeros(cap, dtype=np.int64)
+        od = np.zeros(cap)
+        ob = np.zeros(cap, dtype=np.int8)
+        rc_ = _lib().or_neighbors(dim, x.shape[0], _p(x), _p(h), rc, band, _p(idx), k, cap, _p(offs), _p(oj),
+                                  _p(od), _p(ob))
+        if rc_ == -4:
+            cap = int(offs[k]) + 1
+            continue
+        _check(rc_)
+        return [{"j": oj[offs[q]:offs[q + 1]], "d": od[offs[q]:offs[q + 1]],
+                 "band": ob[offs[q]:offs[q + 1]].astype(bool)} for q in range(k)]
 
 
 def energy(x, h, rc):

@@ -483,6 +483,84 @@ int or_particles(int dim, long long n, const double* x, const double* h, double 
   return OR_OK;
 }
 
+/* Neighbours j > a of each query particle a (Sec. 4.1 list restricted to the
+ * rows of chosen particles): every j > a with r < rc(1 + 4 band), sorted by
+ * j, with its distance and band flag. Row q occupies out[offs[q] ..
+ * offs[q+1]); offs has k + 1 entries. Returns OR_ERR_CAPACITY when the rows
+ * need more than cap entries (offs[k] then holds the total). */
+static int cmp_j(const void* a, const void* b) {
+  const pl_entry* p = (const pl_entry*)a;
+  const pl_entry* q = (const pl_entry*)b;
+  return (p->j > q->j) - (p->j < q->j);
+}
+
+int or_neighbors(int dim, long long n, const double* x, const double* h, double rc, double band,
+                 const long long* idx, long long k, long long cap, long long* offs, long long* out_j,
+                 double* out_d, signed char* out_band) {
+  geom g;
+  int err = geom_init(&g, dim, h);
+  if (err) return err;
+  if (!(rc > 0) || band < 0) return OR_ERR_ARG;
+  const double rce = rc * (1.0 + 4.0 * band), delta = band * rc;
+  clist cl;
+  err = clist_build(&cl, &g, n, x, rce);
+  if (err) return err;
+  int span[3] = {1, 1, 1};
+  for (int a = 0; a < dim; ++a) span[a] = 2 * cl.m[a] + 1;
+  long long used = 0;
+  pl_entry* row = (pl_entry*)malloc(sizeof(pl_entry) * (size_t)(n > 0 ? n : 1));
+  if (!row) { clist_free(&cl); return OR_ERR_OOM; }
+  for (long long q = 0; q < k; ++q) {
+    long long i = idx[q], m = 0;
+    offs[q] = used;
+    if (i < 0 || i >= n) { free(row); clist_free(&cl); return OR_ERR_ARG; }
+    int ci[3] = {0, 0, 0};
+    long long lin = cl.cell[i];
+    for (int a = 0; a < dim; ++a) { ci[a] = (int)(lin % cl.n[a]); lin /= cl.n[a]; }
+    const double* xi = cl.xw + i * dim;
+    for (int oz = 0; oz < (dim == 3 ? span[2] : 1); ++oz)
+      for (int oy = 0; oy < span[1]; ++oy)
+        for (int ox = 0; ox < span[0]; ++ox) {
+          int o[3] = {ox - cl.m[0], oy - cl.m[1], dim == 3 ? oz - cl.m[2] : 0};
+          long long T[3] = {0, 0, 0}, cj = 0, stride = 1;
+          for (int a = 0; a < dim; ++a) {
+            long long u = (long long)ci[a] + o[a];
+            T[a] = floordiv_ll(u, cl.n[a]);
+            cj += (u - T[a] * cl.n[a]) * stride;
+            stride *= cl.n[a];
+          }
+          double shift[3] = {0, 0, 0};
+          for (int a = 0; a < dim; ++a)
+            for (int b = 0; b < dim; ++b) shift[a] += (double)T[b] * g.h[b][a];
+          for (long long p = cl.start[cj]; p < cl.start[cj + 1]; ++p) {
+            long long j = cl.order[p];
+            if (j <= i) continue;
+            const double* xj = cl.xw + j * dim;
+            double r2 = 0;
+            for (int a = 0; a < dim; ++a) {
+              double d = xj[a] + shift[a] - xi[a];
+              r2 += d * d;
+            }
+            if (!(r2 < rce * rce)) continue;
+            row[m].i = i; row[m].j = j; row[m].r = sqrt(r2); m++;
+          }
+        }
+    qsort(row, (size_t)m, sizeof(pl_entry), cmp_j);
+    for (long long t = 0; t < m; ++t) {
+      if (used < cap) {
+        out_j[used] = row[t].j;
+        out_d[used] = row[t].r;
+        out_band[used] = fabs(row[t].r - rc) <= delta ? 1 : 0;
+      }
+      used++;
+    }
+  }
+  offs[k] = used;
+  free(row);
+  clist_free(&cl);
+  return used > cap ? OR_ERR_CAPACITY : OR_OK;
+}
+
 /* ---------------------------------------------------------- brute force -- */
 
 static int brute_walk(const geom* g, long long n, const double* x, double rc, double band,

@@ -24,10 +24,11 @@ struct cl_list {
   double* partials;
   double* sums;
   unsigned long long* u64;
-  // pair-list workspace, grown on demand
-  mutable int* pl_count;
-  mutable long long* pl_off;
-  mutable long long pl_cap_n;
+  // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
+  int* pl_count;
+  int* pl_start;
+  int* pl_tiles;
+  int* pl_meta;
   // stencils (host copies of the sweep arguments)
   clk::SweepArgs* half;
   clk::SweepArgs* full;
@@ -70,7 +71,9 @@ void free_all(cl_list* c) {
   cudaFree(c->sums);
   cudaFree(c->u64);
   cudaFree(c->pl_count);
-  cudaFree(c->pl_off);
+  cudaFree(c->pl_start);
+  cudaFree(c->pl_tiles);
+  cudaFree(c->pl_meta);
   delete c->half;
   delete c->full;
 }
@@ -144,6 +147,44 @@ int run_build(cl_list* c, cudaStream_t s) {
   b.xs = c->xs;
   b.cellc = c->cellc;
   return clk::launch_build(c->geo, b, s);
+}
+
+// Neighbour list: count pass, scan, one synchronisation to learn the total,
+// fill pass, per-segment sort.
+int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
+  if (!r->npairs || r->capacity < 0) return CL_ERR_INVALID_ARG;
+  for (int k = 0; k < c->geo.dim; ++k)
+    if (!(2.0 * c->geo.rc <= c->geo.w[k])) return CL_ERR_CUTOFF_TOO_LARGE;  // unique images only
+  int e;
+  if (!c->pl_count) {
+    size_t b = 0;
+    const size_t n = (size_t)c->n;
+    if ((e = dev_alloc(&c->pl_count, n, &b)) || (e = dev_alloc(&c->pl_start, n + 1, &b)) ||
+        (e = dev_alloc(&c->pl_tiles, (size_t)clk::scan_tiles_for(c->n), &b)) || (e = dev_alloc(&c->pl_meta, 4, &b))) {
+      cudaFree(c->pl_count);
+      cudaFree(c->pl_start);
+      cudaFree(c->pl_tiles);
+      cudaFree(c->pl_meta);
+      c->pl_count = c->pl_start = c->pl_tiles = c->pl_meta = nullptr;
+      return e;
+    }
+    c->bytes += b;
+  }
+  const int dim = c->geo.dim;
+  if ((e = clk::launch_pairs_count(*c->full, dim, c->pl_count, s))) return e;
+  if ((e = clk::launch_scan(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
+  int total = 0, meta[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(&total, c->pl_start + c->n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(meta, c->pl_meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CL_ERR_CUDA;
+  *r->npairs = total;
+  if (meta[2] > clk::kMaxSegment) return CL_ERR_UNSUPPORTED;
+  if (total > r->capacity) return CL_ERR_CAPACITY;
+  if (total == 0) return CL_OK;
+  if (!r->pair_i || !r->pair_j || !r->pair_d) return CL_ERR_INVALID_ARG;
+  if ((e = clk::launch_pairs_fill(*c->full, dim, c->pl_start, r->pair_i, r->pair_j, r->pair_d, s))) return e;
+  return clk::launch_pairs_sort(c->n, c->pl_count, c->pl_start, r->pair_j, r->pair_d, s);
 }
 
 }  // namespace
@@ -268,7 +309,7 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       return clk::launch_hist(*c->half, dim, params->nbins, (float)rmax, r->hist, s);
     }
     case CL_RED_PAIRLIST:
-      return CL_ERR_UNSUPPORTED;
+      return map_pairlist(c, r, s);
     default:
       return CL_ERR_INVALID_ARG;
   }

@@ -250,3 +250,19 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
 }
 
 }  // namespace clk
+
+namespace clk {
+
+// Exclusive scan of n int counts into start[n + 1] (start[n] = total), with
+// the same three kernels as the cell offsets; meta receives the number of
+// non-zero counts and the largest one.
+int launch_scan(const int* counts, long long n, int* tile_sum, int* start, int* meta, cudaStream_t s) {
+  const int ntiles = scan_tiles_for(n);
+  if (cudaMemsetAsync(meta + 1, 0, sizeof(int) * 2, s) != cudaSuccess) return CL_ERR_CUDA;
+  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, meta);
+  k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sum, ntiles, start, n);
+  k_scan_final<<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, start);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+}  // namespace clk

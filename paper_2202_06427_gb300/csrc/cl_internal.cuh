@@ -91,6 +91,7 @@ struct BuildBufs {
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
+int launch_scan(const int* counts, long long n, int* tile_sum, int* start, int* meta, cudaStream_t s);
 
 // Sweeps and reductions (cl_sweep.cu).
 int sweep_partials_needed(int n);
@@ -102,5 +103,12 @@ int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, floa
                  const double* gE, const double* pos, double* partials, double* sums, double* energy,
                  double* virial, double* gradbox, cudaStream_t s);
 int launch_candidates(const SweepArgs& A, long long ncells, unsigned long long* out, cudaStream_t s);
+
+// Neighbour list (cl_pairs.cu). count[n], start[n+1] (scan of count), tiles,
+// meta: workspace; outputs pair_i/j/d of capacity entries.
+constexpr int kMaxSegment = 1024;  // neighbours j > i of one particle the segment sort handles
+int launch_pairs_count(const SweepArgs& A, int dim, int* count, cudaStream_t s);
+int launch_pairs_fill(const SweepArgs& A, int dim, const int* start, int* pi, int* pj, float* pd, cudaStream_t s);
+int launch_pairs_sort(int n, const int* count, const int* start, int* pj, float* pd, cudaStream_t s);
 
 }  // namespace clk

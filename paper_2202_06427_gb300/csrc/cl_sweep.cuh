@@ -1,0 +1,179 @@
+// cl_sweep.cuh -- device building blocks of the neighbour-cell sweep, shared
+// by the reductions of cl_sweep.cu and the neighbour list of cl_pairs.cu.
+#pragma once
+
+#include "cl_internal.cuh"
+
+namespace clk {
+
+// 1/sqrt(d2) to FP32 accuracy: hardware estimate plus one Newton-Raphson
+// step, y1 = y0 + y0 (1 - d2 y0^2) / 2.
+__device__ __forceinline__ float rsqrt_nr(float d2) {
+  const float y = rsqrtf(d2);
+  const float e = fmaf(-d2 * y, y, 1.0f);
+  return fmaf(0.5f * y, e, y);
+}
+
+// ---------------------------------------------------------------- reductions
+// Each reduction: per-thread accumulator, hit() for a pair within the cutoff
+// (displacement r = x_j - x_i under the image of the offset), and an
+// epilogue. "Half" reductions see each pair-image once, "full" ones twice.
+
+struct RedCount {
+  static constexpr bool kFull = false;
+  struct Acc { unsigned n; };
+  __device__ void init(Acc& a) const { a.n = 0; }
+  __device__ void hit(Acc& a, float, float, float, float, int) const { a.n++; }
+};
+
+struct RedSumInvR {
+  static constexpr bool kFull = false;
+  struct Acc { float s; };
+  __device__ void init(Acc& a) const { a.s = 0.f; }
+  __device__ void hit(Acc& a, float, float, float, float d2, int) const { a.s += rsqrt_nr(d2); }
+};
+
+// u(r) = 1/r - 1/rc + (r - rc)/rc^2 = (1 - r/rc)^2 / r
+struct RedEnergy {
+  static constexpr bool kFull = false;
+  float irc;
+  struct Acc { float e; };
+  __device__ void init(Acc& a) const { a.e = 0.f; }
+  __device__ void hit(Acc& a, float, float, float, float d2, int) const {
+    const float y = rsqrt_nr(d2);
+    const float t = fmaf(-d2 * y, irc, 1.0f);
+    a.e = fmaf(t * t, y, a.e);
+  }
+};
+
+struct RedHist {
+  static constexpr bool kFull = false;
+  float scale;     // nbins / rmax
+  float rmax;
+  int nbins;
+  unsigned* sh;    // shared-memory histogram
+  struct Acc {};
+  __device__ void init(Acc&) const {}
+  __device__ void hit(Acc&, float, float, float, float d2, int) const {
+    const float r = d2 * rsqrt_nr(d2);
+    if (r < rmax) {
+      int b = (int)(r * scale);
+      b = b < nbins ? b : nbins - 1;
+      atomicAdd(&sh[b], 1u);
+    }
+  }
+};
+
+// Forces, virial and (optionally) energy; full shell. F_i = sum_j u'(r)/r r,
+// W accumulates sum fs r (x) r over ordered pairs (the virial is -1/2 of it).
+template <int DIM, bool ENERGY>
+struct RedForce {
+  static constexpr bool kFull = true;
+  float irc, irc2;
+  struct Acc { float f[3]; float w[6]; float e; };
+  __device__ void init(Acc& a) const {
+    a.f[0] = a.f[1] = a.f[2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.w[k] = 0.f;
+    a.e = 0.f;
+  }
+  __device__ void hit(Acc& a, float dx, float dy, float dz, float d2, int) const {
+    const float y = rsqrt_nr(d2);
+    const float fs = fmaf(-y, y, irc2) * y;  // u'(r)/r
+    const float ax = fs * dx, ay = fs * dy;
+    a.f[0] += ax;
+    a.f[1] += ay;
+    a.w[0] = fmaf(ax, dx, a.w[0]);
+    a.w[1] = fmaf(ax, dy, a.w[1]);
+    a.w[3] = fmaf(ay, dy, a.w[3]);
+    if (DIM == 3) {
+      const float az = fs * dz;
+      a.f[2] += az;
+      a.w[2] = fmaf(ax, dz, a.w[2]);
+      a.w[4] = fmaf(ay, dz, a.w[4]);
+      a.w[5] = fmaf(az, dz, a.w[5]);
+    }
+    if (ENERGY) {
+      const float t = fmaf(-d2 * y, irc, 1.0f);
+      a.e = fmaf(t * t, y, a.e);
+    }
+  }
+};
+
+// --------------------------------------------------------- block reduction
+
+template <int NV>
+__device__ __forceinline__ void block_sum_store(double (&v)[NV], double* __restrict__ out) {
+  __shared__ double sm[8][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], off);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sm[warp][k] = v[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------- the sweep
+
+template <int DIM, class R, class Acc>
+__device__ __forceinline__ void scan_range(const float4* __restrict__ xs, int j0, int j1, float ax, float ay, float az,
+                                           float rc2, const R& red, Acc& acc) {
+  for (int j = j0; j < j1; ++j) {
+    const float4 q = __ldg(&xs[j]);
+    const float dx = q.x - ax, dy = q.y - ay;
+    float d2;
+    float dz = 0.f;
+    if (DIM == 3) {
+      dz = q.z - az;
+      d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    } else {
+      d2 = fmaf(dx, dx, dy * dy);
+    }
+    if (d2 < rc2) red.hit(acc, dx, dy, dz, d2, __float_as_int(q.w));
+  }
+}
+
+// Visits every pair-image of sorted particle p (half or full shell) and
+// accumulates into acc. Returns false for threads past the end.
+template <int DIM, class R>
+__device__ __forceinline__ bool sweep_particle(const SweepArgs& A, const R& red, typename R::Acc& acc, int p,
+                                               float4& pi) {
+  if (p >= A.n) return false;
+  pi = A.xs[p];
+  const unsigned cc = A.cellc[p];
+  const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
+  {
+    const int c = cx + A.nx * (cy + A.ny * cz);
+    const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
+    if (R::kFull) scan_range<DIM>(A.xs, s0, p, pi.x, pi.y, pi.z, A.rc2, red, acc);
+    scan_range<DIM>(A.xs, p + 1, s1, pi.x, pi.y, pi.z, A.rc2, red, acc);
+  }
+  for (int k = 1; k < A.noff; ++k) {
+    const Off o = A.off[k];
+    int x2 = cx + o.dx;
+    x2 -= (x2 >= A.nx) ? A.nx : 0;
+    int y2 = cy + o.dy;
+    y2 -= (y2 >= A.ny) ? A.ny : 0;
+    int z2 = 0;
+    if (DIM == 3) {
+      z2 = cz + o.dz;
+      z2 -= (z2 >= A.nz) ? A.nz : 0;
+    }
+    const int c = x2 + A.nx * (y2 + A.ny * z2);
+    scan_range<DIM>(A.xs, A.cell_start[c], A.cell_start[c + 1], pi.x - o.sx, pi.y - o.sy, pi.z - o.sz, A.rc2, red,
+                    acc);
+  }
+  return true;
+}
+
+}  // namespace clk
