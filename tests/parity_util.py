@@ -61,21 +61,27 @@ def check_matrix(gpu, ref, tol):
 
 def _part(args):
     import oracle
-    x, h, rc, nbins, forces, lo, hi = args
+    path, h, rc, nbins, forces, lo, hi = args
+    x = np.load(path, mmap_mode="r")
     return oracle.pair_map(x, h, rc, band=BAND, nbins=nbins, forces=forces, i_range=(lo, hi))
 
 
 def oracle_pool(x, h, rc, nbins=0, forces=True, nproc=None):
     """oracle.pair_map over the whole set, split by the smaller index into
-    chunks run in a spawn pool (the oracle itself stays single-threaded)."""
+    chunks run in a spawn pool (the oracle itself stays single-threaded).
+    The positions reach the workers through a memory-mapped file."""
+    import tempfile
     n = x.shape[0]
     nproc = nproc or min(16, mp.cpu_count())
     # the smaller index carries more pairs at the start of the range: cut finer chunks
     cuts = np.unique(np.linspace(0, n, 4 * nproc + 1).astype(np.int64))
-    jobs = [(x, h, rc, nbins, forces, int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:])]
     ctx = mp.get_context("spawn")
-    with ctx.Pool(nproc) as pool:
-        parts = pool.map(_part, jobs)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = tmp + "/x.npy"
+        np.save(path, np.ascontiguousarray(x, dtype=np.float64))
+        jobs = [(path, h, rc, nbins, forces, int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:])]
+        with ctx.Pool(nproc) as pool:
+            parts = pool.map(_part, jobs)
     out = {k: sum(p[k] for p in parts) for k in ("count", "band_in", "band_out", "suminvr", "energy")}
     out["virial"] = sum(p["virial"] for p in parts)
     out["dedh"] = sum(p["dedh"] for p in parts)

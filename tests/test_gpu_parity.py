@@ -210,3 +210,33 @@ def test_update_matches_fresh_build(cuda_ok):
     P.cl_update(cl, pos2, h=h3)
     ref3 = oracle.pair_map(x2, h3, rc, band=BAND)
     check_count(int(P.cl_map(cl, "count")["count"].item()), ref3)
+
+
+@pytest.mark.slow
+def test_workload_clustered_16m(cuda_ok):
+    """3D clustered, 16M particles in a cubic box of side 600 (2,000 Gaussian
+    clusters + 20% background, minimum separation 0.5), rc 8: energy, forces
+    and virial (forward, full shell) and the backward kernel. Energy and virial
+    against the whole oracle (run in a process pool); forces on a sample of
+    particles computed one by one by the oracle."""
+    P = _P()
+    w = synth.w4_clustered()
+    x, h, rc = w["x"], w["h"], w["rc"]
+    n = x.shape[0]
+    ref = oracle_pool(x, h, rc, nbins=0, forces=False)
+    sample = np.sort(np.random.default_rng(44).choice(n, size=3000, replace=False))
+    f_ref, _ = oracle.particles(x, h, rc, sample)
+    pos = torch.from_numpy(x).cuda()
+    cl = P.cl_build(pos, h, rc, 1)
+    assert P.cl_query(cl, "max_occupancy") > 10 * n / P.cl_query(cl, "ncells")  # strongly inhomogeneous
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    efv = P.cl_map(cl, "energy_forces_virial")
+    check_energy(efv["energy"].item(), ref["energy"])
+    check_matrix(efv["virial"].cpu().numpy(), ref["virial"], TOL_W)
+    check_forces(efv["forces"][torch.from_numpy(sample).cuda()].cpu().numpy(), f_ref)
+    del efv
+    gp, gb, vir = P.cl_backward(cl, torch.ones(1, dtype=torch.float64, device="cuda"))
+    check_forces(gp[torch.from_numpy(sample).cuda()].cpu().numpy(), -f_ref)
+    check_matrix(vir.cpu().numpy(), ref["virial"], TOL_W)
+    check_matrix(gb.cpu().numpy(), ref["dedh"], TOL_GB)
