@@ -16,6 +16,7 @@ time is the maximum over ranks.
 """
 import argparse
 import json
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -46,6 +47,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
     return p.parse_args()
 
 
@@ -265,9 +267,90 @@ def run_ours(args, rank, world, local):
 
     if not args.no_e2e:
         line["e2e"] = e2e(P, cl, w, dev, stream, pairs, args, world)
+    if not args.no_serve:
+        line["serve"] = serve_leg(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     return line
+
+
+def serve_leg(dev):
+    """Serving stream (512 seeded requests, Poisson arrivals with 2 ms mean
+    gap, 2D/3D, 1e3..2e5 particles, ortho/triclinic, energy/forces/histogram)
+    through the continuous-batching server, against one-request-at-a-time
+    serving with the same kernels (a server admitting one request at a time)
+    and against plain per-request launches through the public API."""
+    import torch
+    import paper_2202_06427_gb300 as P
+    from paper_2202_06427_gb300 import serve as S
+    import synth
+    specs = synth.serve_stream()
+    reqs = [S.Request(synth.request_positions(s), s["h"], s["rc"], s["task"], lcell=2, nbins=s["nbins"])
+            for s in specs]
+    warm = [S.Request(synth.request_positions(s), s["h"], s["rc"], s["task"], lcell=2, nbins=s["nbins"])
+            for s in synth.serve_stream(n_requests=16, seed=7, n_max=20_000)]
+
+    def run(max_inflight, realtime):
+        srv = S.Server(arena_bytes=8 << 30, max_inflight=max_inflight, device=dev.index)
+        try:
+            for r in warm:
+                srv.submit(r)
+            for r in warm:
+                srv.wait(r.ticket, 120.0)
+            b0 = srv.stats()["batches"]
+            wall0 = time.perf_counter()
+            for spec, r in zip(specs, reqs):
+                if realtime:
+                    target = wall0 + spec["arrival_s"]
+                    while True:
+                        left = target - time.perf_counter()
+                        if left <= 0:
+                            break
+                        time.sleep(left - 2e-4 if left > 5e-4 else 0)
+                srv.submit(r)
+            status = [srv.wait(r.ticket, 300.0) for r in reqs]
+            times = np.array([srv.times(r.ticket) for r in reqs])
+            st = srv.stats()
+        finally:
+            srv.close()
+        lat = (times[:, 3] - times[:, 0]) * 1e3
+        span = times[:, 3].max() - times[:, 0].min()
+        return {"req_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "batches": st["batches"] - b0,
+                "largest_batch": st["largest_batch"], "failed": int(sum(1 for x in status if x != 0))}
+
+    def plain(k_max=None):
+        """one request at a time through cl_build + cl_map, H2D and D2H included"""
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for spec, r in zip(specs, reqs):
+            x = r.pos.to(dev, non_blocking=True)
+            cl = P.cl_build(x, spec["h"], spec["rc"], 2)
+            if spec["task"] == "energy":
+                r.energy.copy_(P.cl_map(cl, "energy")["energy"], non_blocking=True)
+            elif spec["task"] == "forces":
+                o = P.cl_map(cl, "energy_forces_virial")
+                r.energy.copy_(o["energy"], non_blocking=True)
+                r.forces.copy_(o["forces"], non_blocking=True)
+            else:
+                r.hist.copy_(P.cl_map(cl, "hist", nbins=spec["nbins"])["hist"], non_blocking=True)
+            torch.cuda.synchronize(dev)
+            P.cl_free(cl)
+        return {"req_per_s": len(reqs) / (time.perf_counter() - t0)}
+
+    out = {"workload": "w3_serve_stream: 512 requests, Poisson arrivals (mean gap 2 ms), 2D rho 0.7 rc 2.5 / "
+                       "3D rho 0.1 rc 12, N log-uniform 1e3..2e5, ortho/triclinic, energy/forces/100-bin hist",
+           "offered_req_per_s": len(specs) / max(s["arrival_s"] for s in specs),
+           "total_particles": int(sum(s["n"] for s in specs))}
+    sat = run(256, False)
+    poi = run(256, True)
+    one_sat = run(1, False)
+    one_poi = run(1, True)
+    out.update({"req_per_s": sat["req_per_s"], "p50_ms": poi["p50_ms"], "p99_ms": poi["p99_ms"],
+                "batched_saturation": sat, "batched_poisson": poi,
+                "one_at_a_time": {"saturation": one_sat, "poisson": one_poi},
+                "plain_api_one_at_a_time": plain()})
+    return out
 
 
 def e2e(P, cl, w, dev, stream, pairs, args, world):

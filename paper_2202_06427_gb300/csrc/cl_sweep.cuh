@@ -145,8 +145,10 @@ __device__ __forceinline__ void scan_range(const float4* __restrict__ xs, int j0
 
 // Visits every pair-image of sorted particle p (half or full shell) and
 // accumulates into acc. Returns false for threads past the end.
-template <int DIM, class R>
-__device__ __forceinline__ bool sweep_particle(const SweepArgs& A, const R& red, typename R::Acc& acc, int p,
+// ARGS: SweepArgs (stencil in the kernel parameters) or any struct with the
+// same fields (xs, cellc, cell_start, n, nx, ny, nz, rc2, noff, off[]).
+template <int DIM, class R, class ARGS>
+__device__ __forceinline__ bool sweep_particle(const ARGS& A, const R& red, typename R::Acc& acc, int p,
                                                float4& pi) {
   if (p >= A.n) return false;
   pi = A.xs[p];
