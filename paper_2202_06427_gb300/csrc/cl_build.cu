@@ -80,10 +80,10 @@ __global__ void __launch_bounds__(256) k_bin(const __grid_constant__ BinArgs a) 
     if (DIM == 3) o.z = fmaf(u[k], a.g[k * 3 + 2], o.z);
   }
   if (!finite) {
-    // park the particle in cell 0 with NaN coordinates: every distance test
-    // against it is false, and the host learns of it through the latch
+    // park the particle in cell 0 at its sentinel position: every distance
+    // test against it fails, and the host learns of it through the latch
     c[0] = c[1] = c[2] = 0;
-    o.x = o.y = o.z = __int_as_float(0x7fc00000);
+    o = sentinel_pos(i);
     atomicOr(a.err, kErrNonFinite);
   }
   o.w = __int_as_float(i);
@@ -213,6 +213,18 @@ __global__ void __launch_bounds__(256) k_scatter(int n, int nx, int ny, const un
   cellc[p] = cc;
 }
 
+// Shifted pairs for the packed sweep: element j holds particles j and j+1 of
+// the sorted order, so a range of any start and parity is read two at a time.
+__global__ void __launch_bounds__(256) k_pack_pairs(int n, const float4* __restrict__ xs, float4* __restrict__ xy2,
+                                                   float4* __restrict__ zn2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const float4 a = xs[j];
+  const float4 b = (j + 1 < n) ? xs[j + 1] : sentinel_pos(n);
+  xy2[j] = make_float4(a.x, b.x, a.y, b.y);
+  zn2[j] = make_float4(a.z, b.z, fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z)), fmaf(b.x, b.x, fmaf(b.y, b.y, b.z * b.z)));
+}
+
 // ------------------------------------------------------------ host entry --
 
 
@@ -246,12 +258,40 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
   k_scan_final<<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
   if (b.n > 0)
     k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.packed, b.slot, b.xl, b.cell_start, b.xs, b.cellc);
+  if (b.n > 0 && b.xy2 && b.zn2) k_pack_pairs<<<blocks, 256, 0, s>>>(b.n, b.xs, b.xy2, b.zn2);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
 }  // namespace clk
 
 namespace clk {
+
+// Work list of the warp sweep: every non-empty cell is cut into chunks of at
+// most 32 particles; chunk k is (cell, first particle). nch[c] = chunks of c.
+__global__ void __launch_bounds__(256) k_chunk_count(long long ncells, const int* __restrict__ counts,
+                                                    int* __restrict__ nch) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < ncells) nch[c] = (counts[c] + 31) >> 5;
+}
+
+__global__ void __launch_bounds__(256) k_chunk_fill(long long ncells, const int* __restrict__ nch,
+                                                   const int* __restrict__ chunk_start,
+                                                   const int* __restrict__ cell_start, int2* __restrict__ items) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= ncells) return;
+  const int k0 = chunk_start[c], first = cell_start[c];
+  for (int g = 0; g < nch[c]; ++g) items[k0 + g] = make_int2((int)c, first + 32 * g);
+}
+
+int launch_worklist(long long ncells, const int* counts, const int* cell_start, int* nch, int* chunk_start,
+                    int* tiles, int* meta, int2* items, cudaStream_t s) {
+  const int blocks = (int)((ncells + 255) / 256);
+  k_chunk_count<<<blocks, 256, 0, s>>>(ncells, counts, nch);
+  int e = launch_scan(nch, ncells, tiles, chunk_start, meta, s);
+  if (e) return e;
+  k_chunk_fill<<<blocks, 256, 0, s>>>(ncells, nch, chunk_start, cell_start, items);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
 
 // Exclusive scan of n int counts into start[n + 1] (start[n] = total), with
 // the same three kernels as the cell offsets; meta receives the number of

@@ -54,11 +54,26 @@ struct Geo {
 // Device-side error latch bits.
 constexpr int kErrNonFinite = 1;
 
+// Stand-in coordinates for a particle whose input position is not finite (and
+// for the element past the last one in the shifted-pair arrays): far outside
+// any box, unique per index and at least 1e12 apart from each other, finite,
+// so that every distance test against them fails without producing NaN.
+__device__ __forceinline__ float4 sentinel_pos(int i) {
+  const float big = 1e15f, step = 1.0f / 1024.0f;
+  return make_float4(big * (1.0f + (float)(i & 1023) * step), big * (1.0f + (float)((i >> 10) & 1023) * step),
+                     big * (1.0f + (float)((i >> 20) & 1023) * step), 0.0f);
+}
+
 // Launch arguments of the sweep kernels (passed as one __grid_constant__ parameter).
 struct SweepArgs {
   const float4* xs;
   const unsigned* cellc;
   const int* cell_start;
+  const float4* xy2;    // shifted pairs (x_j, x_j+1, y_j, y_j+1), 3D; null: unpaired sweep
+  const float4* zn2;    // (z_j, z_j+1, |x_j|^2, |x_j+1|^2)
+  const int2* items;    // chunk work list (cell, first particle); null: one thread per particle
+  const int* nitems;    // device: number of chunks
+  int max_items;        // upper bound on the number of chunks (grid size)
   int n;
   int nx, ny, nz;
   float rc2, irc, irc2;
@@ -88,10 +103,14 @@ struct BuildBufs {
   int* meta;  // [0] error latch, [1] non-empty cells, [2] max occupancy
   float4* xs;
   unsigned* cellc;
+  float4* xy2;  // optional (null: not built): shifted pairs of xs for the packed 3D sweep
+  float4* zn2;
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
 int launch_scan(const int* counts, long long n, int* tile_sum, int* start, int* meta, cudaStream_t s);
+int launch_worklist(long long ncells, const int* counts, const int* cell_start, int* nch, int* chunk_start,
+                    int* tiles, int* meta, int2* items, cudaStream_t s);
 
 // Sweeps and reductions (cl_sweep.cu).
 int sweep_partials_needed(int n);
