@@ -31,10 +31,13 @@ METRIC = "pairs-within-cutoff/sec at 1M particles"
 UNIT = "pairs/s"
 WORKLOAD = "w1_lattice_1m"
 LCELL = 2
-# FP32 arithmetic per pair test and per pair in the cutoff (FMA = 2 FLOP):
+# FP32 arithmetic per pair test and per pair in the cutoff (FMA = 2 FLOP, 1/r = 1):
 FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j + S - x_i|^2
-FLOP_PER_HIT_BACKWARD = 27  # Newton-refined 1/r (6), u'(r)/r (3), force (6), virial (12)
-FLOP_PER_HIT_ENERGY = 12    # Newton-refined 1/r (6), (1 - r/rc)^2 / r accumulated (6)
+FLOP_PER_HIT_BACKWARD = 22  # 1/r (1), u'(r)/r = y (1/rc^2 - y^2) (3), force 3 mul + 3 add, virial 6 fma (12)
+FLOP_PER_HIT_ENERGY = 7     # 1/r (1), r (1), 1 - r/rc (2), (..)^2 / r (2), accumulate (1)
+# DRAM bytes per launch of the backward sweep (k_sweep2_force<1>, 1M lattice, lcell 2), from
+# ncu --set full: dram__bytes_read.sum + dram__bytes_write.sum = 79.06 MB + 7.20 MB.
+BACKWARD_DRAM_BYTES = 86.25e6
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -250,7 +253,8 @@ def run_ours(args, rank, world, local):
     flop = 2 * cand_half * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_BACKWARD
     achieved = flop / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": None, "kernel": "k_sweep_force<3,1> (cl_backward)",
+                "frac": achieved / peak_tflops, "traffic": BACKWARD_DRAM_BYTES,
+                "kernel": "k_sweep2_force<1> (cl_backward: full-shell force and virial sweep)",
                 "kernel_ms": kms, "flop_per_launch": flop,
                 "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (of max clock, not measured)" % (sms, max_mhz)}
 
@@ -262,7 +266,7 @@ def run_ours(args, rank, world, local):
                        "step": "binning + energy sweep (forward) + force/virial sweep (backward)",
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "gpu_launches": 11 * args.steps,
+            "gpu_launches": 12 * args.steps,  # bin, 3 scan, scatter, pair pack; energy sweep + 2 reduce; backward + 2
             "clocks": clocks, "roofline": roofline}
 
     if not args.no_e2e:

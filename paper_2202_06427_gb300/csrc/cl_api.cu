@@ -26,14 +26,6 @@ struct cl_list {
   double* partials;
   double* sums;
   unsigned long long* u64;
-  // chunk work list of the warp sweep
-  int* wl_nch;
-  int* wl_start;
-  int* wl_tiles;
-  int* wl_meta;
-  int2* wl_items;
-  int wl_max;
-  int wl_on;
   // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
   int* pl_count;
   int* pl_start;
@@ -64,13 +56,9 @@ void free_cells(cl_list* c) {
   cudaFree(c->counts);
   cudaFree(c->cell_start);
   cudaFree(c->tile_sum);
-  cudaFree(c->wl_nch);
-  cudaFree(c->wl_start);
-  cudaFree(c->wl_tiles);
   c->counts = nullptr;
   c->cell_start = nullptr;
   c->tile_sum = nullptr;
-  c->wl_nch = c->wl_start = c->wl_tiles = nullptr;
 }
 
 void free_all(cl_list* c) {
@@ -83,8 +71,6 @@ void free_all(cl_list* c) {
   cudaFree(c->xy2);
   cudaFree(c->zn2);
   cudaFree(c->meta);
-  cudaFree(c->wl_meta);
-  cudaFree(c->wl_items);
   cudaFree(c->partials);
   cudaFree(c->sums);
   cudaFree(c->u64);
@@ -102,11 +88,6 @@ int alloc_cells(cl_list* c, long long ncells) {
   if ((e = dev_alloc(&c->counts, (size_t)ncells, &b))) return e;
   if ((e = dev_alloc(&c->cell_start, (size_t)ncells + 1, &b))) return e;
   if ((e = dev_alloc(&c->tile_sum, (size_t)clk::scan_tiles_for(ncells), &b))) return e;
-  if (c->wl_on) {
-    if ((e = dev_alloc(&c->wl_nch, (size_t)ncells, &b))) return e;
-    if ((e = dev_alloc(&c->wl_start, (size_t)ncells + 1, &b))) return e;
-    if ((e = dev_alloc(&c->wl_tiles, (size_t)clk::scan_tiles_for(ncells), &b))) return e;
-  }
   c->ncells_alloc = ncells;
   c->bytes += b;
   return CL_OK;
@@ -117,13 +98,6 @@ void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
   A->cellc = c->cellc;
   A->cell_start = c->cell_start;
   A->xy2 = c->geo.dim == 3 ? c->xy2 : nullptr;
-  const bool wl = c->wl_on && c->geo.dim == 3;
-  A->items = wl ? c->wl_items : nullptr;
-  A->nitems = wl ? c->wl_start + c->geo.ncells : nullptr;
-  {
-    long long bound = (long long)c->n / 32 + (c->geo.ncells < c->n ? c->geo.ncells : c->n) + 1;
-    A->max_items = (int)(bound < c->wl_max ? bound : c->wl_max);
-  }
   A->zn2 = c->geo.dim == 3 ? c->zn2 : nullptr;
   A->n = c->n;
   A->nx = c->geo.n[0];
@@ -180,11 +154,7 @@ int run_build(cl_list* c, cudaStream_t s) {
   b.cellc = c->cellc;
   b.xy2 = c->geo.dim == 3 ? c->xy2 : nullptr;
   b.zn2 = c->geo.dim == 3 ? c->zn2 : nullptr;
-  int e = clk::launch_build(c->geo, b, s);
-  if (!e && c->wl_on && c->geo.dim == 3)
-    e = clk::launch_worklist(c->geo.ncells, c->counts, c->cell_start, c->wl_nch, c->wl_start, c->wl_tiles,
-                             c->wl_meta, c->wl_items, s);
-  return e;
+  return clk::launch_build(c->geo, b, s);
 }
 
 // Neighbour list: count pass, scan, one synchronisation to learn the total,
@@ -286,10 +256,6 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   c->n = (int)n;
   c->pos = pos_dev;
   c->ncells_alloc = -1;
-  {
-    const char* v = getenv("CELLMAP_SWEEP");  // experiment switch between the two 3D sweep mappings
-    c->wl_on = (box->dim == 3 && v && v[0] == 'c') ? 1 : 0;
-  }
   int e = CL_OK;
   size_t b = 0;
   const size_t nn = (size_t)n;
@@ -301,9 +267,6 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e && box->dim == 3) e = dev_alloc(&c->xy2, nn, &b);
   if (!e && box->dim == 3) e = dev_alloc(&c->zn2, nn, &b);
   if (!e) e = dev_alloc(&c->meta, 4, &b);
-  if (!e && c->wl_on) e = dev_alloc(&c->wl_meta, 4, &b);
-  c->wl_max = (int)(nn / 32 + nn + 1);
-  if (!e && c->wl_on) e = dev_alloc(&c->wl_items, (size_t)c->wl_max, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
   if (!e) e = dev_alloc(&c->u64, 8, &b);

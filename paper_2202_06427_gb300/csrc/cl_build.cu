@@ -266,33 +266,6 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
 
 namespace clk {
 
-// Work list of the warp sweep: every non-empty cell is cut into chunks of at
-// most 32 particles; chunk k is (cell, first particle). nch[c] = chunks of c.
-__global__ void __launch_bounds__(256) k_chunk_count(long long ncells, const int* __restrict__ counts,
-                                                    int* __restrict__ nch) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c < ncells) nch[c] = (counts[c] + 31) >> 5;
-}
-
-__global__ void __launch_bounds__(256) k_chunk_fill(long long ncells, const int* __restrict__ nch,
-                                                   const int* __restrict__ chunk_start,
-                                                   const int* __restrict__ cell_start, int2* __restrict__ items) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= ncells) return;
-  const int k0 = chunk_start[c], first = cell_start[c];
-  for (int g = 0; g < nch[c]; ++g) items[k0 + g] = make_int2((int)c, first + 32 * g);
-}
-
-int launch_worklist(long long ncells, const int* counts, const int* cell_start, int* nch, int* chunk_start,
-                    int* tiles, int* meta, int2* items, cudaStream_t s) {
-  const int blocks = (int)((ncells + 255) / 256);
-  k_chunk_count<<<blocks, 256, 0, s>>>(ncells, counts, nch);
-  int e = launch_scan(nch, ncells, tiles, chunk_start, meta, s);
-  if (e) return e;
-  k_chunk_fill<<<blocks, 256, 0, s>>>(ncells, nch, chunk_start, cell_start, items);
-  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
-}
-
 // Exclusive scan of n int counts into start[n + 1] (start[n] = total), with
 // the same three kernels as the cell offsets; meta receives the number of
 // non-zero counts and the largest one.

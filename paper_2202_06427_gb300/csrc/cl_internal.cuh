@@ -71,9 +71,6 @@ struct SweepArgs {
   const int* cell_start;
   const float4* xy2;    // shifted pairs (x_j, x_j+1, y_j, y_j+1), 3D; null: unpaired sweep
   const float4* zn2;    // (z_j, z_j+1, |x_j|^2, |x_j+1|^2)
-  const int2* items;    // chunk work list (cell, first particle); null: one thread per particle
-  const int* nitems;    // device: number of chunks
-  int max_items;        // upper bound on the number of chunks (grid size)
   int n;
   int nx, ny, nz;
   float rc2, irc, irc2;
@@ -109,8 +106,6 @@ struct BuildBufs {
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
 int launch_scan(const int* counts, long long n, int* tile_sum, int* start, int* meta, cudaStream_t s);
-int launch_worklist(long long ncells, const int* counts, const int* cell_start, int* nch, int* chunk_start,
-                    int* tiles, int* meta, int2* items, cudaStream_t s);
 
 // Sweeps and reductions (cl_sweep.cu).
 int sweep_partials_needed(int n);

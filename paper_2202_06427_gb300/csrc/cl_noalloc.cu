@@ -133,9 +133,6 @@ extern "C" int cl_energy_noalloc(const double* pos_dev, long long n, const cl_bo
   A.xs = b.xs;
   A.xy2 = nullptr;
   A.zn2 = nullptr;
-  A.items = nullptr;
-  A.nitems = nullptr;
-  A.max_items = 0;
   A.cellc = b.cellc;
   A.cell_start = b.cell_start;
   A.n = (int)n;

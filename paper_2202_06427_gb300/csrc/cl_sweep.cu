@@ -190,95 +190,23 @@ __global__ void __launch_bounds__(256) k_sweep2_force(const __grid_constant__ Sw
   block_sum_store<NV>(v, partials + (size_t)blockIdx.x * NV);
 }
 
-// Warp-per-chunk variants (A.items): warp w sweeps chunk w.
-__device__ __forceinline__ bool chunk_of_warp(const SweepArgs& A, int& cell, int& p, int& end) {
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= *A.nitems) return false;
-  const int2 it = A.items[w];
-  cell = it.x;
-  end = A.cell_start[cell + 1];
-  p = it.y + (threadIdx.x & 31);
-  return true;
-}
-
-__global__ void __launch_bounds__(256) k_sweep3_energy(const __grid_constant__ SweepArgs A, double* partials) {
-  Red2Energy red;
-  red.irc = A.irc;
-  Red2Energy::Acc acc;
-  red.init(acc);
-  int cell, p, end;
-  float4 pi;
-  if (chunk_of_warp(A, cell, p, end)) sweep_chunk2(A, red, acc, cell, p, end, pi);
-  double v[1] = {(double)acc.e.x + (double)acc.e.y};
-  block_sum_store<1>(v, partials + blockIdx.x);
-}
-
-template <int MODE>
-__global__ void __launch_bounds__(256) k_sweep3_force(const __grid_constant__ SweepArgs A, float* __restrict__ forces,
-                                                      double* __restrict__ grad, const double* __restrict__ gE,
-                                                      const double* __restrict__ pos, double* __restrict__ partials) {
-  Red2Force<MODE == 0> red;
-  red.irc = A.irc;
-  red.irc2 = A.irc2;
-  typename Red2Force<MODE == 0>::Acc acc;
-  red.init(acc);
-  float4 pi;
-  int cell, p, end;
-  bool live = false;
-  if (chunk_of_warp(A, cell, p, end)) live = sweep_chunk2(A, red, acc, cell, p, end, pi);
-  const float F[3] = {-(acc.gx.x + acc.gx.y), -(acc.gy.x + acc.gy.y), -(acc.gz.x + acc.gz.y)};
-  constexpr int NV = (MODE == 0) ? 1 + kVirN3 : kVirN3 + 9;
-  double v[NV];
-  v[0] = -((double)acc.vxx.x + (double)acc.vxx.y);
-  v[1] = -((double)acc.vxy.x + (double)acc.vxy.y);
-  v[2] = -((double)acc.vxz.x + (double)acc.vxz.y);
-  v[3] = -((double)acc.vyy.x + (double)acc.vyy.y);
-  v[4] = -((double)acc.vyz.x + (double)acc.vyz.y);
-  v[5] = -((double)acc.vzz.x + (double)acc.vzz.y);
-  if (MODE == 0) {
-    v[kVirN3] = 0.5 * ((double)acc.e.x + (double)acc.e.y);
-    if (live) {
-      const int i = __float_as_int(A.xs[p].w);
-#pragma unroll
-      for (int a = 0; a < 3; ++a) forces[(size_t)i * 3 + a] = F[a];
-    }
-  } else {
-#pragma unroll
-    for (int k = kVirN3; k < NV; ++k) v[k] = 0.0;
-    if (live) {
-      const int i = __float_as_int(A.xs[p].w);
-      const double g = *gE;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = -g * (double)F[a];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        const double xa = pos[(size_t)i * 3 + a];
-#pragma unroll
-        for (int b = 0; b < 3; ++b) v[kVirN3 + a * 3 + b] = xa * (double)F[b];
-      }
-    }
-  }
-  block_sum_store<NV>(v, partials + (size_t)blockIdx.x * NV);
-}
-
 // ----------------------------------------------------------- final reduce
 
-// Sums partials[nblocks][nv] in a fixed order into sums[nv] (one CTA).
+// Sums partials[nblocks][nv] in a fixed order into sums[nv]: CTA k sums
+// component k (strided per thread, then a fixed tree).
 __global__ void __launch_bounds__(256) k_final_sum(const double* __restrict__ partials, int nblocks, int nv,
                                                    double* __restrict__ sums) {
   __shared__ double sm[256];
-  for (int k = 0; k < nv; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * nv + k];
-    sm[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) sums[k] = sm[0];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * nv + k];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
     __syncthreads();
   }
+  if (threadIdx.x == 0) sums[k] = sm[0];
 }
 
 struct FinalArgs {
@@ -360,9 +288,7 @@ __global__ void __launch_bounds__(256) k_candidates(const __grid_constant__ Swee
 
 static int blocks_for(int n) { return n > 0 ? (n + 255) / 256 : 1; }
 
-// partials: one row per CTA of the particle sweeps, or of the chunk sweeps
-// (at most n/32 + n chunks, 8 per CTA)
-int sweep_partials_needed(int n) { return (blocks_for(n) + (n + 7) / 8 + 1) * 16; }
+int sweep_partials_needed(int n) { return blocks_for(n) * 16; }
 
 int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStream_t s) {
   if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
@@ -375,14 +301,11 @@ int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStrea
 
 int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, double* sums, double* out,
                   cudaStream_t s) {
-  int nb = blocks_for(A.n);
+  const int nb = blocks_for(A.n);
   if (A.n > 0) {
     if (dim == 3) {
       if (kind == 0) k_sweep_scalar<3, 0><<<nb, 256, 0, s>>>(A, partials);
-      else if (A.xy2 && A.zn2 && A.items) {
-        nb = (A.max_items + 7) / 8;
-        k_sweep3_energy<<<nb, 256, 0, s>>>(A, partials);
-      } else if (A.xy2 && A.zn2) k_sweep2_energy<<<nb, 256, 0, s>>>(A, partials);
+      else if (A.xy2 && A.zn2) k_sweep2_energy<<<nb, 256, 0, s>>>(A, partials);
       else k_sweep_scalar<3, 1><<<nb, 256, 0, s>>>(A, partials);
     } else {
       if (kind == 0) k_sweep_scalar<2, 0><<<nb, 256, 0, s>>>(A, partials);
@@ -415,15 +338,11 @@ int launch_hist(const SweepArgs& A, int dim, int nbins, float rmax, unsigned lon
 int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, float* forces, double* grad,
                  const double* gE, const double* pos, double* partials, double* sums, double* energy,
                  double* virial, double* gradbox, cudaStream_t s) {
-  int nb = blocks_for(A.n);
+  const int nb = blocks_for(A.n);
   const int NW = dim == 3 ? kVirN3 : kVirN2;
   const int NV = mode == 0 ? 1 + NW : NW + dim * dim;
   if (A.n > 0) {
-    if (dim == 3 && A.xy2 && A.zn2 && A.items) {
-      nb = (A.max_items + 7) / 8;
-      if (mode == 0) k_sweep3_force<0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
-      else k_sweep3_force<1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
-    } else if (dim == 3 && A.xy2 && A.zn2) {
+    if (dim == 3 && A.xy2 && A.zn2) {
       if (mode == 0) k_sweep2_force<0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
       else k_sweep2_force<1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
     } else if (dim == 3) {
@@ -436,7 +355,7 @@ int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, floa
   } else {
     if (cudaMemsetAsync(partials, 0, sizeof(double) * NV, s) != cudaSuccess) return CL_ERR_CUDA;
   }
-  k_final_sum<<<1, 256, 0, s>>>(partials, A.n > 0 ? nb : 1, NV, sums);
+  k_final_sum<<<NV, 256, 0, s>>>(partials, A.n > 0 ? nb : 1, NV, sums);
   FinalArgs F;
   memset(&F, 0, sizeof(F));
   F.mode = mode == 0 ? 2 : 3;

@@ -301,30 +301,4 @@ __device__ __forceinline__ bool sweep_particle2(const SweepArgs& A, const R& red
   return true;
 }
 
-// Chunk of up to 32 particles of one cell, swept by one warp: every lane walks
-// the same neighbour cells with the same trip counts (no divergence between
-// cells inside the warp), and all lanes read the same neighbour particle at
-// each step. The chunk list is built by k_chunk_* from the cell offsets.
-template <class R>
-__device__ __forceinline__ bool sweep_chunk2(const SweepArgs& A, const R& red, typename R::Acc& acc, int cell,
-                                             int p, int cell_end, float4& pi) {
-  const bool live = p < cell_end;
-  const int pp = live ? p : cell_end - 1;
-  pi = A.xs[pp];
-  const int cx = cell % A.nx, cy = (cell / A.nx) % A.ny, cz = cell / (A.nx * A.ny);
-  const int s0 = A.cell_start[cell];
-  if (live) {
-    if (R::kFull) scan_pairs(A.xy2, A.zn2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
-    scan_pairs(A.xy2, A.zn2, p + 1, cell_end, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
-  }
-  if (!live) pi.x = pi.y = pi.z = __int_as_float(0x7f800000);  // +inf: no pair with anything
-  for (int k = 1; k < A.noff; ++k) {
-    const int c = stencil_cell(A, k, cx, cy, cz);
-    const Off& o = A.off[k];
-    scan_pairs(A.xy2, A.zn2, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
-               red, acc);
-  }
-  return live;
-}
-
 }  // namespace clk
