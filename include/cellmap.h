@@ -153,7 +153,7 @@ int cl_backward(const cl_list* cl, const double* grad_energy_dev, double* grad_p
 #define CL_INFO_STENCIL_HALF 9      /* neighbour-cell offsets visited per cell by the half-shell sweep */
 #define CL_INFO_STENCIL_FULL 10     /* offsets of the full stencil (forces, backward) */
 #define CL_INFO_CANDIDATES 11       /* candidate pairs the half-shell sweep tests (cell occupancy products) */
-#define CL_INFO_WORK_TILES 12       /* tiles in the sweep's work list */
+#define CL_INFO_WORK_TILES 12       /* CTAs of 256 threads the particle sweeps launch (one thread per particle) */
 int cl_query(const cl_list* cl, int what, long long* value, void* stream);
 
 /* Host-only box preparation, no GPU needed: for box, fills
@@ -195,6 +195,38 @@ void cl_free(cl_list* cl);
 
 /* Static description of an error code. */
 const char* cl_error_string(int code);
+
+/* One neighbour-cell offset o of the stencil: its periodic cell step
+ * (o_k mod n_k, in [0, n_k)) and the Cartesian shift S_o = sum_k (o_k/n_k) H_k
+ * between the centres of a cell and of its neighbour o, unwrapped. */
+typedef struct {
+  int dx, dy, dz;
+  float sx, sy, sz;
+} cl_offset;
+
+/* Read-only device view of a built cell list, for sweeps compiled outside the
+ * library (cellmap_functor.cuh). Cell-sorted particles xs[n] hold FP32
+ * coordinates relative to the centre of their cell and, in w, the original
+ * index (int bits); cellc[n] = cx | cy << 10 | cz << 20; cell_start[ncells+1]
+ * are the cell offsets (cells x-fastest). off_half[0] / off_full[0] is the
+ * own cell; the half stencil holds the lexicographically positive offsets,
+ * the full stencil all of them. All pointers are device memory owned by the
+ * handle, valid until the next cl_update or cl_free. */
+typedef struct {
+  int dim;
+  int n;
+  int nx, ny, nz;
+  float cutoff;
+  const void* xs;          /* float4[n] */
+  const unsigned* cellc;
+  const int* cell_start;
+  const cl_offset* off_half;
+  int noff_half;
+  const cl_offset* off_full;
+  int noff_full;
+} cl_view;
+
+int cl_get_view(const cl_list* cl, cl_view* view);
 
 #ifdef __cplusplus
 }

@@ -31,6 +31,9 @@ struct cl_list {
   int* pl_start;
   int* pl_tiles;
   int* pl_meta;
+  // device copies of the stencils (for sweeps compiled outside the library)
+  clk::Off* d_off_half;
+  clk::Off* d_off_full;
   // stencils (host copies of the sweep arguments)
   clk::SweepArgs* half;
   clk::SweepArgs* full;
@@ -74,6 +77,8 @@ void free_all(cl_list* c) {
   cudaFree(c->partials);
   cudaFree(c->sums);
   cudaFree(c->u64);
+  cudaFree(c->d_off_half);
+  cudaFree(c->d_off_full);
   cudaFree(c->pl_count);
   cudaFree(c->pl_start);
   cudaFree(c->pl_tiles);
@@ -130,6 +135,11 @@ int set_geometry(cl_list* c, const cl_box* box) {
   }
   std::memcpy(c->half->off, th, sizeof(clk::Off) * nh);
   std::memcpy(c->full->off, tf, sizeof(clk::Off) * nf);
+  if (cudaMemcpy(c->d_off_half, th, sizeof(clk::Off) * nh, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(c->d_off_full, tf, sizeof(clk::Off) * nf, cudaMemcpyHostToDevice) != cudaSuccess) {
+    delete[] th;
+    return CL_ERR_CUDA;
+  }
   c->half->noff = nh;
   c->full->noff = nf;
   delete[] th;
@@ -270,6 +280,8 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
   if (!e) e = dev_alloc(&c->u64, 8, &b);
+  if (!e) e = dev_alloc(&c->d_off_half, (size_t)clk::kMaxOff, &b);
+  if (!e) e = dev_alloc(&c->d_off_full, (size_t)clk::kMaxOff, &b);
   c->bytes = b;
   if (!e) e = set_geometry(c, box);
   cudaStream_t s = (cudaStream_t)stream;
@@ -366,6 +378,25 @@ int cl_query(const cl_list* c, int what, long long* value, void* stream) {
     }
     default: return CL_ERR_INVALID_ARG;
   }
+}
+
+int cl_get_view(const cl_list* c, cl_view* v) {
+  if (!c || !v) return CL_ERR_INVALID_ARG;
+  static_assert(sizeof(cl_offset) == sizeof(clk::Off), "public and internal stencil entries differ");
+  v->dim = c->geo.dim;
+  v->n = c->n;
+  v->nx = c->geo.n[0];
+  v->ny = c->geo.n[1];
+  v->nz = c->geo.n[2];
+  v->cutoff = (float)c->geo.rc;
+  v->xs = c->xs;
+  v->cellc = c->cellc;
+  v->cell_start = c->cell_start;
+  v->off_half = reinterpret_cast<const cl_offset*>(c->d_off_half);
+  v->noff_half = c->half->noff;
+  v->off_full = reinterpret_cast<const cl_offset*>(c->d_off_full);
+  v->noff_full = c->full->noff;
+  return CL_OK;
 }
 
 int cl_status(cl_list* c, void* stream) {
