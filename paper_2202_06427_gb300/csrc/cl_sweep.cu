@@ -154,16 +154,14 @@ __global__ void __launch_bounds__(256) k_sweep2_force(const __grid_constant__ Sw
   float4 pi;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   const bool live = sweep_particle2(A, red, acc, p, pi);
-  const float F[3] = {-(acc.gx.x + acc.gx.y), -(acc.gy.x + acc.gy.y), -(acc.gz.x + acc.gz.y)};
+  const float F[3] = {-acc.tx, -acc.ty, -acc.tz};
   constexpr int NV = (MODE == 0) ? 1 + kVirN3 : kVirN3 + 9;
   double v[NV];
-  // the symmetric accumulator of the scalar kernels is sum fs r(x)r = -V
-  v[0] = -((double)acc.vxx.x + (double)acc.vxx.y);
-  v[1] = -((double)acc.vxy.x + (double)acc.vxy.y);
-  v[2] = -((double)acc.vxz.x + (double)acc.vxz.y);
-  v[3] = -((double)acc.vyy.x + (double)acc.vyy.y);
-  v[4] = -((double)acc.vyz.x + (double)acc.vyz.y);
-  v[5] = -((double)acc.vzz.x + (double)acc.vzz.y);
+  // the symmetric accumulator of the scalar kernels is sum fs r(x)r = -(sum fsn r(x)r)
+  float v6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (live) red.virial(acc, pi.x, pi.y, pi.z, v6);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) v[k] = -(double)v6[k];
   if (MODE == 0) {
     v[kVirN3] = 0.5 * ((double)acc.e.x + (double)acc.e.y);
     if (live) {

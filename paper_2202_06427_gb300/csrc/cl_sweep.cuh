@@ -207,32 +207,40 @@ struct Red2Energy {
   }
 };
 
-// Forces and virial (optionally energy), full shell. Accumulates with the
-// opposite sign, fsn = -u'(r)/r = y^3 - y/rc^2: G = sum fsn r = -F_i and
-// V = sum fsn r (x) r.
+// Forces and virial (optionally energy), full shell, with the opposite sign:
+// fsn = -u'(r)/r = y^3 - y/rc^2 and Gn = sum fsn r = -F_i. The virial needs no
+// per-pair work: writing r = x_j + S_o - x_i (cell-local coordinates, S_o the
+// shift of neighbour cell o) and pairing each ordered pair-image (i, j, o) with
+// its reverse (j, i, -o), whose r is -r,
+//   sum over ordered pairs of fsn r (x) r
+//     = sum_i [ sum_o S_o (x) Gn_i(o)  -  2 x_i (x) Gn_i ],
+// where Gn_i(o) is the part of Gn_i from neighbour cell o. So the sweep keeps a
+// per-cell partial force (packed, two lanes) and folds S_o (x) Gn_i(o) into a
+// 3x3 accumulator once per cell visit.
 template <bool ENERGY>
 struct Red2Force {
   static constexpr bool kFull = true;
   float irc, irc2;
-  struct Acc { float2 gx, gy, gz, vxx, vxy, vxz, vyy, vyz, vzz, e; };
+  struct Acc {
+    float2 gx, gy, gz;  // partial Gn of the current neighbour cell
+    float tx, ty, tz;   // Gn so far
+    float m[9];         // sum_o S_o (x) Gn(o)
+    float2 e;
+  };
   __device__ void init(Acc& a) const {
-    a.gx = a.gy = a.gz = a.vxx = a.vxy = a.vxz = a.vyy = a.vyz = a.vzz = a.e = f2(0.f);
+    a.gx = a.gy = a.gz = a.e = f2(0.f);
+    a.tx = a.ty = a.tz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a.m[k] = 0.f;
   }
   __device__ void hit2(Acc& a, float2 dx, float2 dy, float2 dz, float2 d2, bool h0, bool h1) const {
     const float2 y = rsqrt2(d2);
     float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
     fsn.x = h0 ? fsn.x : 0.f;
     fsn.y = h1 ? fsn.y : 0.f;
-    const float2 ax = __fmul2_rn(fsn, dx), ay = __fmul2_rn(fsn, dy), az = __fmul2_rn(fsn, dz);
-    a.gx = __fadd2_rn(a.gx, ax);
-    a.gy = __fadd2_rn(a.gy, ay);
-    a.gz = __fadd2_rn(a.gz, az);
-    a.vxx = __ffma2_rn(ax, dx, a.vxx);
-    a.vxy = __ffma2_rn(ax, dy, a.vxy);
-    a.vxz = __ffma2_rn(ax, dz, a.vxz);
-    a.vyy = __ffma2_rn(ay, dy, a.vyy);
-    a.vyz = __ffma2_rn(ay, dz, a.vyz);
-    a.vzz = __ffma2_rn(az, dz, a.vzz);
+    a.gx = __ffma2_rn(fsn, dx, a.gx);
+    a.gy = __ffma2_rn(fsn, dy, a.gy);
+    a.gz = __ffma2_rn(fsn, dz, a.gz);
     if (ENERGY) {
       const float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-irc), f2(1.0f));
       float2 u = __fmul2_rn(__fmul2_rn(t, t), y);
@@ -241,7 +249,45 @@ struct Red2Force {
       a.e = __fadd2_rn(a.e, u);
     }
   }
+  // end of one neighbour cell with shift (sx, sy, sz)
+  __device__ void cell_done(Acc& a, float sx, float sy, float sz) const {
+    const float gx = a.gx.x + a.gx.y, gy = a.gy.x + a.gy.y, gz = a.gz.x + a.gz.y;
+    a.m[0] = fmaf(sx, gx, a.m[0]);
+    a.m[1] = fmaf(sx, gy, a.m[1]);
+    a.m[2] = fmaf(sx, gz, a.m[2]);
+    a.m[3] = fmaf(sy, gx, a.m[3]);
+    a.m[4] = fmaf(sy, gy, a.m[4]);
+    a.m[5] = fmaf(sy, gz, a.m[5]);
+    a.m[6] = fmaf(sz, gx, a.m[6]);
+    a.m[7] = fmaf(sz, gy, a.m[7]);
+    a.m[8] = fmaf(sz, gz, a.m[8]);
+    a.tx += gx;
+    a.ty += gy;
+    a.tz += gz;
+    a.gx = a.gy = a.gz = f2(0.f);
+  }
+  // per-particle share of sum fsn r (x) r, symmetrised: xx, xy, xz, yy, yz, zz
+  __device__ void virial(const Acc& a, float px, float py, float pz, float* v6) const {
+    const float M[9] = {fmaf(-2.f * px, a.tx, a.m[0]), fmaf(-2.f * px, a.ty, a.m[1]), fmaf(-2.f * px, a.tz, a.m[2]),
+                        fmaf(-2.f * py, a.tx, a.m[3]), fmaf(-2.f * py, a.ty, a.m[4]), fmaf(-2.f * py, a.tz, a.m[5]),
+                        fmaf(-2.f * pz, a.tx, a.m[6]), fmaf(-2.f * pz, a.ty, a.m[7]), fmaf(-2.f * pz, a.tz, a.m[8])};
+    v6[0] = M[0];
+    v6[1] = 0.5f * (M[1] + M[3]);
+    v6[2] = 0.5f * (M[2] + M[6]);
+    v6[3] = M[4];
+    v6[4] = 0.5f * (M[5] + M[7]);
+    v6[5] = M[8];
+  }
 };
+
+// Reductions without per-cell work.
+template <class R, class Acc>
+__device__ __forceinline__ void cell_done_of(const R&, Acc&, float, float, float) {}
+template <bool E>
+__device__ __forceinline__ void cell_done_of(const Red2Force<E>& r, typename Red2Force<E>::Acc& a, float sx, float sy,
+                                             float sz) {
+  r.cell_done(a, sx, sy, sz);
+}
 
 // Candidates j in [j0, j1) against one particle, two at a time. (sx, sy, sz)
 // = S_o - x_i, so that the displacement is x_j + S_o - x_i = x_j + s.
@@ -291,12 +337,14 @@ __device__ __forceinline__ bool sweep_particle2(const SweepArgs& A, const R& red
     const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
     if (R::kFull) scan_pairs(A.xy2, A.zn2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
     scan_pairs(A.xy2, A.zn2, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    cell_done_of(red, acc, 0.f, 0.f, 0.f);
   }
   for (int k = 1; k < A.noff; ++k) {
     const int c = stencil_cell(A, k, cx, cy, cz);
     const Off& o = A.off[k];
     scan_pairs(A.xy2, A.zn2, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
                red, acc);
+    cell_done_of(red, acc, o.sx, o.sy, o.sz);
   }
   return true;
 }
