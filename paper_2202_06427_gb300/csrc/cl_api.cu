@@ -18,7 +18,7 @@ struct cl_list {
   float4* xs;
   unsigned* cellc;
   float4* xy2;  // shifted pairs for the packed 3D sweeps
-  float4* zn2;
+  float2* zz2;
   int* counts;
   int* cell_start;
   int* tile_sum;
@@ -72,7 +72,7 @@ void free_all(cl_list* c) {
   cudaFree(c->xs);
   cudaFree(c->cellc);
   cudaFree(c->xy2);
-  cudaFree(c->zn2);
+  cudaFree(c->zz2);
   cudaFree(c->meta);
   cudaFree(c->partials);
   cudaFree(c->sums);
@@ -103,7 +103,7 @@ void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
   A->cellc = c->cellc;
   A->cell_start = c->cell_start;
   A->xy2 = c->geo.dim == 3 ? c->xy2 : nullptr;
-  A->zn2 = c->geo.dim == 3 ? c->zn2 : nullptr;
+  A->zz2 = c->geo.dim == 3 ? c->zz2 : nullptr;
   A->n = c->n;
   A->nx = c->geo.n[0];
   A->ny = c->geo.n[1];
@@ -163,7 +163,7 @@ int run_build(cl_list* c, cudaStream_t s) {
   b.xs = c->xs;
   b.cellc = c->cellc;
   b.xy2 = c->geo.dim == 3 ? c->xy2 : nullptr;
-  b.zn2 = c->geo.dim == 3 ? c->zn2 : nullptr;
+  b.zz2 = c->geo.dim == 3 ? c->zz2 : nullptr;
   return clk::launch_build(c->geo, b, s);
 }
 
@@ -275,7 +275,7 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->xs, nn, &b);
   if (!e) e = dev_alloc(&c->cellc, nn, &b);
   if (!e && box->dim == 3) e = dev_alloc(&c->xy2, nn, &b);
-  if (!e && box->dim == 3) e = dev_alloc(&c->zn2, nn, &b);
+  if (!e && box->dim == 3) e = dev_alloc(&c->zz2, nn, &b);
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);

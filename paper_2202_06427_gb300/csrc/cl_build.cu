@@ -216,13 +216,13 @@ __global__ void __launch_bounds__(256) k_scatter(int n, int nx, int ny, const un
 // Shifted pairs for the packed sweep: element j holds particles j and j+1 of
 // the sorted order, so a range of any start and parity is read two at a time.
 __global__ void __launch_bounds__(256) k_pack_pairs(int n, const float4* __restrict__ xs, float4* __restrict__ xy2,
-                                                   float4* __restrict__ zn2) {
+                                                   float2* __restrict__ zz2) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const float4 a = xs[j];
   const float4 b = (j + 1 < n) ? xs[j + 1] : sentinel_pos(n);
   xy2[j] = make_float4(a.x, b.x, a.y, b.y);
-  zn2[j] = make_float4(a.z, b.z, fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z)), fmaf(b.x, b.x, fmaf(b.y, b.y, b.z * b.z)));
+  zz2[j] = make_float2(a.z, b.z);
 }
 
 // ------------------------------------------------------------ host entry --
@@ -258,7 +258,7 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
   k_scan_final<<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
   if (b.n > 0)
     k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.packed, b.slot, b.xl, b.cell_start, b.xs, b.cellc);
-  if (b.n > 0 && b.xy2 && b.zn2) k_pack_pairs<<<blocks, 256, 0, s>>>(b.n, b.xs, b.xy2, b.zn2);
+  if (b.n > 0 && b.xy2 && b.zz2) k_pack_pairs<<<blocks, 256, 0, s>>>(b.n, b.xs, b.xy2, b.zz2);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 

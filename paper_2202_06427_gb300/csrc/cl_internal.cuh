@@ -70,7 +70,7 @@ struct SweepArgs {
   const unsigned* cellc;
   const int* cell_start;
   const float4* xy2;    // shifted pairs (x_j, x_j+1, y_j, y_j+1), 3D; null: unpaired sweep
-  const float4* zn2;    // (z_j, z_j+1, |x_j|^2, |x_j+1|^2)
+  const float2* zz2;    // (z_j, z_j+1)
   int n;
   int nx, ny, nz;
   float rc2, irc, irc2;
@@ -101,7 +101,7 @@ struct BuildBufs {
   float4* xs;
   unsigned* cellc;
   float4* xy2;  // optional (null: not built): shifted pairs of xs for the packed 3D sweep
-  float4* zn2;
+  float2* zz2;
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);

@@ -127,12 +127,12 @@ extern "C" int cl_energy_noalloc(const double* pos_dev, long long n, const cl_bo
   b.tile_sum = reinterpret_cast<int*>(base + kOffTiles);
   b.meta = reinterpret_cast<int*>(base + kOffMeta);
   b.xy2 = nullptr;  // unpaired sweep: no room for the shifted pairs in the fixed workspace
-  b.zn2 = nullptr;
+  b.zz2 = nullptr;
   if (cudaMemsetAsync(b.meta, 0, 4 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if ((e = clk::launch_build(g, b, s))) return e;
   A.xs = b.xs;
   A.xy2 = nullptr;
-  A.zn2 = nullptr;
+  A.zz2 = nullptr;
   A.cellc = b.cellc;
   A.cell_start = b.cell_start;
   A.n = (int)n;

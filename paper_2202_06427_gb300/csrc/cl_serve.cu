@@ -338,7 +338,7 @@ bool cl_server::admit_one(Req* q) {
   B.tile_sum = reinterpret_cast<int*>(take((size_t)clk::scan_tiles_for((long long)C) * 4 + 4));
   B.meta = reinterpret_cast<int*>(take(16));
   B.xy2 = nullptr;  // the batched sweep reads the unpaired layout
-  B.zn2 = nullptr;
+  B.zz2 = nullptr;
   q->d_off = reinterpret_cast<clk::Off*>(take(q->off.size() * sizeof(clk::Off)));
   q->nitems = n > 0 ? (int)((n + clk::kServeThreads - 1) / clk::kServeThreads) : 0;
   q->d_partials = reinterpret_cast<double*>(take((size_t)std::max(q->nitems, 1) * 7 * 8));
