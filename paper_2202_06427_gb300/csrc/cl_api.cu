@@ -25,6 +25,7 @@ struct cl_list {
   int* meta;
   double* partials;
   double* sums;
+  int* work;  // work counter of the persistent neighbourhood sweep
   unsigned long long* u64;
   // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
   int* pl_count;
@@ -37,6 +38,7 @@ struct cl_list {
   // stencils (host copies of the sweep arguments)
   clk::SweepArgs* half;
   clk::SweepArgs* full;
+  clk::HoodArgs* hood;  // 3D neighbourhood sweep arguments
   size_t bytes;
 };
 
@@ -76,6 +78,7 @@ void free_all(cl_list* c) {
   cudaFree(c->meta);
   cudaFree(c->partials);
   cudaFree(c->sums);
+  cudaFree(c->work);
   cudaFree(c->u64);
   cudaFree(c->d_off_half);
   cudaFree(c->d_off_full);
@@ -85,6 +88,7 @@ void free_all(cl_list* c) {
   cudaFree(c->pl_meta);
   delete c->half;
   delete c->full;
+  delete c->hood;
 }
 
 int alloc_cells(cl_list* c, long long ncells) {
@@ -97,6 +101,9 @@ int alloc_cells(cl_list* c, long long ncells) {
   c->bytes += b;
   return CL_OK;
 }
+
+// CTAs of the persistent neighbourhood sweep that the partials buffer holds at nv doubles each.
+int hood_blocks(const cl_list* c, int nv) { return clk::sweep_partials_needed(c->n) / nv; }
 
 void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
   A->xs = c->xs;
@@ -118,14 +125,22 @@ int set_geometry(cl_list* c, const cl_box* box) {
   int e = clk::prepare_geometry(box, &g);
   if (e) return e;
   clk::Off* th = new (std::nothrow) clk::Off[2 * clk::kMaxOff];
-  if (!th) return CL_ERR_OOM;
+  int* opk = new (std::nothrow) int[2 * clk::kMaxOff];
+  if (!th || !opk) {
+    delete[] th;
+    delete[] opk;
+    return CL_ERR_OOM;
+  }
   clk::Off* tf = th + clk::kMaxOff;
-  int nh = clk::build_stencil(g, 1, th, clk::kMaxOff);
-  int nf = nh < 0 ? nh : clk::build_stencil(g, 0, tf, clk::kMaxOff);
+  int nh = clk::build_stencil(g, 1, th, clk::kMaxOff, opk + clk::kMaxOff);
+  int nf = nh < 0 ? nh : clk::build_stencil(g, 0, tf, clk::kMaxOff, opk);
   if (nh < 0 || nf < 0) {
     delete[] th;
+    delete[] opk;
     return nh < 0 ? nh : nf;
   }
+  if (g.dim == 3) clk::fill_hood_args(g, opk, nf, opk + clk::kMaxOff, nh, c->hood);
+  delete[] opk;
   if (g.ncells != c->ncells_alloc) {
     free_cells(c);
     if ((e = alloc_cells(c, g.ncells))) {
@@ -256,7 +271,8 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   std::memset(c, 0, sizeof(*c));
   c->half = new (std::nothrow) clk::SweepArgs;
   c->full = new (std::nothrow) clk::SweepArgs;
-  if (!c->half || !c->full) {
+  c->hood = new (std::nothrow) clk::HoodArgs;
+  if (!c->half || !c->full || !c->hood) {
     free_all(c);
     delete c;
     return CL_ERR_OOM;
@@ -279,6 +295,7 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
+  if (!e) e = dev_alloc(&c->work, 1, &b);
   if (!e) e = dev_alloc(&c->u64, 8, &b);
   if (!e) e = dev_alloc(&c->d_off_half, (size_t)clk::kMaxOff, &b);
   if (!e) e = dev_alloc(&c->d_off_full, (size_t)clk::kMaxOff, &b);
@@ -320,9 +337,15 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       return clk::launch_scalar(*c->half, dim, 0, c->partials, c->sums, r->sum_inv_r, s);
     case CL_RED_SF_ENERGY:
       if (!r->energy) return CL_ERR_INVALID_ARG;
+      if (dim == 3 && c->n > 0)
+        return clk::launch_hood(*c->half, *c->hood, c->work, 2, c->geo.hinv, nullptr, nullptr, nullptr, nullptr,
+                                c->partials, hood_blocks(c, 1), c->sums, r->energy, nullptr, nullptr, s);
       return clk::launch_scalar(*c->half, dim, 1, c->partials, c->sums, r->energy, s);
     case CL_RED_SF_ENERGY_FORCES_VIRIAL:
       if (!r->forces && c->n > 0) return CL_ERR_INVALID_ARG;
+      if (dim == 3 && c->n > 0)
+        return clk::launch_hood(*c->full, *c->hood, c->work, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr,
+                                c->partials, hood_blocks(c, 7), c->sums, r->energy, r->virial, nullptr, s);
       return clk::launch_force(*c->full, dim, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr, c->partials,
                                c->sums, r->energy, r->virial, nullptr, s);
     case CL_RED_HIST: {
@@ -341,6 +364,10 @@ int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_p
                 double* virial_dev, void* stream) {
   if (!cc || !grad_energy_dev || (cc->n > 0 && !grad_pos_dev)) return CL_ERR_INVALID_ARG;
   cl_list* c = const_cast<cl_list*>(cc);
+  if (c->geo.dim == 3 && c->n > 0)
+    return clk::launch_hood(*c->full, *c->hood, c->work, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev,
+                            c->pos, c->partials, hood_blocks(c, 15), c->sums, nullptr, virial_dev, grad_box_dev,
+                            (cudaStream_t)stream);
   return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev, c->pos,
                            c->partials, c->sums, nullptr, virial_dev, grad_box_dev, (cudaStream_t)stream);
 }

@@ -161,12 +161,13 @@ static double min_dist2(const Geo& geo, const int* o) {
   return best;
 }
 
-int build_stencil(const Geo& geo, int half, Off* out, int cap) {
+int build_stencil(const Geo& geo, int half, Off* out, int cap, int* opk) {
   const int dim = geo.dim;
   int m[3] = {0, 0, 0};
   for (int k = 0; k < dim; ++k) m[k] = (int)std::ceil(geo.rc * geo.n[k] / geo.w[k]);
   const double keep2 = geo.rc * geo.rc * (1.0 + 1e-9);
   std::vector<Off> v;
+  std::vector<int> pk;
   // own cell first
   for (int pass = 0; pass < 2; ++pass)
     for (int oz = -m[2]; oz <= m[2]; ++oz)
@@ -193,9 +194,11 @@ int build_stencil(const Geo& geo, int half, Off* out, int cap) {
           e.sy = (float)s[1];
           e.sz = (float)s[2];
           v.push_back(e);
+          pk.push_back((ox & 255) | ((oy & 255) << 8) | ((oz & 255) << 16));
         }
   if ((int)v.size() > cap) return CL_ERR_UNSUPPORTED;
   std::copy(v.begin(), v.end(), out);
+  if (opk) std::copy(pk.begin(), pk.end(), opk);
   return (int)v.size();
 }
 

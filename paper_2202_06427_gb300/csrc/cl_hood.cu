@@ -1,0 +1,673 @@
+// cl_hood.cu -- neighbourhood sweep of the shifted-force pair energy, forces
+// and virial in 3D: the loop over cells of Sec. 2.8 with the reduction fused,
+// organised around shared memory instead of one thread per particle.
+//
+// One CTA takes one home cell at a time (persistent CTAs, atomic work counter).
+//  1. Staging. The particles of every neighbour cell of the stencil are copied
+//     into shared memory, shifted into the frame of the home cell's centre
+//     (x' = x + S_o, once per staged particle), and only those with
+//     |x'| < rc + d_max are kept, d_max being the largest distance of a home
+//     particle from the centre: by the triangle inequality nothing farther is
+//     within rc of any home particle. A warp stages one neighbour cell at a time
+//     with coalesced loads and compacts the kept particles with a ballot.
+//  2. Sweep. A warp takes two home particles at a time; its lanes run over the
+//     staged array, two staged particles per lane in packed f32x2 arithmetic
+//     (staged pairs are stored interleaved), so one loaded neighbour serves four
+//     candidate pairs.
+//  3. The own cell is staged apart, in sorted order, so that a particle's pair
+//     with itself (and, for the half shell, pairs already counted) is masked by
+//     index.
+// Against the cell stencil, whose volume is (2 m + 1)^3 cells, the candidates
+// per home particle shrink to the ball of radius rc + d_max: about 2.6 per pair
+// within the cutoff instead of 4.0 at two cells per cutoff length.
+//
+// Virial. For ordered pair-images (i, j) whose lattice image T is zero the
+// reverse pair-image (j, i) also has T = 0, so with X the wrapped absolute
+// positions (cell centre plus local coordinate),
+//   sum over T = 0 pairs of fsn r (x) r = -2 sum_i X_i (x) Gn_i^(T=0),
+// Gn_i^(T=0) = sum over j with T = 0 of fsn r (fsn = -u'(r)/r). Neighbours
+// across the periodic boundary (T != 0) are staged in a segment of their own,
+// growing from the far end of the buffer, and add fsn r (x) r directly. Every
+// path of this file computes the same per-particle share, so their sums agree.
+//
+// Home cells that do not fit (more than kHome particles, or more than kCap
+// staged neighbours) are swept by the CTA one thread per particle over the
+// stencil (hood_fallback), with the same per-particle virial share.
+#include <cmath>
+#include <cstring>
+
+#include "cl_sweep.cuh"
+
+namespace clk {
+
+namespace {
+
+constexpr int kThreads = 128;
+constexpr int kWarps = kThreads / 32;
+constexpr int kHome = 128;             // home particles of the fast path (one per thread)
+constexpr int kCap = 2560;             // staged neighbour entries (even)
+constexpr int kTab = 1 + kWarps * 32;  // stencil entries the fast path takes (32 per warp)
+constexpr int kRound = 4;              // neighbour cells a warp loads before using them
+// Padding entries sit at (kFar, kFar, kFar) and a missing second home particle
+// of a group at -kFar: far from everything and from each other (the stand-ins
+// of non-finite inputs lie within [1e15, 2e15) per axis), with squared
+// distances that stay finite in FP32.
+constexpr float kFar = 3e15f;
+
+struct Smem {
+  float4 xy[kCap / 2];   // staged pairs (x_2k, x_2k+1, y_2k, y_2k+1)
+  float2 zz[kCap / 2];   // (z_2k, z_2k+1)
+  float4 oxy[kHome / 2]; // own cell in sorted order, same layout
+  float2 ozz[kHome / 2];
+  int hid[kHome];        // original index of the home particle
+  float acc[kHome][6];   // Gn and its T = 0 part
+  float4 otab[kTab];     // stencil entry: (shift x, y, z, unwrapped offset as int bits)
+  float wmax[kWarps];
+  int nf, nb;            // staged entries with T = 0 (from the front) and T != 0 (from the back)
+  int item;
+  int next;
+};
+
+__device__ __forceinline__ void unpack_off(int v, int& ox, int& oy, int& oz) {
+  ox = (int)(signed char)(v & 0xff);
+  oy = (int)(signed char)((v >> 8) & 0xff);
+  oz = (int)(signed char)((v >> 16) & 0xff);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float own_x(const Smem& S, int t) {
+  return reinterpret_cast<const float*>(S.oxy)[(t >> 1) * 4 + (t & 1)];
+}
+__device__ __forceinline__ float own_y(const Smem& S, int t) {
+  return reinterpret_cast<const float*>(S.oxy)[(t >> 1) * 4 + 2 + (t & 1)];
+}
+__device__ __forceinline__ float own_z(const Smem& S, int t) {
+  return reinterpret_cast<const float*>(S.ozz)[(t >> 1) * 2 + (t & 1)];
+}
+
+// Per-lane accumulators of one home particle (packed over the lane's two
+// staged neighbours).
+struct HAcc {
+  float2 gx, gy, gz;
+};
+
+// One home particle against the two staged neighbours (qx, qy, qz) of a lane.
+// (ix, iy, iz) = minus the home particle's coordinates in both halves.
+template <bool ENERGY, bool FORCE, bool VIR>
+__device__ __forceinline__ void hood_pair(float2 qx, float2 qy, float2 qz, float2 ix, float2 iy, float2 iz, bool m0,
+                                          bool m1, float rc2, float irc, float irc2, HAcc& a, float2& e, float2* w) {
+  const float2 dx = __fadd2_rn(qx, ix), dy = __fadd2_rn(qy, iy), dz = __fadd2_rn(qz, iz);
+  float2 d2 = __fmul2_rn(dz, dz);
+  d2 = __ffma2_rn(dy, dy, d2);
+  d2 = __ffma2_rn(dx, dx, d2);
+  const bool h0 = m0 && d2.x < rc2;
+  const bool h1 = m1 && d2.y < rc2;
+  if (h0 || h1) {
+    const float2 y = rsqrt2(d2);
+    if (FORCE) {
+      float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
+      fsn.x = h0 ? fsn.x : 0.f;
+      fsn.y = h1 ? fsn.y : 0.f;
+      if (VIR) {
+        const float2 tx = __fmul2_rn(fsn, dx), ty = __fmul2_rn(fsn, dy), tz = __fmul2_rn(fsn, dz);
+        a.gx = __fadd2_rn(a.gx, tx);
+        a.gy = __fadd2_rn(a.gy, ty);
+        a.gz = __fadd2_rn(a.gz, tz);
+        w[0] = __ffma2_rn(tx, dx, w[0]);
+        w[1] = __ffma2_rn(tx, dy, w[1]);
+        w[2] = __ffma2_rn(tx, dz, w[2]);
+        w[3] = __ffma2_rn(ty, dy, w[3]);
+        w[4] = __ffma2_rn(ty, dz, w[4]);
+        w[5] = __ffma2_rn(tz, dz, w[5]);
+      } else {
+        a.gx = __ffma2_rn(fsn, dx, a.gx);
+        a.gy = __ffma2_rn(fsn, dy, a.gy);
+        a.gz = __ffma2_rn(fsn, dz, a.gz);
+      }
+    }
+    if (ENERGY) {
+      const float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-irc), f2(1.0f));
+      float2 u = __fmul2_rn(__fmul2_rn(t, t), y);
+      u.x = h0 ? u.x : 0.f;
+      u.y = h1 ? u.y : 0.f;
+      e = __fadd2_rn(e, u);
+    }
+  }
+}
+
+// Lanes over staged pairs [k0, k1) against the two home particles of a group.
+template <bool ENERGY, bool FORCE, bool VIR>
+__device__ __forceinline__ void hood_scan(const float4* __restrict__ xy, const float2* __restrict__ zz, int k0, int k1,
+                                          const float2 (&I)[6], float rc2, float irc, float irc2, HAcc& a0, HAcc& a1,
+                                          float2& e, float2* w) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll 2
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const float4 q = xy[k];
+    const float2 z = zz[k];
+    const float2 qx = make_float2(q.x, q.y), qy = make_float2(q.z, q.w);
+    hood_pair<ENERGY, FORCE, VIR>(qx, qy, z, I[0], I[1], I[2], true, true, rc2, irc, irc2, a0, e, w);
+    hood_pair<ENERGY, FORCE, VIR>(qx, qy, z, I[3], I[4], I[5], true, true, rc2, irc, irc2, a1, e, w);
+  }
+}
+
+// Own cell in home order: entries 2k, 2k+1 of pair k; home particles t0, t1.
+// Full shell: every entry but the particle itself; half shell: entries after it.
+template <bool ENERGY, bool FORCE, bool HALF>
+__device__ __forceinline__ void hood_own(const float4* __restrict__ xy, const float2* __restrict__ zz, int npairs,
+                                         int t0, int t1, const float2 (&I)[6], float rc2, float irc, float irc2,
+                                         HAcc& a0, HAcc& a1, float2& e) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < npairs; k += 32) {
+    const float4 q = xy[k];
+    const float2 z = zz[k];
+    const float2 qx = make_float2(q.x, q.y), qy = make_float2(q.z, q.w);
+    const int e0 = 2 * k, e1 = 2 * k + 1;
+    const bool m00 = HALF ? e0 > t0 : e0 != t0, m01 = HALF ? e1 > t0 : e1 != t0;
+    const bool m10 = HALF ? e0 > t1 : e0 != t1, m11 = HALF ? e1 > t1 : e1 != t1;
+    hood_pair<ENERGY, FORCE, false>(qx, qy, z, I[0], I[1], I[2], m00, m01, rc2, irc, irc2, a0, e, nullptr);
+    hood_pair<ENERGY, FORCE, false>(qx, qy, z, I[3], I[4], I[5], m10, m11, rc2, irc, irc2, a1, e, nullptr);
+  }
+}
+
+// Neighbour cell of stencil entry k for one home cell: its particle range, its
+// shift, and the key offset of its segment (T != 0 staged apart).
+struct OffInfo {
+  int j0, j1, seg;
+  float sx, sy, sz;
+};
+
+template <bool FORCE>
+__device__ __forceinline__ OffInfo off_info(const SweepArgs& A, const Smem& S, int k, int cx, int cy, int cz) {
+  OffInfo f;
+  const float4 t = S.otab[k];
+  int ox, oy, oz;
+  unpack_off(__float_as_int(t.w), ox, oy, oz);
+  int x2 = cx + ox, y2 = cy + oy, z2 = cz + oz;
+  const bool wrap = (x2 < 0) || (x2 >= A.nx) || (y2 < 0) || (y2 >= A.ny) || (z2 < 0) || (z2 >= A.nz);
+  x2 %= A.nx;
+  x2 += x2 < 0 ? A.nx : 0;
+  y2 %= A.ny;
+  y2 += y2 < 0 ? A.ny : 0;
+  z2 %= A.nz;
+  z2 += z2 < 0 ? A.nz : 0;
+  const int c = x2 + A.nx * (y2 + A.ny * z2);
+  f.j0 = A.cell_start[c];
+  f.j1 = A.cell_start[c + 1];
+  f.seg = (FORCE && wrap) ? 1 : 0;
+  f.sx = t.x;
+  f.sy = t.y;
+  f.sz = t.z;
+  return f;
+}
+
+// Staging by one warp of its stencil entries 1 + warp + kWarps m, m < nmine
+// (lane m holds entry m's OffInfo). Lanes take consecutive particles of a
+// neighbour cell (coalesced loads); kRound cells are loaded before any is
+// used. Kept particles are compacted with a ballot: T = 0 entries from the
+// front of the buffer, T != 0 entries from the back. Writes stay in bounds;
+// overflow (nf + nb + 2 > kCap) is detected afterwards.
+__device__ __forceinline__ void stage_group(Smem& S, float4 q, float sx, float sy, float sz, int seg, float top2) {
+  const int lane = threadIdx.x & 31;
+  const float x = q.x + sx, y = q.y + sy, z = q.z + sz;
+  const float r2 = fmaf(x, x, fmaf(y, y, z * z));
+  const bool keep = r2 < top2;
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  if (!m) return;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(seg ? &S.nb : &S.nf, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (keep) {
+    const int r = base + __popc(m & ((1u << lane) - 1u));
+    const int e = seg ? kCap - 1 - r : r;
+    if (e >= 0 && e < kCap) {
+      float* const xyf = reinterpret_cast<float*>(S.xy);
+      float* const zzf = reinterpret_cast<float*>(S.zz);
+      xyf[(e >> 1) * 4 + (e & 1)] = x;
+      xyf[(e >> 1) * 4 + 2 + (e & 1)] = y;
+      zzf[(e >> 1) * 2 + (e & 1)] = z;
+    }
+  }
+}
+
+__device__ __forceinline__ void stage_warp(const SweepArgs& A, Smem& S, const OffInfo& mine, int nmine, float top2) {
+  const int lane = threadIdx.x & 31;
+  for (int m0 = 0; m0 < nmine; m0 += kRound) {
+    float4 q[kRound];
+    int j0[kRound], j1[kRound];
+#pragma unroll
+    for (int r = 0; r < kRound; ++r) {
+      j0[r] = __shfl_sync(0xffffffffu, mine.j0, (m0 + r) & 31);
+      j1[r] = __shfl_sync(0xffffffffu, mine.j1, (m0 + r) & 31);
+      if (m0 + r >= nmine) j1[r] = j0[r];
+      const int j = j0[r] + lane;
+      q[r] = j < j1[r] ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f);
+    }
+#pragma unroll
+    for (int r = 0; r < kRound; ++r) {
+      const float sx = __shfl_sync(0xffffffffu, mine.sx, (m0 + r) & 31);
+      const float sy = __shfl_sync(0xffffffffu, mine.sy, (m0 + r) & 31);
+      const float sz = __shfl_sync(0xffffffffu, mine.sz, (m0 + r) & 31);
+      const int seg = __shfl_sync(0xffffffffu, mine.seg, (m0 + r) & 31);
+      stage_group(S, q[r], sx, sy, sz, seg, top2);
+      for (int jb = j0[r] + 32; jb < j1[r]; jb += 32) {
+        const int j = jb + lane;
+        stage_group(S, j < j1[r] ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f), sx, sy, sz, seg, top2);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- fallback
+// One thread per home particle over the stencil on the shifted-pair arrays,
+// with the same per-particle virial share as the fast path.
+template <bool ENERGY, bool FORCE>
+struct RedFallback {
+  static constexpr bool kFull = FORCE;
+  float irc, irc2;
+  struct Acc {
+    float2 gx, gy, gz;  // current neighbour cell
+    float tx, ty, tz;   // Gn
+    float ax, ay, az;   // Gn^(T=0)
+    float2 w[6];        // direct fsn r (x) r of T != 0 cells
+    float2 e;
+    bool wrap;
+  };
+  __device__ void init(Acc& a) const {
+    a.gx = a.gy = a.gz = a.e = f2(0.f);
+    a.tx = a.ty = a.tz = a.ax = a.ay = a.az = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a.w[k] = f2(0.f);
+    a.wrap = false;
+  }
+  __device__ void hit2(Acc& a, float2 dx, float2 dy, float2 dz, float2 d2, bool h0, bool h1) const {
+    const float2 y = rsqrt2(d2);
+    if (FORCE) {
+      float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
+      fsn.x = h0 ? fsn.x : 0.f;
+      fsn.y = h1 ? fsn.y : 0.f;
+      const float2 tx = __fmul2_rn(fsn, dx), ty = __fmul2_rn(fsn, dy), tz = __fmul2_rn(fsn, dz);
+      a.gx = __fadd2_rn(a.gx, tx);
+      a.gy = __fadd2_rn(a.gy, ty);
+      a.gz = __fadd2_rn(a.gz, tz);
+      if (a.wrap) {
+        a.w[0] = __ffma2_rn(tx, dx, a.w[0]);
+        a.w[1] = __ffma2_rn(tx, dy, a.w[1]);
+        a.w[2] = __ffma2_rn(tx, dz, a.w[2]);
+        a.w[3] = __ffma2_rn(ty, dy, a.w[3]);
+        a.w[4] = __ffma2_rn(ty, dz, a.w[4]);
+        a.w[5] = __ffma2_rn(tz, dz, a.w[5]);
+      }
+    }
+    if (ENERGY) {
+      const float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-irc), f2(1.0f));
+      float2 u = __fmul2_rn(__fmul2_rn(t, t), y);
+      u.x = h0 ? u.x : 0.f;
+      u.y = h1 ? u.y : 0.f;
+      a.e = __fadd2_rn(a.e, u);
+    }
+  }
+  __device__ void cell_done(Acc& a) const {
+    const float gx = a.gx.x + a.gx.y, gy = a.gy.x + a.gy.y, gz = a.gz.x + a.gz.y;
+    a.tx += gx;
+    a.ty += gy;
+    a.tz += gz;
+    if (!a.wrap) {
+      a.ax += gx;
+      a.ay += gy;
+      a.az += gz;
+    }
+    a.gx = a.gy = a.gz = f2(0.f);
+  }
+};
+
+// Per-thread outputs of the sweep: energy (Kahan-compensated FP32), the share
+// of sum fsn r (x) r (xx, xy, xz, yy, yz, zz) and X = sum x_raw (x) F (backward).
+struct ThreadOut {
+  float es, ec;
+  float v[6];
+  float x[9];
+  __device__ void add_energy(float t) {
+    const float y = t - ec;
+    const float s = es + y;
+    ec = (s - es) - y;
+    es = s;
+  }
+};
+
+// Per-particle epilogue: force, virial share -2 X (x) Gn^(T=0), and X.
+template <int MODE>
+__device__ __forceinline__ void hood_particle_out(ThreadOut& T, int i, float px, float py, float pz, const float* c,
+                                                  float gx, float gy, float gz, float ax, float ay, float az,
+                                                  float* __restrict__ forces, double* __restrict__ grad, double g,
+                                                  const double* __restrict__ pos) {
+  const float X[3] = {c[0] + px, c[1] + py, c[2] + pz};
+  const float A[3] = {ax, ay, az};
+  // symmetric part of -2 X (x) A
+  T.v[0] -= 2.f * X[0] * A[0];
+  T.v[1] -= X[0] * A[1] + X[1] * A[0];
+  T.v[2] -= X[0] * A[2] + X[2] * A[0];
+  T.v[3] -= 2.f * X[1] * A[1];
+  T.v[4] -= X[1] * A[2] + X[2] * A[1];
+  T.v[5] -= 2.f * X[2] * A[2];
+  const float F[3] = {-gx, -gy, -gz};
+  if (MODE == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) forces[(size_t)i * 3 + a] = F[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = -g * (double)F[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float xa = (float)pos[(size_t)i * 3 + a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) T.x[a * 3 + b] = fmaf(xa, F[b], T.x[a * 3 + b]);
+    }
+  }
+}
+
+template <int MODE>
+__device__ void hood_fallback(const SweepArgs& A, const HoodArgs& H, int hs, int nh, int cx, int cy, int cz,
+                              const float* cc, ThreadOut& T, float* __restrict__ forces, double* __restrict__ grad,
+                              double g, const double* __restrict__ pos) {
+  constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1;
+  RedFallback<ENERGY, FORCE> red;
+  red.irc = A.irc;
+  red.irc2 = A.irc2;
+  for (int t = threadIdx.x; t < nh; t += kThreads) {
+    const int p = hs + t;
+    const float4 pi = A.xs[p];
+    typename RedFallback<ENERGY, FORCE>::Acc acc;
+    red.init(acc);
+    {
+      const int s0 = hs, s1 = hs + nh;
+      if (FORCE) scan_pairs(A.xy2, A.zz2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+      scan_pairs(A.xy2, A.zz2, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+      red.cell_done(acc);
+    }
+    for (int k = 1; k < A.noff; ++k) {
+      const Off& o = A.off[k];
+      const int c = stencil_cell(A, k, cx, cy, cz);
+      if (FORCE) {
+        int ox, oy, oz;
+        unpack_off(H.opk[0][k], ox, oy, oz);
+        acc.wrap = (cx + ox < 0) || (cx + ox >= A.nx) || (cy + oy < 0) || (cy + oy >= A.ny) || (cz + oz < 0) ||
+                   (cz + oz >= A.nz);
+      }
+      scan_pairs(A.xy2, A.zz2, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
+                 red, acc);
+      red.cell_done(acc);
+    }
+    if (ENERGY) T.add_energy(acc.e.x + acc.e.y);
+    if (FORCE) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) T.v[k] += acc.w[k].x + acc.w[k].y;
+      hood_particle_out<MODE>(T, __float_as_int(pi.w), pi.x, pi.y, pi.z, cc, acc.tx, acc.ty, acc.tz, acc.ax, acc.ay,
+                              acc.az, forces, grad, g, pos);
+    }
+  }
+}
+
+// MODE 0: energy, forces, virial (full shell). MODE 1: backward: grad_pos, X,
+// virial (full shell). MODE 2: energy (half shell).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ SweepArgs A, const __grid_constant__ HoodArgs H,
+                                                      float* __restrict__ forces, double* __restrict__ grad,
+                                                      const double* __restrict__ gE, const double* __restrict__ pos,
+                                                      double* __restrict__ partials) {
+  constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1, HALF = MODE == 2;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Smem& S = *reinterpret_cast<Smem*>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double g = (MODE == 1) ? *gE : 0.0;
+  ThreadOut T;
+  T.es = T.ec = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) T.v[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) T.x[k] = 0.f;
+  float* const xyf = reinterpret_cast<float*>(S.xy);
+  float* const zzf = reinterpret_cast<float*>(S.zz);
+  float* const oxyf = reinterpret_cast<float*>(S.oxy);
+  float* const ozzf = reinterpret_cast<float*>(S.ozz);
+  const bool table = A.noff <= kTab;  // otherwise every cell takes the fallback
+  for (int k = tid; k < A.noff && k < kTab; k += kThreads) {
+    const Off& o = A.off[k];
+    S.otab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[HALF ? 1 : 0][k]));
+  }
+  if (tid == 0) S.next = atomicAdd(H.work, 1);
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      S.item = S.next;
+      S.nf = 0;
+      S.nb = 0;
+    }
+    __syncthreads();
+    const int h = S.item;
+    if (h >= H.ncells) break;
+    const int hs = A.cell_start[h];
+    const int nh = A.cell_start[h + 1] - hs;
+    if (tid == 0) S.next = atomicAdd(H.work, 1);  // read at the top of the next iteration
+    if (nh == 0) continue;
+    const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
+    float cc[3];  // centre of the home cell (wrapped absolute frame)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      cc[a] = (float)((cx + 0.5) * H.g[a] + (cy + 0.5) * H.g[3 + a] + (cz + 0.5) * H.g[6 + a]);
+    if (nh > kHome || !table) {
+      hood_fallback<MODE>(A, H, hs, nh, cx, cy, cz, cc, T, forces, grad, g, pos);
+      continue;
+    }
+
+    // ---- home particles (sorted order) and their largest distance from the centre
+    float d = 0.f;
+    if (tid < nh) {
+      const float4 hq = A.xs[hs + tid];
+      d = fminf(sqrtf(fmaf(hq.x, hq.x, fmaf(hq.y, hq.y, hq.z * hq.z))), H.hd);
+      S.hid[tid] = __float_as_int(hq.w);
+      oxyf[(tid >> 1) * 4 + (tid & 1)] = hq.x;
+      oxyf[(tid >> 1) * 4 + 2 + (tid & 1)] = hq.y;
+      ozzf[(tid >> 1) * 2 + (tid & 1)] = hq.z;
+    }
+    if (tid == 0 && (nh & 1)) {
+      oxyf[(nh >> 1) * 4 + 1] = kFar;
+      oxyf[(nh >> 1) * 4 + 3] = kFar;
+      ozzf[(nh >> 1) * 2 + 1] = kFar;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if (lane == 0) S.wmax[warp] = d;
+    // stencil entries of this warp: 1 + warp + kWarps m, lane m holding entry m
+    OffInfo mine;
+    mine.j0 = mine.j1 = mine.seg = 0;
+    mine.sx = mine.sy = mine.sz = 0.f;
+    const int kmine = 1 + warp + kWarps * lane;
+    if (kmine < A.noff) mine = off_info<FORCE>(A, S, kmine, cx, cy, cz);
+    const int nmine = (A.noff - 1 - warp + kWarps - 1) / kWarps;
+    __syncthreads();
+    float dmax = S.wmax[0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) dmax = fmaxf(dmax, S.wmax[w]);
+    const float top = H.rc + dmax + H.eps;
+
+    // ---- staging
+    stage_warp(A, S, mine, nmine, top * top);
+    __syncthreads();
+    const int nf = S.nf, nb = S.nb;
+    if (nf + nb + 2 > kCap) {
+      hood_fallback<MODE>(A, H, hs, nh, cx, cy, cz, cc, T, forces, grad, g, pos);
+      continue;
+    }
+    if (tid == 0 && (nf & 1)) {  // padding after an odd segment
+      xyf[(nf >> 1) * 4 + 1] = kFar;
+      xyf[(nf >> 1) * 4 + 3] = kFar;
+      zzf[(nf >> 1) * 2 + 1] = kFar;
+    }
+    if (tid == 1 && (nb & 1)) {
+      const int e = kCap - nb - 1;
+      xyf[(e >> 1) * 4 + 0] = kFar;
+      xyf[(e >> 1) * 4 + 2] = kFar;
+      zzf[(e >> 1) * 2 + 0] = kFar;
+    }
+    __syncthreads();
+
+    // ---- sweep: groups of two home particles per warp
+    const int ngroups = (nh + 1) >> 1;
+    const int k0a = 0, k1a = (nf + 1) >> 1;
+    const int k0b = (kCap - nb) >> 1, k1b = kCap >> 1;
+    for (int gi = warp; gi < ngroups; gi += kWarps) {
+      const int t0 = 2 * gi, t1 = 2 * gi + 1;
+      const bool has1 = t1 < nh;
+      float2 I[6];
+      I[0] = f2(-own_x(S, t0));
+      I[1] = f2(-own_y(S, t0));
+      I[2] = f2(-own_z(S, t0));
+      I[3] = f2(has1 ? -own_x(S, t1) : kFar);
+      I[4] = f2(has1 ? -own_y(S, t1) : kFar);
+      I[5] = f2(has1 ? -own_z(S, t1) : kFar);
+      HAcc a0, a1;
+      a0.gx = a0.gy = a0.gz = a1.gx = a1.gy = a1.gz = f2(0.f);
+      float2 e = f2(0.f);
+      hood_scan<ENERGY, FORCE, false>(S.xy, S.zz, k0a, k1a, I, A.rc2, A.irc, A.irc2, a0, a1, e, nullptr);
+      hood_own<ENERGY, FORCE, HALF>(S.oxy, S.ozz, ngroups, t0, t1, I, A.rc2, A.irc, A.irc2, a0, a1, e);
+      if (FORCE) {
+        // T = 0 part first, then the neighbours across the boundary
+        float g6[6] = {a0.gx.x + a0.gx.y, a0.gy.x + a0.gy.y, a0.gz.x + a0.gz.y,
+                       a1.gx.x + a1.gx.y, a1.gy.x + a1.gy.y, a1.gz.x + a1.gz.y};
+        float A6[6];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) A6[q] = warp_sum(g6[q]);
+        if (k1b > k0b) {
+          a0.gx = a0.gy = a0.gz = a1.gx = a1.gy = a1.gz = f2(0.f);
+          float2 w[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) w[q] = f2(0.f);
+          hood_scan<ENERGY, FORCE, true>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, w);
+#pragma unroll
+          for (int q = 0; q < 6; ++q) T.v[q] += w[q].x + w[q].y;
+          const float b6[6] = {a0.gx.x + a0.gx.y, a0.gy.x + a0.gy.y, a0.gz.x + a0.gz.y,
+                               a1.gx.x + a1.gx.y, a1.gy.x + a1.gy.y, a1.gz.x + a1.gz.y};
+#pragma unroll
+          for (int q = 0; q < 6; ++q) g6[q] = A6[q] + warp_sum(b6[q]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) g6[q] = A6[q];
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            S.acc[t0][q] = g6[q];
+            S.acc[t0][3 + q] = A6[q];
+          }
+          if (has1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+              S.acc[t1][q] = g6[3 + q];
+              S.acc[t1][3 + q] = A6[3 + q];
+            }
+          }
+        }
+      } else if (k1b > k0b) {
+        hood_scan<ENERGY, FORCE, false>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, nullptr);
+      }
+      if (ENERGY) T.add_energy(e.x + e.y);
+    }
+    __syncthreads();
+    if (FORCE && tid < nh) {
+      const int t = tid;
+      hood_particle_out<MODE>(T, S.hid[t], own_x(S, t), own_y(S, t), own_z(S, t), cc, S.acc[t][0], S.acc[t][1],
+                              S.acc[t][2], S.acc[t][3], S.acc[t][4], S.acc[t][5], forces, grad, g, pos);
+    }
+  }
+
+  // per-CTA partials in the layout of the other sweeps
+  constexpr int NV = (MODE == 0) ? 1 + kVirN3 : (MODE == 1 ? kVirN3 + 9 : 1);
+  double v[NV];
+  if (MODE == 2) {
+    v[0] = (double)T.es - (double)T.ec;
+  } else {
+    // the accumulator of the other sweeps is sum fs r (x) r = -(sum fsn r (x) r)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = -(double)T.v[k];
+    if (MODE == 0) v[kVirN3] = 0.5 * ((double)T.es - (double)T.ec);
+    if (MODE == 1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[kVirN3 + k] = (double)T.x[k];
+    }
+  }
+  block_sum_store<NV>(v, partials + (size_t)blockIdx.x * NV);
+}
+
+}  // namespace
+
+int hood_grid(int mode) {
+  static int cached[3] = {0, 0, 0};
+  if (mode < 0 || mode > 2) return 0;
+  if (cached[mode]) return cached[mode];
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cudaError_t e;
+  if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<0>, kThreads, sizeof(Smem));
+  else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<1>, kThreads, sizeof(Smem));
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<2>, kThreads, sizeof(Smem));
+  if (e != cudaSuccess || per < 1) return 0;
+  cached[mode] = sms * per;
+  return cached[mode];
+}
+
+size_t hood_smem_bytes() { return sizeof(Smem); }
+
+int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
+                   HoodArgs* H) {
+  std::memset(H, 0, sizeof(*H));
+  for (int k = 0; k < noff_full && k < kMaxOff; ++k) H->opk[0][k] = opk_full[k];
+  for (int k = 0; k < noff_half && k < kMaxOff; ++k) H->opk[1][k] = opk_half[k];
+  double hd = 0.0;
+  for (int s = 0; s < 8; ++s) {
+    double v[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      const double sg = ((s >> k) & 1) ? 0.5 : -0.5;
+      for (int a = 0; a < 3; ++a) v[a] += sg * geo.h[k * 3 + a] / geo.n[k];
+    }
+    const double d = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (d > hd) hd = d;
+  }
+  for (int k = 0; k < 3; ++k)
+    for (int a = 0; a < 3; ++a) H->g[k * 3 + a] = geo.h[k * 3 + a] / geo.n[k];
+  const double eps = 1e-4 * (geo.rc + hd);
+  H->rc = (float)geo.rc;
+  H->hd = (float)(hd * (1.0 + 1e-6));
+  H->eps = (float)eps;
+  H->ncells = (int)geo.ncells;
+  return CL_OK;
+}
+
+int launch_hood(const SweepArgs& A, const HoodArgs& Hin, int* work, int mode, const double* hinv, float* forces,
+                double* grad, const double* gE, const double* pos, double* partials, int max_blocks, double* sums,
+                double* energy, double* virial, double* gradbox, cudaStream_t s) {
+  const int NV = mode == 0 ? 1 + kVirN3 : (mode == 1 ? kVirN3 + 9 : 1);
+  int nb = hood_grid(mode);
+  if (nb <= 0) return CL_ERR_CUDA;
+  if (nb > Hin.ncells) nb = Hin.ncells;
+  if (nb > max_blocks) nb = max_blocks;
+  if (nb < 1) nb = 1;
+  HoodArgs H = Hin;
+  H.work = work;
+  if (cudaMemsetAsync(work, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  const size_t smem = sizeof(Smem);
+  if (mode == 0) k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+  else if (mode == 1) k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+  else k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+  return finish_reduction(mode == 2 ? 1 : (mode == 0 ? 2 : 3), 3, hinv, nb, NV, partials, sums, energy, virial,
+                          gradbox, gE, s);
+}
+
+}  // namespace clk

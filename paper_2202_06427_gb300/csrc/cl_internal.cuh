@@ -80,8 +80,10 @@ struct SweepArgs {
 
 // Host helpers implemented in cl_geom.cu.
 int prepare_geometry(const cl_box* box, Geo* geo);
-// Builds the half-shell (half = 1) or full stencil; returns the entry count or a negative error.
-int build_stencil(const Geo& geo, int half, Off* out, int cap);
+// Builds the half-shell (half = 1) or full stencil; returns the entry count or a
+// negative error. opk (optional) receives each entry's unwrapped offset packed
+// as bytes: (ox & 255) | (oy & 255) << 8 | (oz & 255) << 16.
+int build_stencil(const Geo& geo, int half, Off* out, int cap, int* opk = nullptr);
 
 }  // namespace clk
 
@@ -117,6 +119,29 @@ int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, floa
                  const double* gE, const double* pos, double* partials, double* sums, double* energy,
                  double* virial, double* gradbox, cudaStream_t s);
 int launch_candidates(const SweepArgs& A, long long ncells, unsigned long long* out, cudaStream_t s);
+// Sums per-CTA partials[nblocks][nv] and writes the caller's outputs. final_mode:
+// 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward.
+int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, int nv, const double* partials,
+                     double* sums, double* scalar, double* virial, double* gradbox, const double* gE,
+                     cudaStream_t s);
+
+// Neighbourhood sweep of the 3D shifted-force energy (cl_hood.cu).
+struct HoodArgs {
+  int opk[2][kMaxOff];  // unwrapped stencil offsets (see build_stencil): [0] full, [1] half stencil
+  double g[9];        // cell edge vectors G_k = H_k / n_k (rows), FP64
+  float rc;
+  float hd;           // largest distance of a cell point from the cell centre
+  float eps;          // rounding margin of the staging radius
+  int ncells;
+  int* work;          // work counter, zeroed by the launcher
+};
+int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
+                   HoodArgs* H);
+size_t hood_smem_bytes();
+// mode 0: energy, forces, virial; 1: backward; 2: energy (half shell, A = half stencil).
+int launch_hood(const SweepArgs& A, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
+                double* grad, const double* gE, const double* pos, double* partials, int max_blocks, double* sums,
+                double* energy, double* virial, double* gradbox, cudaStream_t s);
 
 // Neighbour list (cl_pairs.cu). count[n], start[n+1] (scan of count), tiles,
 // meta: workspace; outputs pair_i/j/d of capacity entries.

@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(256) k_sweep_hist(const __grid_constant__ Swee
 // Full shell: forces (FP32, original order), and per CTA the energy (x1/2) and
 // the symmetric accumulator of the virial. MODE 0: forward forces; MODE 1:
 // backward, grad_pos = -g F in FP64 plus X = sum x_raw (x) F for the box gradient.
-constexpr int kVirN3 = 6, kVirN2 = 3;
 template <int DIM, int MODE>
 __global__ void __launch_bounds__(256) k_sweep_force(const __grid_constant__ SweepArgs A, float* __restrict__ forces,
                                                      double* __restrict__ grad, const double* __restrict__ gE,
@@ -256,6 +255,24 @@ __global__ void k_final_assemble(const __grid_constant__ FinalArgs F, const doub
   }
 }
 
+int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, int nv, const double* partials,
+                     double* sums, double* scalar, double* virial, double* gradbox, const double* gE,
+                     cudaStream_t s) {
+  k_final_sum<<<nv, 256, 0, s>>>(partials, nblocks, nv, sums);
+  FinalArgs F;
+  memset(&F, 0, sizeof(F));
+  F.mode = final_mode;
+  F.dim = dim;
+  if (hinv)
+    for (int k = 0; k < 9; ++k) F.hinv[k] = hinv[k];
+  F.out_scalar = scalar;
+  F.out_virial = virial;
+  F.out_gradbox = gradbox;
+  F.gE = gE;
+  k_final_assemble<<<1, 32, 0, s>>>(F, sums);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
 // Candidate pairs the half-shell sweep tests: for each cell c,
 // n_c (n_c - 1)/2 + n_c sum_{o != 0} n_{c+o}.
 __global__ void __launch_bounds__(256) k_candidates(const __grid_constant__ SweepArgs A, long long ncells,
@@ -286,7 +303,10 @@ __global__ void __launch_bounds__(256) k_candidates(const __grid_constant__ Swee
 
 static int blocks_for(int n) { return n > 0 ? (n + 255) / 256 : 1; }
 
-int sweep_partials_needed(int n) { return blocks_for(n) * 16; }
+// Per-CTA partials (16 doubles each) for the one-thread-per-particle sweeps and
+// for the persistent neighbourhood sweep (at most kMaxPersistent CTAs).
+constexpr int kMaxPersistent = 4096;
+int sweep_partials_needed(int n) { return (blocks_for(n) > kMaxPersistent ? blocks_for(n) : kMaxPersistent) * 16; }
 
 int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStream_t s) {
   if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
@@ -312,14 +332,7 @@ int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, doubl
   } else {
     if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
   }
-  k_final_sum<<<1, 256, 0, s>>>(partials, A.n > 0 ? nb : 1, 1, sums);
-  FinalArgs F;
-  memset(&F, 0, sizeof(F));
-  F.mode = kind;
-  F.dim = dim;
-  F.out_scalar = out;
-  k_final_assemble<<<1, 32, 0, s>>>(F, sums);
-  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+  return finish_reduction(kind, dim, nullptr, A.n > 0 ? nb : 1, 1, partials, sums, out, nullptr, nullptr, nullptr, s);
 }
 
 int launch_hist(const SweepArgs& A, int dim, int nbins, float rmax, unsigned long long* hist, cudaStream_t s) {
@@ -353,18 +366,8 @@ int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, floa
   } else {
     if (cudaMemsetAsync(partials, 0, sizeof(double) * NV, s) != cudaSuccess) return CL_ERR_CUDA;
   }
-  k_final_sum<<<NV, 256, 0, s>>>(partials, A.n > 0 ? nb : 1, NV, sums);
-  FinalArgs F;
-  memset(&F, 0, sizeof(F));
-  F.mode = mode == 0 ? 2 : 3;
-  F.dim = dim;
-  for (int k = 0; k < 9; ++k) F.hinv[k] = hinv[k];
-  F.out_scalar = energy;
-  F.out_virial = virial;
-  F.out_gradbox = gradbox;
-  F.gE = gE;
-  k_final_assemble<<<1, 32, 0, s>>>(F, sums);
-  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+  return finish_reduction(mode == 0 ? 2 : 3, dim, hinv, A.n > 0 ? nb : 1, NV, partials, sums, energy, virial, gradbox,
+                          gE, s);
 }
 
 int launch_candidates(const SweepArgs& A, long long ncells, unsigned long long* out, cudaStream_t s) {

@@ -6,6 +6,9 @@
 
 namespace clk {
 
+// Entries of the symmetric virial accumulator (xx, xy, xz, yy, yz, zz / xx, xy, yy).
+constexpr int kVirN3 = 6, kVirN2 = 3;
+
 // 1/sqrt(d2) to FP32 accuracy: hardware estimate plus one Newton-Raphson
 // step, y1 = y0 + y0 (1 - d2 y0^2) / 2.
 __device__ __forceinline__ float rsqrt_nr(float d2) {
