@@ -138,6 +138,23 @@ int cl_map(const cl_list* cl, cl_reduction red, const cl_params* params, cl_resu
 int cl_backward(const cl_list* cl, const double* grad_energy_dev, double* grad_pos_dev, double* grad_box_dev,
                 double* virial_dev, void* stream);
 
+/* Energy and its gradient in one sweep: the forward pass of a differentiable
+ * caller that needs the gradient afterwards (Sec. 3.3, Code 9, with the
+ * forward and the adjoint fused). Writes energy_dev[0] = E (the value
+ * cl_map(CL_RED_SF_ENERGY) gives) and, scaled by s = scale_dev[0] (1 FP64
+ * value, device; 1 for the plain derivatives), grad_pos_dev = s dE/dx
+ * ((n, dim) FP64, original order) and, when grad_box_dev is not NULL,
+ * grad_box_dev = s dE/dH (dim*dim); virial_dev (optional) receives W. The
+ * same outputs as cl_map(CL_RED_SF_ENERGY) plus cl_backward(scale_dev), at the
+ * cost of one full-shell sweep. Errors as cl_backward. */
+int cl_energy_grad(const cl_list* cl, const double* scale_dev, double* energy_dev, double* grad_pos_dev,
+                   double* grad_box_dev, double* virial_dev, void* stream);
+
+/* out_dev[k] = s * in_dev[k] for k < count, s = scale_dev[0] (FP64, device):
+ * the chain rule applied to a gradient saved by cl_energy_grad. in_dev and
+ * out_dev may be the same array. Errors: INVALID_ARG, CUDA. */
+int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, long long count, void* stream);
+
 /* Queries. Grid and size values are answered from the host; NONEMPTY,
  * MAX_OCCUPANCY and CANDIDATES read device counters and synchronize
  * `stream` (NULL = legacy default stream) first. */

@@ -1,9 +1,10 @@
 """GB300 cell-list pair map (CellListMap.jl, arXiv 2202.06427): binning and
 neighbour-cell sweep in hand-written CUDA for sm_103a behind a C ABI
 (include/cellmap.h), with this thin Python binding over it."""
-from .api import (CellList, CellMapError, cl_backward, cl_box_info, cl_build, cl_error_string, cl_free, cl_map,
-                  cl_query, cl_status, cl_update, make_box)
+from .api import (CellList, CellMapError, cl_backward, cl_box_info, cl_build, cl_energy_grad, cl_error_string,
+                  cl_free, cl_map, cl_query, cl_scale, cl_status, cl_update, make_box)
 from .autograd import ShiftedForceEnergy, energy
 
-__all__ = ["CellList", "CellMapError", "cl_backward", "cl_box_info", "cl_build", "cl_error_string", "cl_free",
-           "cl_map", "cl_query", "cl_status", "cl_update", "make_box", "ShiftedForceEnergy", "energy"]
+__all__ = ["CellList", "CellMapError", "cl_backward", "cl_box_info", "cl_build", "cl_energy_grad", "cl_error_string",
+           "cl_free", "cl_map", "cl_query", "cl_scale", "cl_status", "cl_update", "make_box", "ShiftedForceEnergy",
+           "energy"]

@@ -58,6 +58,8 @@ def lib():
         L.cl_update.argtypes = [P, P, ctypes.POINTER(cl_box), P]
         L.cl_map.argtypes = [P, i32, ctypes.POINTER(cl_params), ctypes.POINTER(cl_result), P]
         L.cl_backward.argtypes = [P, P, P, P, P, P]
+        L.cl_energy_grad.argtypes = [P, P, P, P, P, P, P]
+        L.cl_scale.argtypes = [P, P, P, ll, P]
         L.cl_query.argtypes = [P, i32, ctypes.POINTER(ll), P]
         L.cl_box_info.argtypes = [ctypes.POINTER(cl_box), P, P, P]
         L.cl_status.argtypes = [P, P]
@@ -67,7 +69,8 @@ def lib():
         L.cl_energy_noalloc.restype = ctypes.c_int
         L.cl_error_string.argtypes = [i32]
         L.cl_error_string.restype = ctypes.c_char_p
-        for f in ("cl_build", "cl_update", "cl_map", "cl_backward", "cl_query", "cl_box_info", "cl_status"):
+        for f in ("cl_build", "cl_update", "cl_map", "cl_backward", "cl_energy_grad", "cl_scale", "cl_query",
+                  "cl_box_info", "cl_status"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib

@@ -177,6 +177,37 @@ def cl_backward(cl, grad_energy, want_box=True, want_virial=True, stream=None):
     return gp, gb, vir
 
 
+def cl_energy_grad(cl, scale=None, want_box=True, want_virial=False, stream=None):
+    """Energy and scale * (dE/dx, dE/dH) in one sweep: (energy (1,), dE/dx (n, dim),
+    dE/dH (dim, dim) or None, virial or None), float64 on the list's device.
+    scale: 1-element tensor (default 1)."""
+    dev = cl.device
+    if scale is None:
+        g = torch.ones(1, dtype=torch.float64, device=dev)
+    else:
+        g = scale.to(device=dev, dtype=torch.float64).reshape(1).contiguous()
+    e = torch.empty(1, dtype=torch.float64, device=dev)
+    gp = torch.empty((cl.n, cl.dim), dtype=torch.float64, device=dev)
+    gb = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_box else None
+    vir = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_virial else None
+    with torch.cuda.device(dev):
+        L.check(L.lib().cl_energy_grad(cl.handle, _ptr(g), _ptr(e), _ptr(gp), _ptr(gb), _ptr(vir), _stream(stream)),
+                "cl_energy_grad")
+    return e, gp, gb, vir
+
+
+def cl_scale(scale, x, out=None, stream=None):
+    """out = scale * x for float64 CUDA tensors (scale: 1 element); returns out."""
+    if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float64 CUDA tensor")
+    g = scale.to(device=x.device, dtype=torch.float64).reshape(1).contiguous()
+    if out is None:
+        out = torch.empty_like(x)
+    with torch.cuda.device(x.device):
+        L.check(L.lib().cl_scale(_ptr(g), _ptr(x), _ptr(out), x.numel(), _stream(stream)), "cl_scale")
+    return out
+
+
 def cl_query(cl, what, stream=None):
     v = ctypes.c_longlong(0)
     key = L.INFO[what] if isinstance(what, str) else int(what)

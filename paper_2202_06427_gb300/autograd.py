@@ -5,14 +5,16 @@ CUDA kernel, not tracing).
     E(x, H) = sum over pair-images within rc of u(r),
     u(r) = 1/r - 1/rc + (r - rc)/rc^2.
 
-Forward runs the half-shell energy sweep. Backward runs the full-shell force
-sweep: dL/dx = dL/dE * dE/dx = -dL/dE * F, and dL/dH at fixed Cartesian
-positions = dL/dE * H^-T (X - W) with X = sum_i x_i (x) F_i and W the virial.
+When a gradient will be needed, forward runs one full-shell sweep that gives
+the energy together with dE/dx = -F and dE/dH at fixed Cartesian positions,
+H^-T (X - W) with X = sum_i x_i (x) F_i and W the virial (cl_energy_grad), and
+backward only scales them by dL/dE (cl_scale). Otherwise forward runs the
+half-shell energy sweep alone.
 """
 import numpy as np
 import torch
 
-from .api import cl_backward, cl_build, cl_map, cl_update
+from .api import cl_build, cl_energy_grad, cl_map, cl_scale, cl_update
 
 
 class _Holder:
@@ -30,17 +32,23 @@ class ShiftedForceEnergy(torch.autograd.Function):
             holder.cl = cl_build(pos, hnp, holder.cutoff, holder.lcell)
         else:
             cl_update(holder.cl, pos, h=hnp)
-        e = cl_map(holder.cl, "energy")["energy"]
-        ctx.holder = holder
         ctx.h_meta = (h.device, h.dtype) if torch.is_tensor(h) else None
+        want_box = bool(ctx.needs_input_grad[1]) and ctx.h_meta is not None
+        if ctx.needs_input_grad[0] or want_box:
+            e, dedx, dedh, _ = cl_energy_grad(holder.cl, want_box=want_box)
+            ctx.save_for_backward(dedx, dedh if want_box else None)
+        else:
+            e = cl_map(holder.cl, "energy")["energy"]
         return e.reshape(())
 
     @staticmethod
     def backward(ctx, g):
-        want_box = bool(ctx.needs_input_grad[1]) and ctx.h_meta is not None
-        gp, gb, _ = cl_backward(ctx.holder.cl, g.detach(), want_box=want_box, want_virial=False)
-        if want_box:
-            gb = gb.to(device=ctx.h_meta[0], dtype=ctx.h_meta[1])
+        dedx, dedh = ctx.saved_tensors
+        g = g.detach()
+        gp = cl_scale(g, dedx) if ctx.needs_input_grad[0] else None
+        gb = None
+        if dedh is not None:
+            gb = cl_scale(g, dedh).to(device=ctx.h_meta[0], dtype=ctx.h_meta[1])
         return gp, gb, None
 
 

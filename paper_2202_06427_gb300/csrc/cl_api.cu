@@ -372,6 +372,26 @@ int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_p
                            c->partials, c->sums, nullptr, virial_dev, grad_box_dev, (cudaStream_t)stream);
 }
 
+int cl_energy_grad(const cl_list* cc, const double* scale_dev, double* energy_dev, double* grad_pos_dev,
+                   double* grad_box_dev, double* virial_dev, void* stream) {
+  if (!cc || !scale_dev || !energy_dev || (cc->n > 0 && !grad_pos_dev)) return CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->geo.dim == 3 && c->n > 0)
+    return clk::launch_hood(*c->full, *c->hood, c->work, 3, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
+                            c->partials, hood_blocks(c, 16), c->sums, energy_dev, virial_dev, grad_box_dev, s);
+  // 2D (and the empty list): the energy sweep, then the backward sweep
+  int e = clk::launch_scalar(*c->half, c->geo.dim, 1, c->partials, c->sums, energy_dev, s);
+  if (e) return e;
+  return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
+                           c->partials, c->sums, nullptr, virial_dev, grad_box_dev, s);
+}
+
+int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, long long count, void* stream) {
+  if (count < 0 || (count > 0 && (!scale_dev || !in_dev || !out_dev))) return CL_ERR_INVALID_ARG;
+  return clk::launch_scale(scale_dev, in_dev, out_dev, count, (cudaStream_t)stream);
+}
+
 int cl_query(const cl_list* c, int what, long long* value, void* stream) {
   if (!c || !value) return CL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;

@@ -47,12 +47,17 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kHome = 128;             // home particles of the fast path (one per thread)
 constexpr int kCap = 2560;             // staged neighbour entries (even)
 constexpr int kTab = 1 + kWarps * 32;  // stencil entries the fast path takes (32 per warp)
-constexpr int kRound = 4;              // neighbour cells a warp loads before using them
+constexpr int kRound = 8;              // neighbour cells a warp loads before using them
 // Padding entries sit at (kFar, kFar, kFar) and a missing second home particle
 // of a group at -kFar: far from everything and from each other (the stand-ins
 // of non-finite inputs lie within [1e15, 2e15) per axis), with squared
 // distances that stay finite in FP32.
 constexpr float kFar = 3e15f;
+
+// Per-CTA partials: mode 0: S6, E; mode 1: S6, X9; mode 2: E; mode 3: S6, X9, E.
+__host__ __device__ constexpr int hood_nv(int mode) {
+  return mode == 0 ? 1 + kVirN3 : (mode == 1 ? kVirN3 + 9 : (mode == 2 ? 1 : kVirN3 + 10));
+}
 
 struct Smem {
   float4 xy[kCap / 2];   // staged pairs (x_2k, x_2k+1, y_2k, y_2k+1)
@@ -65,7 +70,7 @@ struct Smem {
   float wmax[kWarps];
   int nf, nb;            // staged entries with T = 0 (from the front) and T != 0 (from the back)
   int item;
-  int next;
+  int pref;              // the cell after this one
 };
 
 __device__ __forceinline__ void unpack_off(int v, int& ox, int& oy, int& oz) {
@@ -97,46 +102,56 @@ struct HAcc {
 };
 
 // One home particle against the two staged neighbours (qx, qy, qz) of a lane.
-// (ix, iy, iz) = minus the home particle's coordinates in both halves.
-template <bool ENERGY, bool FORCE, bool VIR>
+// (ix, iy, iz) = minus the home particle's coordinates in both halves. Inside
+// the staged ball about a third of the candidates are within the cutoff, so
+// every warp-step has hits: the pair terms are computed for every candidate.
+// Both factors of the shifted-force terms change sign at the cutoff,
+//   fsn = y (y^2 - 1/rc^2) and t = 1 - r/rc (u = t^2 y),  y = 1/r,
+// so the cutoff is applied by clamping them at zero. With MASK (own cell) the
+// index masks m0, m1 and the cutoff test d2 < rc^2 zero y instead, which zeroes
+// both terms (and keeps the particle's pair with itself, y = inf, out).
+template <bool ENERGY, bool FORCE, bool VIR, bool MASK>
 __device__ __forceinline__ void hood_pair(float2 qx, float2 qy, float2 qz, float2 ix, float2 iy, float2 iz, bool m0,
                                           bool m1, float rc2, float irc, float irc2, HAcc& a, float2& e, float2* w) {
   const float2 dx = __fadd2_rn(qx, ix), dy = __fadd2_rn(qy, iy), dz = __fadd2_rn(qz, iz);
   float2 d2 = __fmul2_rn(dz, dz);
   d2 = __ffma2_rn(dy, dy, d2);
   d2 = __ffma2_rn(dx, dx, d2);
-  const bool h0 = m0 && d2.x < rc2;
-  const bool h1 = m1 && d2.y < rc2;
-  if (h0 || h1) {
-    const float2 y = rsqrt2(d2);
-    if (FORCE) {
-      float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
-      fsn.x = h0 ? fsn.x : 0.f;
-      fsn.y = h1 ? fsn.y : 0.f;
-      if (VIR) {
-        const float2 tx = __fmul2_rn(fsn, dx), ty = __fmul2_rn(fsn, dy), tz = __fmul2_rn(fsn, dz);
-        a.gx = __fadd2_rn(a.gx, tx);
-        a.gy = __fadd2_rn(a.gy, ty);
-        a.gz = __fadd2_rn(a.gz, tz);
-        w[0] = __ffma2_rn(tx, dx, w[0]);
-        w[1] = __ffma2_rn(tx, dy, w[1]);
-        w[2] = __ffma2_rn(tx, dz, w[2]);
-        w[3] = __ffma2_rn(ty, dy, w[3]);
-        w[4] = __ffma2_rn(ty, dz, w[4]);
-        w[5] = __ffma2_rn(tz, dz, w[5]);
-      } else {
-        a.gx = __ffma2_rn(fsn, dx, a.gx);
-        a.gy = __ffma2_rn(fsn, dy, a.gy);
-        a.gz = __ffma2_rn(fsn, dz, a.gz);
-      }
+  float2 y = rsqrt2(d2);
+  if (MASK) {
+    y.x = (m0 && d2.x < rc2) ? y.x : 0.f;
+    y.y = (m1 && d2.y < rc2) ? y.y : 0.f;
+  }
+  if (FORCE) {
+    float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
+    if (!MASK) {
+      fsn.x = fmaxf(fsn.x, 0.f);
+      fsn.y = fmaxf(fsn.y, 0.f);
     }
-    if (ENERGY) {
-      const float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-irc), f2(1.0f));
-      float2 u = __fmul2_rn(__fmul2_rn(t, t), y);
-      u.x = h0 ? u.x : 0.f;
-      u.y = h1 ? u.y : 0.f;
-      e = __fadd2_rn(e, u);
+    if (VIR) {
+      const float2 tx = __fmul2_rn(fsn, dx), ty = __fmul2_rn(fsn, dy), tz = __fmul2_rn(fsn, dz);
+      a.gx = __fadd2_rn(a.gx, tx);
+      a.gy = __fadd2_rn(a.gy, ty);
+      a.gz = __fadd2_rn(a.gz, tz);
+      w[0] = __ffma2_rn(tx, dx, w[0]);
+      w[1] = __ffma2_rn(tx, dy, w[1]);
+      w[2] = __ffma2_rn(tx, dz, w[2]);
+      w[3] = __ffma2_rn(ty, dy, w[3]);
+      w[4] = __ffma2_rn(ty, dz, w[4]);
+      w[5] = __ffma2_rn(tz, dz, w[5]);
+    } else {
+      a.gx = __ffma2_rn(fsn, dx, a.gx);
+      a.gy = __ffma2_rn(fsn, dy, a.gy);
+      a.gz = __ffma2_rn(fsn, dz, a.gz);
     }
+  }
+  if (ENERGY) {
+    float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-irc), f2(1.0f));
+    if (!MASK) {
+      t.x = fmaxf(t.x, 0.f);
+      t.y = fmaxf(t.y, 0.f);
+    }
+    e = __ffma2_rn(__fmul2_rn(t, t), y, e);
   }
 }
 
@@ -151,8 +166,8 @@ __device__ __forceinline__ void hood_scan(const float4* __restrict__ xy, const f
     const float4 q = xy[k];
     const float2 z = zz[k];
     const float2 qx = make_float2(q.x, q.y), qy = make_float2(q.z, q.w);
-    hood_pair<ENERGY, FORCE, VIR>(qx, qy, z, I[0], I[1], I[2], true, true, rc2, irc, irc2, a0, e, w);
-    hood_pair<ENERGY, FORCE, VIR>(qx, qy, z, I[3], I[4], I[5], true, true, rc2, irc, irc2, a1, e, w);
+    hood_pair<ENERGY, FORCE, VIR, false>(qx, qy, z, I[0], I[1], I[2], true, true, rc2, irc, irc2, a0, e, w);
+    hood_pair<ENERGY, FORCE, VIR, false>(qx, qy, z, I[3], I[4], I[5], true, true, rc2, irc, irc2, a1, e, w);
   }
 }
 
@@ -170,8 +185,8 @@ __device__ __forceinline__ void hood_own(const float4* __restrict__ xy, const fl
     const int e0 = 2 * k, e1 = 2 * k + 1;
     const bool m00 = HALF ? e0 > t0 : e0 != t0, m01 = HALF ? e1 > t0 : e1 != t0;
     const bool m10 = HALF ? e0 > t1 : e0 != t1, m11 = HALF ? e1 > t1 : e1 != t1;
-    hood_pair<ENERGY, FORCE, false>(qx, qy, z, I[0], I[1], I[2], m00, m01, rc2, irc, irc2, a0, e, nullptr);
-    hood_pair<ENERGY, FORCE, false>(qx, qy, z, I[3], I[4], I[5], m10, m11, rc2, irc, irc2, a1, e, nullptr);
+    hood_pair<ENERGY, FORCE, false, true>(qx, qy, z, I[0], I[1], I[2], m00, m01, rc2, irc, irc2, a0, e, nullptr);
+    hood_pair<ENERGY, FORCE, false, true>(qx, qy, z, I[3], I[4], I[5], m10, m11, rc2, irc, irc2, a1, e, nullptr);
   }
 }
 
@@ -206,58 +221,123 @@ __device__ __forceinline__ OffInfo off_info(const SweepArgs& A, const Smem& S, i
   return f;
 }
 
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// L1 prefetch of the cell ranges (cell_start pairs) that stencil entry k of cell
+// h reads, and of the cell's own range.
+__device__ __forceinline__ void prefetch_ranges(const SweepArgs& A, const Smem& S, int h, int k) {
+  const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
+  if (k == 1) prefetch_l1(A.cell_start + h);
+  if (k < A.noff && k < kTab) {
+    int ox, oy, oz;
+    unpack_off(__float_as_int(S.otab[k].w), ox, oy, oz);
+    int x2 = (cx + ox) % A.nx, y2 = (cy + oy) % A.ny, z2 = (cz + oz) % A.nz;
+    x2 += x2 < 0 ? A.nx : 0;
+    y2 += y2 < 0 ? A.ny : 0;
+    z2 += z2 < 0 ? A.nz : 0;
+    prefetch_l1(A.cell_start + x2 + A.nx * (y2 + A.ny * z2));
+  }
+}
+
 // Staging by one warp of its stencil entries 1 + warp + kWarps m, m < nmine
 // (lane m holds entry m's OffInfo). Lanes take consecutive particles of a
-// neighbour cell (coalesced loads); kRound cells are loaded before any is
-// used. Kept particles are compacted with a ballot: T = 0 entries from the
-// front of the buffer, T != 0 entries from the back. Writes stay in bounds;
+// neighbour cell (coalesced loads); the first 32 particles of kRound cells are
+// loaded before any is used. Kept particles are compacted with ballots, T = 0
+// entries from the front of the buffer and T != 0 entries from the back, with
+// one shared-memory atomic per segment and round. Writes stay in bounds;
 // overflow (nf + nb + 2 > kCap) is detected afterwards.
-__device__ __forceinline__ void stage_group(Smem& S, float4 q, float sx, float sy, float sz, int seg, float top2) {
-  const int lane = threadIdx.x & 31;
+__device__ __forceinline__ void stage_put(Smem& S, int e, float x, float y, float z) {
+  if (e >= 0 && e < kCap) {
+    // entry e of the pair layout: x at 2e - (e & 1), y two floats later, z at e
+    float* const xyf = reinterpret_cast<float*>(S.xy);
+    const int ix = 2 * e - (e & 1);
+    xyf[ix] = x;
+    xyf[ix + 2] = y;
+    reinterpret_cast<float*>(S.zz)[e] = z;
+  }
+}
+
+// One 32-particle group of a cell, compacted on its own (cells of more than 32).
+__device__ __forceinline__ void stage_group(Smem& S, float4 q, float sx, float sy, float sz, int seg, float top2,
+                                            unsigned lt) {
   const float x = q.x + sx, y = q.y + sy, z = q.z + sz;
-  const float r2 = fmaf(x, x, fmaf(y, y, z * z));
-  const bool keep = r2 < top2;
+  const bool keep = fmaf(x, x, fmaf(y, y, z * z)) < top2;
   const unsigned m = __ballot_sync(0xffffffffu, keep);
   if (!m) return;
   int base = 0;
-  if (lane == 0) base = atomicAdd(seg ? &S.nb : &S.nf, __popc(m));
+  if (lt == 0u) base = atomicAdd(seg ? &S.nb : &S.nf, __popc(m));
   base = __shfl_sync(0xffffffffu, base, 0);
   if (keep) {
-    const int r = base + __popc(m & ((1u << lane) - 1u));
-    const int e = seg ? kCap - 1 - r : r;
-    if (e >= 0 && e < kCap) {
-      float* const xyf = reinterpret_cast<float*>(S.xy);
-      float* const zzf = reinterpret_cast<float*>(S.zz);
-      xyf[(e >> 1) * 4 + (e & 1)] = x;
-      xyf[(e >> 1) * 4 + 2 + (e & 1)] = y;
-      zzf[(e >> 1) * 2 + (e & 1)] = z;
-    }
+    const int r = base + __popc(m & lt);
+    stage_put(S, seg ? kCap - 1 - r : r, x, y, z);
   }
 }
 
 __device__ __forceinline__ void stage_warp(const SweepArgs& A, Smem& S, const OffInfo& mine, int nmine, float top2) {
   const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
   for (int m0 = 0; m0 < nmine; m0 += kRound) {
     float4 q[kRound];
-    int j0[kRound], j1[kRound];
 #pragma unroll
     for (int r = 0; r < kRound; ++r) {
-      j0[r] = __shfl_sync(0xffffffffu, mine.j0, (m0 + r) & 31);
-      j1[r] = __shfl_sync(0xffffffffu, mine.j1, (m0 + r) & 31);
-      if (m0 + r >= nmine) j1[r] = j0[r];
-      const int j = j0[r] + lane;
-      q[r] = j < j1[r] ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f);
+      const int src = (m0 + r) & 31;
+      const int j0 = __shfl_sync(0xffffffffu, mine.j0, src);
+      int j1 = __shfl_sync(0xffffffffu, mine.j1, src);
+      if (m0 + r >= nmine) j1 = j0;
+      const int j = j0 + lane;
+      q[r] = j < j1 ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f);
     }
+    // ballots of the round, then one atomic per segment
+    unsigned m[kRound];
+    int seg[kRound];
+    int nF = 0, nB = 0;
 #pragma unroll
     for (int r = 0; r < kRound; ++r) {
-      const float sx = __shfl_sync(0xffffffffu, mine.sx, (m0 + r) & 31);
-      const float sy = __shfl_sync(0xffffffffu, mine.sy, (m0 + r) & 31);
-      const float sz = __shfl_sync(0xffffffffu, mine.sz, (m0 + r) & 31);
-      const int seg = __shfl_sync(0xffffffffu, mine.seg, (m0 + r) & 31);
-      stage_group(S, q[r], sx, sy, sz, seg, top2);
-      for (int jb = j0[r] + 32; jb < j1[r]; jb += 32) {
+      const int src = (m0 + r) & 31;
+      const float x = q[r].x + __shfl_sync(0xffffffffu, mine.sx, src);
+      const float y = q[r].y + __shfl_sync(0xffffffffu, mine.sy, src);
+      const float z = q[r].z + __shfl_sync(0xffffffffu, mine.sz, src);
+      seg[r] = __shfl_sync(0xffffffffu, mine.seg, src);
+      m[r] = __ballot_sync(0xffffffffu, fmaf(x, x, fmaf(y, y, z * z)) < top2);
+      q[r].x = x;
+      q[r].y = y;
+      q[r].z = z;
+      if (seg[r]) nB += __popc(m[r]);
+      else nF += __popc(m[r]);
+    }
+    int bF = 0, bB = 0;
+    if (lane == 0) {
+      if (nF) bF = atomicAdd(&S.nf, nF);
+      if (nB) bB = atomicAdd(&S.nb, nB);
+    }
+    bF = __shfl_sync(0xffffffffu, bF, 0);
+    bB = __shfl_sync(0xffffffffu, bB, 0);
+#pragma unroll
+    for (int r = 0; r < kRound; ++r) {
+      if ((m[r] >> lane) & 1u) {
+        const int rk = __popc(m[r] & lt);
+        stage_put(S, seg[r] ? kCap - 1 - (bB + rk) : bF + rk, q[r].x, q[r].y, q[r].z);
+      }
+      if (seg[r]) bB += __popc(m[r]);
+      else bF += __popc(m[r]);
+    }
+    // the rest of cells with more than 32 particles
+#pragma unroll 1
+    for (int r = 0; r < kRound; ++r) {
+      const int src = (m0 + r) & 31;
+      const int j0 = __shfl_sync(0xffffffffu, mine.j0, src);
+      int j1 = __shfl_sync(0xffffffffu, mine.j1, src);
+      if (m0 + r >= nmine) j1 = j0;
+      if (j1 - j0 <= 32) continue;
+      const float sx = __shfl_sync(0xffffffffu, mine.sx, src);
+      const float sy = __shfl_sync(0xffffffffu, mine.sy, src);
+      const float sz = __shfl_sync(0xffffffffu, mine.sz, src);
+      const int sg = __shfl_sync(0xffffffffu, mine.seg, src);
+      for (int jb = j0 + 32; jb < j1; jb += 32) {
         const int j = jb + lane;
-        stage_group(S, j < j1[r] ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f), sx, sy, sz, seg, top2);
+        stage_group(S, j < j1 ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f), sx, sy, sz, sg, top2, lt);
       }
     }
   }
@@ -344,7 +424,7 @@ struct ThreadOut {
 template <int MODE>
 __device__ __forceinline__ void hood_particle_out(ThreadOut& T, int i, float px, float py, float pz, const float* c,
                                                   float gx, float gy, float gz, float ax, float ay, float az,
-                                                  float* __restrict__ forces, double* __restrict__ grad, double g,
+                                                  float* __restrict__ forces, double* __restrict__ grad, float g,
                                                   const double* __restrict__ pos) {
   const float X[3] = {c[0] + px, c[1] + py, c[2] + pz};
   const float A[3] = {ax, ay, az};
@@ -356,12 +436,12 @@ __device__ __forceinline__ void hood_particle_out(ThreadOut& T, int i, float px,
   T.v[4] -= X[1] * A[2] + X[2] * A[1];
   T.v[5] -= 2.f * X[2] * A[2];
   const float F[3] = {-gx, -gy, -gz};
-  if (MODE == 0) {
+  if (MODE == 0 || MODE == 2) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) forces[(size_t)i * 3 + a] = F[a];
   } else {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = -g * (double)F[a];
+    for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = (double)(-g * F[a]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       const float xa = (float)pos[(size_t)i * 3 + a];
@@ -374,7 +454,7 @@ __device__ __forceinline__ void hood_particle_out(ThreadOut& T, int i, float px,
 template <int MODE>
 __device__ void hood_fallback(const SweepArgs& A, const HoodArgs& H, int hs, int nh, int cx, int cy, int cz,
                               const float* cc, ThreadOut& T, float* __restrict__ forces, double* __restrict__ grad,
-                              double g, const double* __restrict__ pos) {
+                              float g, const double* __restrict__ pos) {
   constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1;
   RedFallback<ENERGY, FORCE> red;
   red.irc = A.irc;
@@ -414,17 +494,19 @@ __device__ void hood_fallback(const SweepArgs& A, const HoodArgs& H, int hs, int
 }
 
 // MODE 0: energy, forces, virial (full shell). MODE 1: backward: grad_pos, X,
-// virial (full shell). MODE 2: energy (half shell).
+// virial (full shell). MODE 2: energy (half shell). MODE 3: energy and the
+// backward outputs in one full-shell sweep.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ SweepArgs A, const __grid_constant__ HoodArgs H,
                                                       float* __restrict__ forces, double* __restrict__ grad,
                                                       const double* __restrict__ gE, const double* __restrict__ pos,
                                                       double* __restrict__ partials) {
   constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1, HALF = MODE == 2;
+  constexpr bool GRAD = MODE == 1 || MODE == 3;
   extern __shared__ __align__(16) unsigned char smraw[];
   Smem& S = *reinterpret_cast<Smem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double g = (MODE == 1) ? *gE : 0.0;
+  const float g = GRAD ? (float)*gE : 0.f;
   ThreadOut T;
   T.es = T.ec = 0.f;
 #pragma unroll
@@ -440,27 +522,40 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     const Off& o = A.off[k];
     S.otab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[HALF ? 1 : 0][k]));
   }
-  if (tid == 0) S.next = atomicAdd(H.work, 1);
+  // Work items come from an atomic counter two cells ahead: thread 0 keeps the
+  // indices in registers, so the atomic's latency overlaps whole cells, and
+  // every thread prefetches into L1 the cell ranges it will read for the next
+  // cell while this one is swept.
+  int next1 = 0, next2 = 0;
+  if (tid == 0) {
+    next1 = atomicAdd(H.work, 1);
+    next2 = atomicAdd(H.work, 1);
+  }
 
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      S.item = S.next;
+      S.item = next1;
+      S.pref = next2;
       S.nf = 0;
       S.nb = 0;
     }
     __syncthreads();
     const int h = S.item;
     if (h >= H.ncells) break;
+    if (tid == 0) {
+      next1 = next2;
+      next2 = atomicAdd(H.work, 1);
+    }
     const int hs = A.cell_start[h];
     const int nh = A.cell_start[h + 1] - hs;
-    if (tid == 0) S.next = atomicAdd(H.work, 1);  // read at the top of the next iteration
+    if (S.pref < H.ncells) prefetch_ranges(A, S, S.pref, 1 + warp + kWarps * lane);
     if (nh == 0) continue;
     const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
-    float cc[3];  // centre of the home cell (wrapped absolute frame)
+    float cc[3];  // centre of the home cell (wrapped absolute frame), FP32
 #pragma unroll
     for (int a = 0; a < 3; ++a)
-      cc[a] = (float)((cx + 0.5) * H.g[a] + (cy + 0.5) * H.g[3 + a] + (cz + 0.5) * H.g[6 + a]);
+      cc[a] = fmaf((float)cx + 0.5f, H.gf[a], fmaf((float)cy + 0.5f, H.gf[3 + a], ((float)cz + 0.5f) * H.gf[6 + a]));
     if (nh > kHome || !table) {
       hood_fallback<MODE>(A, H, hs, nh, cx, cy, cz, cc, T, forces, grad, g, pos);
       continue;
@@ -472,6 +567,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
       const float4 hq = A.xs[hs + tid];
       d = fminf(sqrtf(fmaf(hq.x, hq.x, fmaf(hq.y, hq.y, hq.z * hq.z))), H.hd);
       S.hid[tid] = __float_as_int(hq.w);
+      if (GRAD) prefetch_l1(pos + (size_t)__float_as_int(hq.w) * 3);
       oxyf[(tid >> 1) * 4 + (tid & 1)] = hq.x;
       oxyf[(tid >> 1) * 4 + 2 + (tid & 1)] = hq.y;
       ozzf[(tid >> 1) * 2 + (tid & 1)] = hq.z;
@@ -588,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   }
 
   // per-CTA partials in the layout of the other sweeps
-  constexpr int NV = (MODE == 0) ? 1 + kVirN3 : (MODE == 1 ? kVirN3 + 9 : 1);
+  constexpr int NV = hood_nv(MODE);
   double v[NV];
   if (MODE == 2) {
     v[0] = (double)T.es - (double)T.ec;
@@ -597,10 +693,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
 #pragma unroll
     for (int k = 0; k < 6; ++k) v[k] = -(double)T.v[k];
     if (MODE == 0) v[kVirN3] = 0.5 * ((double)T.es - (double)T.ec);
-    if (MODE == 1) {
+    if (GRAD) {
 #pragma unroll
       for (int k = 0; k < 9; ++k) v[kVirN3 + k] = (double)T.x[k];
     }
+    if (MODE == 3) v[kVirN3 + 9] = 0.5 * ((double)T.es - (double)T.ec);
   }
   block_sum_store<NV>(v, partials + (size_t)blockIdx.x * NV);
 }
@@ -608,8 +705,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
 }  // namespace
 
 int hood_grid(int mode) {
-  static int cached[3] = {0, 0, 0};
-  if (mode < 0 || mode > 2) return 0;
+  static int cached[4] = {0, 0, 0, 0};
+  if (mode < 0 || mode > 3) return 0;
   if (cached[mode]) return cached[mode];
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -617,7 +714,8 @@ int hood_grid(int mode) {
   cudaError_t e;
   if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<0>, kThreads, sizeof(Smem));
   else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<1>, kThreads, sizeof(Smem));
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<2>, kThreads, sizeof(Smem));
+  else if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<2>, kThreads, sizeof(Smem));
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<3>, kThreads, sizeof(Smem));
   if (e != cudaSuccess || per < 1) return 0;
   cached[mode] = sms * per;
   return cached[mode];
@@ -641,7 +739,10 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
     if (d > hd) hd = d;
   }
   for (int k = 0; k < 3; ++k)
-    for (int a = 0; a < 3; ++a) H->g[k * 3 + a] = geo.h[k * 3 + a] / geo.n[k];
+    for (int a = 0; a < 3; ++a) {
+      H->g[k * 3 + a] = geo.h[k * 3 + a] / geo.n[k];
+      H->gf[k * 3 + a] = (float)H->g[k * 3 + a];
+    }
   const double eps = 1e-4 * (geo.rc + hd);
   H->rc = (float)geo.rc;
   H->hd = (float)(hd * (1.0 + 1e-6));
@@ -653,7 +754,7 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
 int launch_hood(const SweepArgs& A, const HoodArgs& Hin, int* work, int mode, const double* hinv, float* forces,
                 double* grad, const double* gE, const double* pos, double* partials, int max_blocks, double* sums,
                 double* energy, double* virial, double* gradbox, cudaStream_t s) {
-  const int NV = mode == 0 ? 1 + kVirN3 : (mode == 1 ? kVirN3 + 9 : 1);
+  const int NV = hood_nv(mode);
   int nb = hood_grid(mode);
   if (nb <= 0) return CL_ERR_CUDA;
   if (nb > Hin.ncells) nb = Hin.ncells;
@@ -665,9 +766,10 @@ int launch_hood(const SweepArgs& A, const HoodArgs& Hin, int* work, int mode, co
   const size_t smem = sizeof(Smem);
   if (mode == 0) k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
   else if (mode == 1) k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
-  else k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
-  return finish_reduction(mode == 2 ? 1 : (mode == 0 ? 2 : 3), 3, hinv, nb, NV, partials, sums, energy, virial,
-                          gradbox, gE, s);
+  else if (mode == 2) k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+  else k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+  const int final_mode = mode == 2 ? 1 : (mode == 0 ? 2 : (mode == 1 ? 3 : 4));
+  return finish_reduction(final_mode, 3, hinv, nb, NV, partials, sums, energy, virial, gradbox, gE, s);
 }
 
 }  // namespace clk

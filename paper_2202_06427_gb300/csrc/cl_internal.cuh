@@ -120,7 +120,9 @@ int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, floa
                  double* virial, double* gradbox, cudaStream_t s);
 int launch_candidates(const SweepArgs& A, long long ncells, unsigned long long* out, cudaStream_t s);
 // Sums per-CTA partials[nblocks][nv] and writes the caller's outputs. final_mode:
-// 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward.
+// 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward, 4 energy
+// and backward (partials S6, X9, E).
+int launch_scale(const double* g, const double* in, double* out, long long count, cudaStream_t s);
 int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, int nv, const double* partials,
                      double* sums, double* scalar, double* virial, double* gradbox, const double* gE,
                      cudaStream_t s);
@@ -129,6 +131,7 @@ int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, i
 struct HoodArgs {
   int opk[2][kMaxOff];  // unwrapped stencil offsets (see build_stencil): [0] full, [1] half stencil
   double g[9];        // cell edge vectors G_k = H_k / n_k (rows), FP64
+  float gf[9];        // the same, FP32
   float rc;
   float hd;           // largest distance of a cell point from the cell centre
   float eps;          // rounding margin of the staging radius
@@ -138,7 +141,8 @@ struct HoodArgs {
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
                    HoodArgs* H);
 size_t hood_smem_bytes();
-// mode 0: energy, forces, virial; 1: backward; 2: energy (half shell, A = half stencil).
+// mode 0: energy, forces, virial; 1: backward; 2: energy (half shell, A = half
+// stencil); 3: energy and the backward outputs.
 int launch_hood(const SweepArgs& A, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
                 double* grad, const double* gE, const double* pos, double* partials, int max_blocks, double* sums,
                 double* energy, double* virial, double* gradbox, cudaStream_t s);

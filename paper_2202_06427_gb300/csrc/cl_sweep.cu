@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(256) k_final_sum(const double* __restrict__ pa
 }
 
 struct FinalArgs {
-  int mode;          // 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward
+  int mode;          // 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward, 4 energy + backward
   int dim;
   double hinv[9];    // 3x3
   double* out_scalar;
@@ -243,6 +243,7 @@ __global__ void k_final_assemble(const __grid_constant__ FinalArgs F, const doub
     if (F.out_scalar) *F.out_scalar = sums[NW];
     return;
   }
+  if (F.mode == 4 && F.out_scalar) *F.out_scalar = sums[NW + d * d];
   // dE/dH at fixed positions = H^-T (X - W), X = sum_i x_i (x) F_i
   const double g = *F.gE;
   if (F.out_gradbox) {
@@ -270,6 +271,21 @@ int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, i
   F.out_gradbox = gradbox;
   F.gE = gE;
   k_final_assemble<<<1, 32, 0, s>>>(F, sums);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+__global__ void __launch_bounds__(256) k_scale(const double* __restrict__ g, const double* __restrict__ in,
+                                              double* __restrict__ out, long long count) {
+  const double s = *g;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count; k += (long long)gridDim.x * blockDim.x)
+    out[k] = s * in[k];
+}
+
+int launch_scale(const double* g, const double* in, double* out, long long count, cudaStream_t s) {
+  if (count <= 0) return CL_OK;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_scale<<<(int)blocks, 256, 0, s>>>(g, in, out, count);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 

@@ -82,6 +82,16 @@ def test_small_all_reductions(cuda_ok, dim, tric, lcell, rc_frac):
     check_forces(gp.cpu().numpy(), -0.75 * ref["forces"])
     check_matrix(gb.cpu().numpy(), 0.75 * ref["dedh"], TOL_GB)
     check_matrix(vir.cpu().numpy(), ref["virial"], TOL_W)
+    # energy and gradient in one sweep, then the chain rule by cl_scale
+    e1, dedx, dedh, vir1 = P.cl_energy_grad(cl, want_virial=True)
+    check_energy(e1.item(), ref["energy"])
+    check_forces(dedx.cpu().numpy(), -ref["forces"])
+    check_matrix(dedh.cpu().numpy(), ref["dedh"], TOL_GB)
+    check_matrix(vir1.cpu().numpy(), ref["virial"], TOL_W)
+    check_forces(P.cl_scale(g, dedx).cpu().numpy(), -0.75 * ref["forces"])
+    e2, gp2, _, _ = P.cl_energy_grad(cl, g, want_box=False)
+    check_energy(e2.item(), ref["energy"])
+    check_forces(gp2.cpu().numpy(), -0.75 * ref["forces"])
     assert P.cl_status(cl) == 0
 
 
@@ -129,6 +139,12 @@ def test_workload_lattice_1m(cuda_ok):
     efv = P.cl_map(cl, "energy_forces_virial")
     check_forces(efv["forces"].cpu().numpy(), ref["forces"])
     check_energy(efv["energy"].item(), ref["energy"])
+    del efv
+    e1, dedx, dedh, vir1 = P.cl_energy_grad(cl, want_virial=True)
+    check_energy(e1.item(), ref["energy"])
+    check_forces(dedx.cpu().numpy(), -ref["forces"])
+    check_matrix(dedh.cpu().numpy(), ref["dedh"], TOL_GB)
+    check_matrix(vir1.cpu().numpy(), ref["virial"], TOL_W)
 
 
 def test_empty_and_tiny(cuda_ok):
@@ -145,6 +161,10 @@ def test_empty_and_tiny(cuda_ok):
         assert int(P.cl_map(cl, "hist", nbins=4)["hist"].sum().item()) == 0
         gp, gb, vir = P.cl_backward(cl, torch.ones(1, dtype=torch.float64, device="cuda"))
         assert gp.shape == (n, 3) and float(gb.abs().max()) == 0.0
+        e1, dedx, dedh, _ = P.cl_energy_grad(cl)
+        assert e1.item() == 0.0 and dedx.shape == (n, 3) and float(dedh.abs().max()) == 0.0
+        if n:
+            assert float(dedx.abs().max()) == 0.0
     # two particles across the periodic boundary: distance 1.5 through the face
     x = np.array([[0.25, 5.0, 5.0], [8.75, 5.0, 5.0]])
     cl = P.cl_build(torch.from_numpy(x).cuda(), h, 3.0, 2)
@@ -240,3 +260,10 @@ def test_workload_clustered_16m(cuda_ok):
     check_forces(gp[torch.from_numpy(sample).cuda()].cpu().numpy(), -f_ref)
     check_matrix(vir.cpu().numpy(), ref["virial"], TOL_W)
     check_matrix(gb.cpu().numpy(), ref["dedh"], TOL_GB)
+    del gp
+    cl2 = P.cl_build(pos, h, rc, 2)  # the launch configuration of the benchmark
+    e1, dedx, dedh, vir1 = P.cl_energy_grad(cl2, want_virial=True)
+    check_energy(e1.item(), ref["energy"])
+    check_forces(dedx[torch.from_numpy(sample).cuda()].cpu().numpy(), -f_ref)
+    check_matrix(vir1.cpu().numpy(), ref["virial"], TOL_W)
+    check_matrix(dedh.cpu().numpy(), ref["dedh"], TOL_GB)
