@@ -2,11 +2,13 @@
 1M particles.
 
 One step is one pass of the whole hot path over the 1M jittered-lattice
-workload (3D, 100^3 sites at density 0.1, box 215.44, rc 12):
+workload (3D, 100^3 sites at density 0.1, box 215.44, rc 12), the forward
+and backward of a differentiable energy:
   cell binning (FP64 wrap, fractional cell, counting sort, prefix sum, scatter)
-  -> half-shell sweep with the shifted-force energy fused in (forward)
-  -> full-shell backward sweep: forces (dE/dx) and virial / box gradient
-  -> fixed-order FP64 reduction of the per-CTA partials.
+  -> neighbourhood sweep: shifted-force energy, dE/dx (forces) and dE/dH
+     (virial) fused in one pass (cl_energy_grad)
+  -> fixed-order FP64 reduction of the per-CTA partials
+  -> chain rule by the upstream gradient (cl_scale) for positions and box.
 value = pairs within the cutoff per step * ranks / time per step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -31,13 +33,14 @@ METRIC = "pairs-within-cutoff/sec at 1M particles"
 UNIT = "pairs/s"
 WORKLOAD = "w1_lattice_1m"
 LCELL = 2
-# FP32 arithmetic per pair test and per pair in the cutoff (FMA = 2 FLOP, 1/r = 1):
-FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j + S - x_i|^2
-FLOP_PER_HIT_BACKWARD = 22  # 1/r (1), u'(r)/r = y (1/rc^2 - y^2) (3), force 3 mul + 3 add, virial 6 fma (12)
-FLOP_PER_HIT_ENERGY = 7     # 1/r (1), r (1), 1 - r/rc (2), (..)^2 / r (2), accumulate (1)
-# DRAM bytes per launch of the backward sweep (k_sweep2_force<1>, 1M lattice, lcell 2), from
-# ncu --set full: dram__bytes_read.sum + dram__bytes_write.sum = 79.06 MB + 7.20 MB.
-BACKWARD_DRAM_BYTES = 86.25e6
+# FP32 arithmetic per candidate pair and per ordered pair-image within the cutoff
+# (FMA = 2 FLOP, 1/r = 1) of the fused energy-and-gradient sweep:
+FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j' - x_i|^2
+FLOP_PER_HIT_FUSED = 16     # 1/r (1); fsn = y (y^2 - 1/rc^2) (3); force 3 fma (6); r = d2 y (1),
+                            # t = 1 - r/rc (2), t^2 (1), e += t^2 y (2)
+# DRAM bytes per launch of the fused sweep (k_hood<3>, 1M lattice, lcell 2), from
+# ncu --set full: dram__bytes_read.sum + dram__bytes_write.sum = 40.77 MB + 1.22 MB.
+SWEEP_DRAM_BYTES = 41.99e6
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -208,16 +211,23 @@ def run_ours(args, rank, world, local):
     pairs = int(P.cl_map(cl, "count")["count"].item())
     cand_half = P.cl_query(cl, "candidates")
     g = torch.ones(1, dtype=torch.float64, device=dev)
+    out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float64, device=dev),
+           torch.empty((3, 3), dtype=torch.float64, device=dev), None)
+    grad_x = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    grad_h = torch.empty((3, 3), dtype=torch.float64, device=dev)
+    P.cl_energy_grad(cl, out=out)
+    cand = P.cl_query(cl, "sweep_candidates")  # candidate pairs the fused sweep evaluates
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     def step(ev=None):
         P.cl_update(cl, x)
-        P.cl_map(cl, "energy")
         if ev is not None:
             ev[0].record(stream)
-        P.cl_backward(cl, g)
+        P.cl_energy_grad(cl, out=out)  # forward: energy, dE/dx, dE/dH in one sweep
         if ev is not None:
             ev[1].record(stream)
+        P.cl_scale(g, out[1], grad_x)  # backward: dL/dx = dL/dE dE/dx
+        P.cl_scale(g, out[2], grad_h)
 
     for _ in range(args.warmup):
         step()
@@ -244,29 +254,30 @@ def run_ours(args, rank, world, local):
     kms = sum(kern_ms) / len(kern_ms)
     value = pairs * world / (ms / 1e3)
 
-    # roofline of the dominant kernel (full-shell backward sweep)
+    # roofline of the dominant kernel (the fused energy-and-gradient sweep)
     clocks = sampler.summary()
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     max_mhz = clocks["sm_max_mhz"] or 2070.0
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    flop = 2 * cand_half * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_BACKWARD
+    flop = cand * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_FUSED
     achieved = flop / (kms / 1e3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": BACKWARD_DRAM_BYTES,
-                "kernel": "k_sweep2_force<1> (cl_backward: full-shell force and virial sweep)",
-                "kernel_ms": kms, "flop_per_launch": flop,
+                "frac": achieved / peak_tflops, "traffic": SWEEP_DRAM_BYTES,
+                "kernel": "k_hood<3> (cl_energy_grad: neighbourhood sweep, energy + forces + box gradient)",
+                "kernel_ms": kms, "flop_per_launch": flop, "candidates_per_launch": cand,
                 "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (of max clock, not measured)" % (sms, max_mhz)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "box": 215.443469, "cutoff": rc, "lcell": LCELL,
-                       "pairs_per_step": pairs, "candidates_half_shell": cand_half,
-                       "step": "binning + energy sweep (forward) + force/virial sweep (backward)",
+                       "pairs_per_step": pairs, "candidates_sweep": cand, "candidates_half_shell_stencil": cand_half,
+                       "step": "binning + fused energy/forces/box-gradient sweep (forward) + chain rule (backward)",
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "gpu_launches": 12 * args.steps,  # bin, 3 scan, scatter, pair pack; energy sweep + 2 reduce; backward + 2
+            # bin, 3 scan, scatter, pair pack; cell list, sweep, per-particle companion, 2 reduce; 2 scale
+            "gpu_launches": 13 * args.steps,
             "clocks": clocks, "roofline": roofline}
 
     if not args.no_e2e:
@@ -369,14 +380,20 @@ def e2e(P, cl, w, dev, stream, pairs, args, world):
     g = torch.ones(1, dtype=torch.float64, device=dev)
     steps = max(3, min(args.steps, 50))
 
+    out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(host_x.shape, dtype=torch.float64, device=dev),
+           torch.empty((3, 3), dtype=torch.float64, device=dev), None)
+    gx = torch.empty(host_x.shape, dtype=torch.float64, device=dev)
+    gh = torch.empty((3, 3), dtype=torch.float64, device=dev)
+
     def one():
         x.copy_(host_x, non_blocking=True)
         P.cl_update(cl, x)
-        e = P.cl_map(cl, "energy")["energy"]
-        gp, gb, _ = P.cl_backward(cl, g, want_virial=False)
-        out_e.copy_(e, non_blocking=True)
-        out_g.copy_(gp, non_blocking=True)
-        out_b.copy_(gb, non_blocking=True)
+        P.cl_energy_grad(cl, out=out)
+        P.cl_scale(g, out[1], gx)
+        P.cl_scale(g, out[2], gh)
+        out_e.copy_(out[0], non_blocking=True)
+        out_g.copy_(gx, non_blocking=True)
+        out_b.copy_(gh, non_blocking=True)
 
     for _ in range(3):
         one()

@@ -171,6 +171,8 @@ int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, lon
 #define CL_INFO_STENCIL_FULL 10     /* offsets of the full stencil (forces, backward) */
 #define CL_INFO_CANDIDATES 11       /* candidate pairs the half-shell sweep tests (cell occupancy products) */
 #define CL_INFO_WORK_TILES 12       /* CTAs of 256 threads the particle sweeps launch (one thread per particle) */
+#define CL_INFO_SWEEP_CANDIDATES 13 /* candidate pairs the last 3D energy/force sweep evaluated (staged
+                                       neighbours x home particles, own cell included); reads a counter */
 int cl_query(const cl_list* cl, int what, long long* value, void* stream);
 
 /* Host-only box preparation, no GPU needed: for box, fills

@@ -177,19 +177,23 @@ def cl_backward(cl, grad_energy, want_box=True, want_virial=True, stream=None):
     return gp, gb, vir
 
 
-def cl_energy_grad(cl, scale=None, want_box=True, want_virial=False, stream=None):
+def cl_energy_grad(cl, scale=None, want_box=True, want_virial=False, stream=None, out=None):
     """Energy and scale * (dE/dx, dE/dH) in one sweep: (energy (1,), dE/dx (n, dim),
     dE/dH (dim, dim) or None, virial or None), float64 on the list's device.
-    scale: 1-element tensor (default 1)."""
+    scale: 1-element tensor (default 1). out: optional tuple of preallocated
+    (energy, dE/dx, dE/dH or None, virial or None) tensors to write into."""
     dev = cl.device
     if scale is None:
         g = torch.ones(1, dtype=torch.float64, device=dev)
     else:
         g = scale.to(device=dev, dtype=torch.float64).reshape(1).contiguous()
-    e = torch.empty(1, dtype=torch.float64, device=dev)
-    gp = torch.empty((cl.n, cl.dim), dtype=torch.float64, device=dev)
-    gb = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_box else None
-    vir = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_virial else None
+    if out is not None:
+        e, gp, gb, vir = out
+    else:
+        e = torch.empty(1, dtype=torch.float64, device=dev)
+        gp = torch.empty((cl.n, cl.dim), dtype=torch.float64, device=dev)
+        gb = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_box else None
+        vir = torch.empty((cl.dim, cl.dim), dtype=torch.float64, device=dev) if want_virial else None
     with torch.cuda.device(dev):
         L.check(L.lib().cl_energy_grad(cl.handle, _ptr(g), _ptr(e), _ptr(gp), _ptr(gb), _ptr(vir), _stream(stream)),
                 "cl_energy_grad")

@@ -21,6 +21,8 @@ struct cl_list {
   float2* zz2;
   int* counts;
   int* cell_start;
+  unsigned char* hflag;  // per cell: 1 when the neighbourhood sweep leaves it to the per-particle sweep
+  int* hlist;            // cells the neighbourhood sweep takes
   int* tile_sum;
   int* meta;
   double* partials;
@@ -61,9 +63,13 @@ void free_cells(cl_list* c) {
   cudaFree(c->counts);
   cudaFree(c->cell_start);
   cudaFree(c->tile_sum);
+  cudaFree(c->hflag);
+  cudaFree(c->hlist);
+  c->hlist = nullptr;
   c->counts = nullptr;
   c->cell_start = nullptr;
   c->tile_sum = nullptr;
+  c->hflag = nullptr;
 }
 
 void free_all(cl_list* c) {
@@ -97,13 +103,15 @@ int alloc_cells(cl_list* c, long long ncells) {
   if ((e = dev_alloc(&c->counts, (size_t)ncells, &b))) return e;
   if ((e = dev_alloc(&c->cell_start, (size_t)ncells + 1, &b))) return e;
   if ((e = dev_alloc(&c->tile_sum, (size_t)clk::scan_tiles_for(ncells), &b))) return e;
+  if ((e = dev_alloc(&c->hflag, (size_t)ncells, &b))) return e;
+  if ((e = dev_alloc(&c->hlist, (size_t)ncells, &b))) return e;
   c->ncells_alloc = ncells;
   c->bytes += b;
   return CL_OK;
 }
 
-// CTAs of the persistent neighbourhood sweep that the partials buffer holds at nv doubles each.
-int hood_blocks(const cl_list* c, int nv) { return clk::sweep_partials_needed(c->n) / nv; }
+// Partials (doubles) available to the neighbourhood sweep and its per-particle companion.
+long long hood_cap(const cl_list* c) { return clk::sweep_partials_needed(c->n); }
 
 void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
   A->xs = c->xs;
@@ -126,9 +134,11 @@ int set_geometry(cl_list* c, const cl_box* box) {
   if (e) return e;
   clk::Off* th = new (std::nothrow) clk::Off[2 * clk::kMaxOff];
   int* opk = new (std::nothrow) int[2 * clk::kMaxOff];
-  if (!th || !opk) {
+  clk::HoodArgs* hood = new (std::nothrow) clk::HoodArgs;
+  if (!th || !opk || !hood) {
     delete[] th;
     delete[] opk;
+    delete hood;
     return CL_ERR_OOM;
   }
   clk::Off* tf = th + clk::kMaxOff;
@@ -137,14 +147,17 @@ int set_geometry(cl_list* c, const cl_box* box) {
   if (nh < 0 || nf < 0) {
     delete[] th;
     delete[] opk;
+    delete hood;
     return nh < 0 ? nh : nf;
   }
-  if (g.dim == 3) clk::fill_hood_args(g, opk, nf, opk + clk::kMaxOff, nh, c->hood);
+  std::memset(hood, 0, sizeof(*hood));
+  if (g.dim == 3) clk::fill_hood_args(g, opk, nf, opk + clk::kMaxOff, nh, hood);
   delete[] opk;
   if (g.ncells != c->ncells_alloc) {
     free_cells(c);
     if ((e = alloc_cells(c, g.ncells))) {
       delete[] th;
+      delete hood;
       return e;
     }
   }
@@ -153,8 +166,13 @@ int set_geometry(cl_list* c, const cl_box* box) {
   if (cudaMemcpy(c->d_off_half, th, sizeof(clk::Off) * nh, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(c->d_off_full, tf, sizeof(clk::Off) * nf, cudaMemcpyHostToDevice) != cudaSuccess) {
     delete[] th;
+    delete hood;
     return CL_ERR_CUDA;
   }
+  *c->hood = *hood;
+  c->hood->flag = c->hflag;
+  c->hood->list = c->hlist;
+  delete hood;
   c->half->noff = nh;
   c->full->noff = nf;
   delete[] th;
@@ -295,7 +313,7 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
-  if (!e) e = dev_alloc(&c->work, 1, &b);
+  if (!e) e = dev_alloc(&c->work, 4, &b);  // [0] work counter, [1] list length, [2..3] candidate counter
   if (!e) e = dev_alloc(&c->u64, 8, &b);
   if (!e) e = dev_alloc(&c->d_off_half, (size_t)clk::kMaxOff, &b);
   if (!e) e = dev_alloc(&c->d_off_full, (size_t)clk::kMaxOff, &b);
@@ -339,13 +357,13 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       if (!r->energy) return CL_ERR_INVALID_ARG;
       if (dim == 3 && c->n > 0)
         return clk::launch_hood(*c->half, *c->hood, c->work, 2, c->geo.hinv, nullptr, nullptr, nullptr, nullptr,
-                                c->partials, hood_blocks(c, 1), c->sums, r->energy, nullptr, nullptr, s);
+                                c->partials, hood_cap(c), c->sums, r->energy, nullptr, nullptr, s);
       return clk::launch_scalar(*c->half, dim, 1, c->partials, c->sums, r->energy, s);
     case CL_RED_SF_ENERGY_FORCES_VIRIAL:
       if (!r->forces && c->n > 0) return CL_ERR_INVALID_ARG;
       if (dim == 3 && c->n > 0)
         return clk::launch_hood(*c->full, *c->hood, c->work, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr,
-                                c->partials, hood_blocks(c, 7), c->sums, r->energy, r->virial, nullptr, s);
+                                c->partials, hood_cap(c), c->sums, r->energy, r->virial, nullptr, s);
       return clk::launch_force(*c->full, dim, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr, c->partials,
                                c->sums, r->energy, r->virial, nullptr, s);
     case CL_RED_HIST: {
@@ -366,7 +384,7 @@ int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_p
   cl_list* c = const_cast<cl_list*>(cc);
   if (c->geo.dim == 3 && c->n > 0)
     return clk::launch_hood(*c->full, *c->hood, c->work, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev,
-                            c->pos, c->partials, hood_blocks(c, 15), c->sums, nullptr, virial_dev, grad_box_dev,
+                            c->pos, c->partials, hood_cap(c), c->sums, nullptr, virial_dev, grad_box_dev,
                             (cudaStream_t)stream);
   return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev, c->pos,
                            c->partials, c->sums, nullptr, virial_dev, grad_box_dev, (cudaStream_t)stream);
@@ -379,7 +397,7 @@ int cl_energy_grad(const cl_list* cc, const double* scale_dev, double* energy_de
   cudaStream_t s = (cudaStream_t)stream;
   if (c->geo.dim == 3 && c->n > 0)
     return clk::launch_hood(*c->full, *c->hood, c->work, 3, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
-                            c->partials, hood_blocks(c, 16), c->sums, energy_dev, virial_dev, grad_box_dev, s);
+                            c->partials, hood_cap(c), c->sums, energy_dev, virial_dev, grad_box_dev, s);
   // 2D (and the empty list): the energy sweep, then the backward sweep
   int e = clk::launch_scalar(*c->half, c->geo.dim, 1, c->partials, c->sums, energy_dev, s);
   if (e) return e;
@@ -412,6 +430,13 @@ int cl_query(const cl_list* c, int what, long long* value, void* stream) {
       if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
       if (cudaMemcpy(m, c->meta, sizeof(m), cudaMemcpyDeviceToHost) != cudaSuccess) return CL_ERR_CUDA;
       *value = what == CL_INFO_NONEMPTY ? m[1] : m[2];
+      return CL_OK;
+    }
+    case CL_INFO_SWEEP_CANDIDATES: {
+      unsigned long long v = 0;
+      if (cudaMemcpyAsync(&v, c->work + 2, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+      *value = (long long)v;
       return CL_OK;
     }
     case CL_INFO_CANDIDATES: {

@@ -30,9 +30,11 @@
 // growing from the far end of the buffer, and add fsn r (x) r directly. Every
 // path of this file computes the same per-particle share, so their sums agree.
 //
-// Home cells that do not fit (more than kHome particles, or more than kCap
-// staged neighbours) are swept by the CTA one thread per particle over the
-// stencil (hood_fallback), with the same per-particle virial share.
+// Home cells that do not pay for the staging (fewer than kMinHome particles) or
+// do not fit (more than kHome particles, or more than kCap staged neighbours)
+// are flagged and swept afterwards by a companion kernel,
+// one thread per particle over the stencil (k_hood_rest), with the same
+// per-particle virial share; both write per-CTA partials to one buffer.
 #include <cmath>
 #include <cstring>
 
@@ -45,6 +47,7 @@ namespace {
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
 constexpr int kHome = 128;             // home particles of the fast path (one per thread)
+constexpr int kMinHome = 8;            // fewer home particles: the per-particle companion is cheaper
 constexpr int kCap = 2560;             // staged neighbour entries (even)
 constexpr int kTab = 1 + kWarps * 32;  // stencil entries the fast path takes (32 per warp)
 constexpr int kRound = 8;              // neighbour cells a warp loads before using them
@@ -71,6 +74,7 @@ struct Smem {
   int nf, nb;            // staged entries with T = 0 (from the front) and T != 0 (from the back)
   int item;
   int pref;              // the cell after this one
+  unsigned long long ncand;  // candidate pairs this CTA evaluated
 };
 
 __device__ __forceinline__ void unpack_off(int v, int& ox, int& oy, int& oz) {
@@ -371,17 +375,21 @@ struct RedFallback {
       float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
       fsn.x = h0 ? fsn.x : 0.f;
       fsn.y = h1 ? fsn.y : 0.f;
-      const float2 tx = __fmul2_rn(fsn, dx), ty = __fmul2_rn(fsn, dy), tz = __fmul2_rn(fsn, dz);
-      a.gx = __fadd2_rn(a.gx, tx);
-      a.gy = __fadd2_rn(a.gy, ty);
-      a.gz = __fadd2_rn(a.gz, tz);
       if (a.wrap) {
+        const float2 tx = __fmul2_rn(fsn, dx), ty = __fmul2_rn(fsn, dy), tz = __fmul2_rn(fsn, dz);
+        a.gx = __fadd2_rn(a.gx, tx);
+        a.gy = __fadd2_rn(a.gy, ty);
+        a.gz = __fadd2_rn(a.gz, tz);
         a.w[0] = __ffma2_rn(tx, dx, a.w[0]);
         a.w[1] = __ffma2_rn(tx, dy, a.w[1]);
         a.w[2] = __ffma2_rn(tx, dz, a.w[2]);
         a.w[3] = __ffma2_rn(ty, dy, a.w[3]);
         a.w[4] = __ffma2_rn(ty, dz, a.w[4]);
         a.w[5] = __ffma2_rn(tz, dz, a.w[5]);
+      } else {
+        a.gx = __ffma2_rn(fsn, dx, a.gx);
+        a.gy = __ffma2_rn(fsn, dy, a.gy);
+        a.gz = __ffma2_rn(fsn, dz, a.gz);
       }
     }
     if (ENERGY) {
@@ -451,46 +459,136 @@ __device__ __forceinline__ void hood_particle_out(ThreadOut& T, int i, float px,
   }
 }
 
+// One particle p (sorted position) of cell (cx, cy, cz) over the stencil on
+// the shifted-pair arrays, with the same per-particle virial share as the
+// neighbourhood sweep. Returns the candidate pairs evaluated.
 template <int MODE>
-__device__ void hood_fallback(const SweepArgs& A, const HoodArgs& H, int hs, int nh, int cx, int cy, int cz,
-                              const float* cc, ThreadOut& T, float* __restrict__ forces, double* __restrict__ grad,
-                              float g, const double* __restrict__ pos) {
+__device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs& H, int p, int cx, int cy, int cz,
+                                             ThreadOut& T, float* __restrict__ forces, double* __restrict__ grad,
+                                             float g, const double* __restrict__ pos) {
   constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1;
+  unsigned long long ncand = 0;
   RedFallback<ENERGY, FORCE> red;
   red.irc = A.irc;
   red.irc2 = A.irc2;
-  for (int t = threadIdx.x; t < nh; t += kThreads) {
-    const int p = hs + t;
-    const float4 pi = A.xs[p];
-    typename RedFallback<ENERGY, FORCE>::Acc acc;
-    red.init(acc);
-    {
-      const int s0 = hs, s1 = hs + nh;
-      if (FORCE) scan_pairs(A.xy2, A.zz2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
-      scan_pairs(A.xy2, A.zz2, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
-      red.cell_done(acc);
-    }
-    for (int k = 1; k < A.noff; ++k) {
-      const Off& o = A.off[k];
-      const int c = stencil_cell(A, k, cx, cy, cz);
-      if (FORCE) {
-        int ox, oy, oz;
-        unpack_off(H.opk[0][k], ox, oy, oz);
-        acc.wrap = (cx + ox < 0) || (cx + ox >= A.nx) || (cy + oy < 0) || (cy + oy >= A.ny) || (cz + oz < 0) ||
-                   (cz + oz >= A.nz);
-      }
-      scan_pairs(A.xy2, A.zz2, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
-                 red, acc);
-      red.cell_done(acc);
-    }
-    if (ENERGY) T.add_energy(acc.e.x + acc.e.y);
-    if (FORCE) {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) T.v[k] += acc.w[k].x + acc.w[k].y;
-      hood_particle_out<MODE>(T, __float_as_int(pi.w), pi.x, pi.y, pi.z, cc, acc.tx, acc.ty, acc.tz, acc.ax, acc.ay,
-                              acc.az, forces, grad, g, pos);
-    }
+  const float4 pi = A.xs[p];
+  typename RedFallback<ENERGY, FORCE>::Acc acc;
+  red.init(acc);
+  {
+    const int c = cx + A.nx * (cy + A.ny * cz);
+    const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
+    if (FORCE) scan_pairs(A.xy2, A.zz2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    scan_pairs(A.xy2, A.zz2, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    red.cell_done(acc);
+    ncand += (unsigned long long)(FORCE ? s1 - s0 - 1 : s1 - p - 1);
   }
+  for (int k = 1; k < A.noff; ++k) {
+    const Off& o = A.off[k];
+    const int c = stencil_cell(A, k, cx, cy, cz);
+    if (FORCE) {
+      int ox, oy, oz;
+      unpack_off(H.opk[0][k], ox, oy, oz);
+      acc.wrap = (cx + ox < 0) || (cx + ox >= A.nx) || (cy + oy < 0) || (cy + oy >= A.ny) || (cz + oz < 0) ||
+                 (cz + oz >= A.nz);
+    }
+    const int j0 = A.cell_start[c], j1 = A.cell_start[c + 1];
+    scan_pairs(A.xy2, A.zz2, j0, j1, o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2, red, acc);
+    red.cell_done(acc);
+    ncand += (unsigned long long)(j1 - j0);
+  }
+  if (ENERGY) T.add_energy(acc.e.x + acc.e.y);
+  if (FORCE) {
+    float cc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      cc[a] = fmaf((float)cx + 0.5f, H.gf[a], fmaf((float)cy + 0.5f, H.gf[3 + a], ((float)cz + 0.5f) * H.gf[6 + a]));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) T.v[k] += acc.w[k].x + acc.w[k].y;
+    hood_particle_out<MODE>(T, __float_as_int(pi.w), pi.x, pi.y, pi.z, cc, acc.tx, acc.ty, acc.tz, acc.ax, acc.ay,
+                            acc.az, forces, grad, g, pos);
+  }
+  return ncand;
+}
+
+// Work list of the neighbourhood sweep: cells with kMinHome..kHome particles
+// (and a stencil that fits the table) are listed; every other cell is flagged
+// for the per-particle companion (empty cells are not). A cell whose staged
+// neighbourhood overflows is flagged later by the sweep itself.
+__global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_start, int ncells, int noff,
+                                                   int* __restrict__ work, int* __restrict__ list,
+                                                   unsigned char* __restrict__ flag) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  bool take = false;
+  if (h < ncells) {
+    const int nh = cell_start[h + 1] - cell_start[h];
+    take = nh >= kMinHome && nh <= kHome && noff <= kTab;
+    flag[h] = (nh > 0 && !take) ? 1 : 0;
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, take);
+  int base = 0;
+  if ((threadIdx.x & 31) == 0 && m) base = atomicAdd(work + 1, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (take) list[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = h;
+}
+
+// Per-CTA partials from the per-thread outputs (layout of the other sweeps).
+template <int MODE>
+__device__ __forceinline__ void store_partials(const ThreadOut& T, double* __restrict__ out) {
+  constexpr bool GRAD = MODE == 1 || MODE == 3;
+  constexpr int NV = hood_nv(MODE);
+  double v[NV];
+  if (MODE == 2) {
+    v[0] = (double)T.es - (double)T.ec;
+  } else {
+    // the accumulator of the other sweeps is sum fs r (x) r = -(sum fsn r (x) r)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = -(double)T.v[k];
+    if (MODE == 0) v[kVirN3] = 0.5 * ((double)T.es - (double)T.ec);
+    if (GRAD) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[kVirN3 + k] = (double)T.x[k];
+    }
+    if (MODE == 3) v[kVirN3 + 9] = 0.5 * ((double)T.es - (double)T.ec);
+  }
+  block_sum_store<NV>(v, out);
+}
+
+// Companion of the neighbourhood sweep: one thread per particle of the cells
+// it left (flag set: more than kHome particles, more than kCap staged
+// neighbours, or a stencil larger than the table).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_hood_rest(const __grid_constant__ SweepArgs A,
+                                                   const __grid_constant__ HoodArgs H, float* __restrict__ forces,
+                                                   double* __restrict__ grad, const double* __restrict__ gE,
+                                                   const double* __restrict__ pos, double* __restrict__ partials) {
+  constexpr bool GRAD = MODE == 1 || MODE == 3;
+  const float g = GRAD ? (float)*gE : 0.f;
+  ThreadOut T;
+  T.es = T.ec = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) T.v[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) T.x[k] = 0.f;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long ncand = 0;
+  bool mine = false;
+  int cx = 0, cy = 0, cz = 0;
+  if (p < A.n) {
+    const unsigned cc = A.cellc[p];
+    cx = (int)(cc & 1023u);
+    cy = (int)((cc >> 10) & 1023u);
+    cz = (int)(cc >> 20);
+    mine = H.flag[cx + A.nx * (cy + A.ny * cz)] != 0;
+  }
+  if (!__syncthreads_or(mine)) {  // nothing left here: zero partials, no reduction
+    if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
+    return;
+  }
+  if (mine) ncand = particle_sweep<MODE>(A, H, p, cx, cy, cz, T, forces, grad, g, pos);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+  if ((threadIdx.x & 31) == 0 && ncand) atomicAdd(H.cand, ncand);
+  store_partials<MODE>(T, partials + (size_t)blockIdx.x * hood_nv(MODE));
 }
 
 // MODE 0: energy, forces, virial (full shell). MODE 1: backward: grad_pos, X,
@@ -517,15 +615,16 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   float* const zzf = reinterpret_cast<float*>(S.zz);
   float* const oxyf = reinterpret_cast<float*>(S.oxy);
   float* const ozzf = reinterpret_cast<float*>(S.ozz);
-  const bool table = A.noff <= kTab;  // otherwise every cell takes the fallback
   for (int k = tid; k < A.noff && k < kTab; k += kThreads) {
     const Off& o = A.off[k];
     S.otab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[HALF ? 1 : 0][k]));
   }
-  // Work items come from an atomic counter two cells ahead: thread 0 keeps the
-  // indices in registers, so the atomic's latency overlaps whole cells, and
-  // every thread prefetches into L1 the cell ranges it will read for the next
-  // cell while this one is swept.
+  // Work items (cells of the list made by k_hood_list) come from an atomic
+  // counter two ahead: thread 0 keeps the list positions in registers, so the
+  // atomic's latency overlaps whole cells, and every thread prefetches into L1
+  // the cell ranges it will read for the next cell while this one is swept.
+  if (tid == 0) S.ncand = 0;
+  const int nlist = H.work[1];
   int next1 = 0, next2 = 0;
   if (tid == 0) {
     next1 = atomicAdd(H.work, 1);
@@ -535,31 +634,26 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      S.item = next1;
-      S.pref = next2;
+      S.item = next1 < nlist ? H.list[next1] : -1;
+      S.pref = next2 < nlist ? H.list[next2] : -1;
       S.nf = 0;
       S.nb = 0;
     }
     __syncthreads();
     const int h = S.item;
-    if (h >= H.ncells) break;
+    if (h < 0) break;
     if (tid == 0) {
       next1 = next2;
       next2 = atomicAdd(H.work, 1);
     }
     const int hs = A.cell_start[h];
     const int nh = A.cell_start[h + 1] - hs;
-    if (S.pref < H.ncells) prefetch_ranges(A, S, S.pref, 1 + warp + kWarps * lane);
-    if (nh == 0) continue;
+    if (S.pref >= 0) prefetch_ranges(A, S, S.pref, 1 + warp + kWarps * lane);
     const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
     float cc[3];  // centre of the home cell (wrapped absolute frame), FP32
 #pragma unroll
     for (int a = 0; a < 3; ++a)
       cc[a] = fmaf((float)cx + 0.5f, H.gf[a], fmaf((float)cy + 0.5f, H.gf[3 + a], ((float)cz + 0.5f) * H.gf[6 + a]));
-    if (nh > kHome || !table) {
-      hood_fallback<MODE>(A, H, hs, nh, cx, cy, cz, cc, T, forces, grad, g, pos);
-      continue;
-    }
 
     // ---- home particles (sorted order) and their largest distance from the centre
     float d = 0.f;
@@ -597,10 +691,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     stage_warp(A, S, mine, nmine, top * top);
     __syncthreads();
     const int nf = S.nf, nb = S.nb;
-    if (nf + nb + 2 > kCap) {
-      hood_fallback<MODE>(A, H, hs, nh, cx, cy, cz, cc, T, forces, grad, g, pos);
+    if (nf + nb + 2 > kCap) {  // left to the per-particle companion sweep
+      if (tid == 0) H.flag[h] = 1;
       continue;
     }
+    if (tid == 0) H.flag[h] = 0;
+    if (tid == 0)
+      S.ncand += (unsigned long long)nh * (unsigned long long)(nf + nb) +
+                 (unsigned long long)(HALF ? nh * (nh - 1) / 2 : nh * (nh - 1));
     if (tid == 0 && (nf & 1)) {  // padding after an odd segment
       xyf[(nf >> 1) * 4 + 1] = kFar;
       xyf[(nf >> 1) * 4 + 3] = kFar;
@@ -683,23 +781,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     }
   }
 
-  // per-CTA partials in the layout of the other sweeps
-  constexpr int NV = hood_nv(MODE);
-  double v[NV];
-  if (MODE == 2) {
-    v[0] = (double)T.es - (double)T.ec;
-  } else {
-    // the accumulator of the other sweeps is sum fs r (x) r = -(sum fsn r (x) r)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) v[k] = -(double)T.v[k];
-    if (MODE == 0) v[kVirN3] = 0.5 * ((double)T.es - (double)T.ec);
-    if (GRAD) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) v[kVirN3 + k] = (double)T.x[k];
-    }
-    if (MODE == 3) v[kVirN3 + 9] = 0.5 * ((double)T.es - (double)T.ec);
-  }
-  block_sum_store<NV>(v, partials + (size_t)blockIdx.x * NV);
+  // candidate count: one atomic per CTA
+  __syncthreads();
+  if (tid == 0 && S.ncand) atomicAdd(H.cand, S.ncand);
+  store_partials<MODE>(T, partials + (size_t)blockIdx.x * hood_nv(MODE));
 }
 
 }  // namespace
@@ -752,24 +837,38 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
 }
 
 int launch_hood(const SweepArgs& A, const HoodArgs& Hin, int* work, int mode, const double* hinv, float* forces,
-                double* grad, const double* gE, const double* pos, double* partials, int max_blocks, double* sums,
-                double* energy, double* virial, double* gradbox, cudaStream_t s) {
+                double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
+                double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s) {
   const int NV = hood_nv(mode);
+  const int nrest = (A.n + 255) / 256;  // CTAs of the companion sweep
   int nb = hood_grid(mode);
   if (nb <= 0) return CL_ERR_CUDA;
   if (nb > Hin.ncells) nb = Hin.ncells;
-  if (nb > max_blocks) nb = max_blocks;
-  if (nb < 1) nb = 1;
+  const long long room = partials_cap / NV - nrest;
+  if (nb > room) nb = (int)room;
+  if (nb < 1) return CL_ERR_INVALID_ARG;
   HoodArgs H = Hin;
   H.work = work;
-  if (cudaMemsetAsync(work, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  H.cand = reinterpret_cast<unsigned long long*>(work + 2);
+  if (cudaMemsetAsync(work, 0, 4 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag);
   const size_t smem = sizeof(Smem);
-  if (mode == 0) k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
-  else if (mode == 1) k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
-  else if (mode == 2) k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
-  else k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+  double* rest = partials + (size_t)nb * NV;
+  if (mode == 0) {
+    k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    k_hood_rest<0><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+  } else if (mode == 1) {
+    k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    k_hood_rest<1><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+  } else if (mode == 2) {
+    k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    k_hood_rest<2><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+  } else {
+    k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    k_hood_rest<3><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+  }
   const int final_mode = mode == 2 ? 1 : (mode == 0 ? 2 : (mode == 1 ? 3 : 4));
-  return finish_reduction(final_mode, 3, hinv, nb, NV, partials, sums, energy, virial, gradbox, gE, s);
+  return finish_reduction(final_mode, 3, hinv, nb + nrest, NV, partials, sums, energy, virial, gradbox, gE, s);
 }
 
 }  // namespace clk

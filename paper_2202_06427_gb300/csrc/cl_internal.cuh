@@ -136,16 +136,20 @@ struct HoodArgs {
   float hd;           // largest distance of a cell point from the cell centre
   float eps;          // rounding margin of the staging radius
   int ncells;
-  int* work;          // work counter, zeroed by the launcher
+  int* work;          // [0] work counter, [1] list length; zeroed by the launcher
+  int* list;          // cells the neighbourhood sweep takes (ncells capacity)
+  unsigned long long* cand;  // candidate pairs evaluated (work[2..3] of the same buffer), zeroed by the launcher
+  unsigned char* flag;       // per cell: 1 when the cell is left to the per-particle companion sweep
 };
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
                    HoodArgs* H);
 size_t hood_smem_bytes();
 // mode 0: energy, forces, virial; 1: backward; 2: energy (half shell, A = half
 // stencil); 3: energy and the backward outputs.
+// partials_cap: doubles available in partials (sweep_partials_needed).
 int launch_hood(const SweepArgs& A, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
-                double* grad, const double* gE, const double* pos, double* partials, int max_blocks, double* sums,
-                double* energy, double* virial, double* gradbox, cudaStream_t s);
+                double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
+                double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s);
 
 // Neighbour list (cl_pairs.cu). count[n], start[n+1] (scan of count), tiles,
 // meta: workspace; outputs pair_i/j/d of capacity entries.

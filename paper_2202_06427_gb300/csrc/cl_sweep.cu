@@ -319,10 +319,11 @@ __global__ void __launch_bounds__(256) k_candidates(const __grid_constant__ Swee
 
 static int blocks_for(int n) { return n > 0 ? (n + 255) / 256 : 1; }
 
-// Per-CTA partials (16 doubles each) for the one-thread-per-particle sweeps and
-// for the persistent neighbourhood sweep (at most kMaxPersistent CTAs).
+// Per-CTA partials (16 doubles each) for the one-thread-per-particle sweeps, and
+// for the persistent neighbourhood sweep (at most kMaxPersistent CTAs)
+// followed by its one-thread-per-particle companion.
 constexpr int kMaxPersistent = 4096;
-int sweep_partials_needed(int n) { return (blocks_for(n) > kMaxPersistent ? blocks_for(n) : kMaxPersistent) * 16; }
+int sweep_partials_needed(int n) { return (blocks_for(n) + kMaxPersistent) * 16; }
 
 int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStream_t s) {
   if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
