@@ -75,6 +75,7 @@ struct Smem {
   int item;
   int pref;              // the cell after this one
   unsigned long long ncand;  // candidate pairs this CTA evaluated
+  double out[kWarps][16];    // per-warp sums: share of sum fsn r (x) r (6), X (9), energy (1)
 };
 
 __device__ __forceinline__ void unpack_off(int v, int& ox, int& oy, int& oz) {
@@ -429,6 +430,36 @@ struct ThreadOut {
 };
 
 // Per-particle epilogue: force, virial share -2 X (x) Gn^(T=0), and X.
+// The same per-particle outputs as hood_particle_out, returned as terms:
+// o[0..5] share of sum fsn r (x) r, o[6..14] x_raw (x) F (gradient modes).
+template <int MODE>
+__device__ __forceinline__ void particle_terms(float* o, int i, float px, float py, float pz, const float* c,
+                                               float gx, float gy, float gz, float ax, float ay, float az,
+                                               float* __restrict__ forces, double* __restrict__ grad, float g,
+                                               const double* __restrict__ pos) {
+  const float X[3] = {c[0] + px, c[1] + py, c[2] + pz};
+  o[0] = -2.f * X[0] * ax;
+  o[1] = -(X[0] * ay + X[1] * ax);
+  o[2] = -(X[0] * az + X[2] * ax);
+  o[3] = -2.f * X[1] * ay;
+  o[4] = -(X[1] * az + X[2] * ay);
+  o[5] = -2.f * X[2] * az;
+  const float F[3] = {-gx, -gy, -gz};
+  if (MODE == 0 || MODE == 2) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) forces[(size_t)i * 3 + a] = F[a];
+  } else {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = (double)(-g * F[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float xa = (float)pos[(size_t)i * 3 + a];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) o[6 + a * 3 + b] = xa * F[b];
+    }
+  }
+}
+
 template <int MODE>
 __device__ __forceinline__ void hood_particle_out(ThreadOut& T, int i, float px, float py, float pz, const float* c,
                                                   float gx, float gy, float gz, float ax, float ay, float az,
@@ -605,12 +636,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   Smem& S = *reinterpret_cast<Smem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float g = GRAD ? (float)*gE : 0.f;
-  ThreadOut T;
-  T.es = T.ec = 0.f;
-#pragma unroll
-  for (int k = 0; k < 6; ++k) T.v[k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < 9; ++k) T.x[k] = 0.f;
+  for (int k = tid; k < kWarps * 16; k += kThreads) (&S.out[0][0])[k] = 0.0;
   float* const xyf = reinterpret_cast<float*>(S.xy);
   float* const zzf = reinterpret_cast<float*>(S.zz);
   float* const oxyf = reinterpret_cast<float*>(S.oxy);
@@ -745,7 +771,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
           for (int q = 0; q < 6; ++q) w[q] = f2(0.f);
           hood_scan<ENERGY, FORCE, true>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, w);
 #pragma unroll
-          for (int q = 0; q < 6; ++q) T.v[q] += w[q].x + w[q].y;
+          for (int q = 0; q < 6; ++q) {
+            const float t = warp_sum(w[q].x + w[q].y);
+            if (lane == 0) S.out[warp][q] += (double)t;
+          }
           const float b6[6] = {a0.gx.x + a0.gx.y, a0.gy.x + a0.gy.y, a0.gz.x + a0.gz.y,
                                a1.gx.x + a1.gx.y, a1.gy.x + a1.gy.y, a1.gz.x + a1.gz.y};
 #pragma unroll
@@ -771,20 +800,57 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
       } else if (k1b > k0b) {
         hood_scan<ENERGY, FORCE, false>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, nullptr);
       }
-      if (ENERGY) T.add_energy(e.x + e.y);
+      if (ENERGY) {
+        const float t = warp_sum(e.x + e.y);
+        if (lane == 0) S.out[warp][15] += (double)t;
+      }
     }
     __syncthreads();
-    if (FORCE && tid < nh) {
-      const int t = tid;
-      hood_particle_out<MODE>(T, S.hid[t], own_x(S, t), own_y(S, t), own_z(S, t), cc, S.acc[t][0], S.acc[t][1],
-                              S.acc[t][2], S.acc[t][3], S.acc[t][4], S.acc[t][5], forces, grad, g, pos);
+    if (FORCE && warp * 32 < nh) {  // warp-uniform: every lane joins the reductions
+      float o[15];
+#pragma unroll
+      for (int q = 0; q < 15; ++q) o[q] = 0.f;
+      if (tid < nh) {
+        const int t = tid;
+        particle_terms<MODE>(o, S.hid[t], own_x(S, t), own_y(S, t), own_z(S, t), cc, S.acc[t][0], S.acc[t][1],
+                             S.acc[t][2], S.acc[t][3], S.acc[t][4], S.acc[t][5], forces, grad, g, pos);
+      }
+      constexpr int NO = GRAD ? 15 : 6;
+#pragma unroll
+      for (int q = 0; q < NO; ++q) {
+        const float t = warp_sum(o[q]);
+        if (lane == 0) S.out[warp][q] += (double)t;
+      }
     }
   }
 
   // candidate count: one atomic per CTA
   __syncthreads();
   if (tid == 0 && S.ncand) atomicAdd(H.cand, S.ncand);
-  store_partials<MODE>(T, partials + (size_t)blockIdx.x * hood_nv(MODE));
+  // per-CTA partials (layout of the other sweeps) from the per-warp sums, fixed order
+  constexpr int NV = hood_nv(MODE);
+  if (tid < NV) {
+    int src;  // S.out column of partial tid
+    double sign = 1.0;
+    if (MODE == 2) {
+      src = 15;
+    } else if (tid < kVirN3) {
+      src = tid;
+      sign = -1.0;  // the accumulator of the other sweeps is sum fs r (x) r = -(sum fsn r (x) r)
+    } else if (MODE == 0) {
+      src = 15;
+      sign = 0.5;  // full shell: each pair-image twice
+    } else if (tid < kVirN3 + 9) {
+      src = tid;
+    } else {
+      src = 15;
+      sign = 0.5;
+    }
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) v += S.out[w][src];
+    partials[(size_t)blockIdx.x * NV + tid] = sign * v;
+  }
 }
 
 }  // namespace
