@@ -18,6 +18,15 @@ Functions and the passages they follow:
   pairlist      -- Sec. 4.1 neighbour list, i<j, sorted by (i, j).
   particles     -- force and half pair energy of chosen particles, one by one.
   brute_map / brute_pairlist -- O(n^2 * images) definitions used to pin the above.
+  images        -- Sec. 2.3 (Code 2): every pair-image with its displacement vector,
+                   the input of the mapped function; brute_images pins it.
+  cross_images  -- Sec. 3.2 (Code 8): pair-images between two sets of particles;
+                   brute_cross_images pins it.
+  lj            -- Code 6 (Lennard-Jones energy) and Code 7 (its forces), with the
+                   virial, summed over images().
+  mass_potential -- Code 5, second example: sum of m_i m_j / r.
+  velocity_hist -- Code 10: pair counts and summed |v_i - v_j| per distance bin.
+  knn_pairs     -- Code 8: the k cross pair-images of smallest distance.
   geom_info     -- widths between lattice faces and the cell grid for lcell.
   closed_form   -- see oracle.closed_form (perfect-lattice sums).
 """
@@ -52,8 +61,13 @@ def _lib():
         lib.or_brute_pairlist.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
         lib.or_particles.argtypes = [i32, ll, P, P, dbl, P, ll, P, P]
         lib.or_neighbors.argtypes = [i32, ll, P, P, dbl, dbl, P, ll, ll, P, P, P, P]
+        lib.or_images.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
+        lib.or_brute_images.argtypes = [i32, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
+        lib.or_cross_images.argtypes = [i32, ll, P, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
+        lib.or_brute_cross_images.argtypes = [i32, ll, P, ll, P, P, dbl, dbl, ll, P, P, P, P, P]
         for f in (lib.or_geom_info, lib.or_map, lib.or_brute_map, lib.or_pairlist,
-                  lib.or_brute_pairlist, lib.or_particles, lib.or_neighbors):
+                  lib.or_brute_pairlist, lib.or_particles, lib.or_neighbors, lib.or_images,
+                  lib.or_brute_images, lib.or_cross_images, lib.or_brute_cross_images):
             f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -197,3 +211,136 @@ def neighbors(x, h, rc, idx, band=1e-6):
 def energy(x, h, rc):
     """Shifted-force energy alone (no forces)."""
     return pair_map(x, h, rc, forces=False)["energy"]
+
+
+def _images(call, dim, cap):
+    while True:
+        pi = np.zeros(cap, dtype=np.int64)
+        pj = np.zeros(cap, dtype=np.int64)
+        rv = np.zeros((cap, dim))
+        r = np.zeros(cap)
+        nimg = np.zeros(1, dtype=np.int64)
+        rc_ = call(cap, pi, pj, rv, r, nimg)
+        if rc_ == -4:
+            cap = int(nimg[0]) + 1
+            continue
+        _check(rc_)
+        k = int(nimg[0])
+        return {"i": pi[:k], "j": pj[:k], "rv": rv[:k], "r": r[:k]}
+
+
+def images(x, h, rc, band=1e-6, cap=1 << 20):
+    """Every pair-image (i < j, image t) with r < rc(1 + 4 band): arrays i, j,
+    rv = x_j - x_i + t.H (n_img, dim) and r. Pairs with r >= rc are only there
+    so that a test can accept an FP32 inclusion; ``band_mask`` selects them."""
+    x, h, dim = _prep(x, h)
+    n = x.shape[0]
+    return _images(lambda c, a, b, v, r, k: _lib().or_images(dim, n, _p(x), _p(h), rc, band, c, _p(a), _p(b), _p(v),
+                                                             _p(r), _p(k)), dim, cap)
+
+
+def brute_images(x, h, rc, band=1e-6, cap=1 << 16):
+    x, h, dim = _prep(x, h)
+    n = x.shape[0]
+    return _images(lambda c, a, b, v, r, k: _lib().or_brute_images(dim, n, _p(x), _p(h), rc, band, c, _p(a), _p(b),
+                                                                   _p(v), _p(r), _p(k)), dim, cap)
+
+
+def cross_images(xa, yb, h, rc, band=1e-6, cap=1 << 20):
+    """Pair-images between the sets xa and yb (Code 8): every (a, b, t) with
+    |y_b - x_a + t.H| < rc(1 + 4 band); arrays i (= a), j (= b), rv, r."""
+    xa, h, dim = _prep(xa, h)
+    yb = np.ascontiguousarray(yb, dtype=np.float64).reshape(-1, dim)
+    na, nb = xa.shape[0], yb.shape[0]
+    return _images(lambda c, a, b, v, r, k: _lib().or_cross_images(dim, na, _p(xa), nb, _p(yb), _p(h), rc, band, c,
+                                                                   _p(a), _p(b), _p(v), _p(r), _p(k)), dim, cap)
+
+
+def brute_cross_images(xa, yb, h, rc, band=1e-6, cap=1 << 16):
+    xa, h, dim = _prep(xa, h)
+    yb = np.ascontiguousarray(yb, dtype=np.float64).reshape(-1, dim)
+    na, nb = xa.shape[0], yb.shape[0]
+    return _images(lambda c, a, b, v, r, k: _lib().or_brute_cross_images(dim, na, _p(xa), nb, _p(yb), _p(h), rc,
+                                                                         band, c, _p(a), _p(b), _p(v), _p(r), _p(k)),
+                   dim, cap)
+
+
+def band_mask(img, rc, band=1e-6):
+    """Images whose distance lies within band*rc of the cutoff."""
+    return np.abs(img["r"] - rc) <= band * rc
+
+
+def lj(x, h, rc, eps, sigma, band=1e-6, img=None):
+    """Lennard-Jones energy of Code 6, u(r) = 4 eps ((sigma^2/r^2)^6 - (sigma^2/r^2)^3),
+    over the pair-images with r < rc (not shifted), its forces F = -dE/dx (the
+    gradient of that energy; Code 7 accumulates f[i] += g, f[j] -= g) and the
+    virial W = -sum u'(r)/r rv (x) rv. Also the same sums over the band pairs
+    alone, the amount by which an FP32 classification may differ."""
+    if img is None:
+        img = images(x, h, rc, band)
+    n, dim = np.asarray(x).shape
+    inside = img["r"] < rc
+    edge = band_mask(img, rc, band)
+    out = {}
+    for key, sel in (("", inside & ~edge), ("band_", edge)):
+        r, rv, i, j = img["r"][sel], img["rv"][sel], img["i"][sel], img["j"][sel]
+        q = (sigma * sigma) / (r * r)
+        q3 = q * q * q
+        u = 4.0 * eps * (q3 * q3 - q3)
+        dudr_over_r = -24.0 * eps * (2.0 * q3 * q3 - q3) / (r * r)   # u'(r)/r
+        g = dudr_over_r[:, None] * rv                                # F_i += g, F_j -= g
+        f = np.zeros((n, dim))
+        np.add.at(f, i, g)
+        np.add.at(f, j, -g)
+        out[key + "energy"] = float(np.sum(u))
+        out[key + "forces"] = f
+        out[key + "virial"] = -(rv * dudr_over_r[:, None]).T @ rv
+        out[key + "abs_energy"] = float(np.sum(np.abs(u)))
+    return out
+
+
+def mass_potential(x, h, rc, m, band=1e-6, img=None):
+    """Code 5, second example: sum over pair-images within rc of m_i m_j / r;
+    also the part of the band pairs."""
+    if img is None:
+        img = images(x, h, rc, band)
+    m = np.asarray(m, dtype=np.float64)
+    inside = img["r"] < rc
+    edge = band_mask(img, rc, band)
+    term = m[img["i"]] * m[img["j"]] / img["r"]
+    return {"value": float(np.sum(term[inside & ~edge])), "band": float(np.sum(np.abs(term[edge])))}
+
+
+def velocity_hist(x, h, rc, v, binstep, nbins, band=1e-6, img=None):
+    """Code 10: for each pair-image within rc, bin k = ceil(r / binstep)
+    (1-based, bins closed on the right); when k <= nbins the pair adds 1 to
+    counts[k-1] and |v_i - v_j| to vsum[k-1]. Returns counts and vsum over the
+    pairs away from the cutoff and the bin edges (by band*rc), and the same over
+    the pairs near them (either classification is correct)."""
+    if img is None:
+        img = images(x, h, rc, band)
+    v = np.asarray(v, dtype=np.float64)
+    r = img["r"]
+    k = np.ceil(r / binstep).astype(np.int64)
+    near_edge = np.abs(r - np.round(r / binstep) * binstep) <= band * rc
+    edge = band_mask(img, rc, band) | near_edge
+    take = (r < rc) & (k >= 1) & (k <= nbins)
+    dv = np.linalg.norm(v[img["i"]] - v[img["j"]], axis=1)
+    out = {}
+    for key, sel in (("", take & ~edge), ("band_", edge & (r < rc * (1 + 4 * band)))):
+        out[key + "counts"] = np.bincount(k[sel] - 1, minlength=nbins)[:nbins] if np.any(sel) else np.zeros(nbins, np.int64)
+        out[key + "vsum"] = (np.bincount(k[sel] - 1, weights=dv[sel], minlength=nbins)[:nbins]
+                             if np.any(sel) else np.zeros(nbins))
+    return out
+
+
+def knn_pairs(xa, yb, h, rc, k, band=1e-6, img=None):
+    """Code 8: the k cross pair-images (a in xa, b in yb) of smallest distance
+    among those within rc, ordered by distance (fewer when fewer exist). Returns
+    arrays i (= a), j (= b), r, and the distance of the k-th pair."""
+    if img is None:
+        img = cross_images(xa, yb, h, rc, band)
+    sel = img["r"] < rc
+    order = np.lexsort((img["j"][sel], img["i"][sel], img["r"][sel]))[:k]
+    r = img["r"][sel][order]
+    return {"i": img["i"][sel][order], "j": img["j"][sel][order], "r": r}

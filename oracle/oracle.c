@@ -285,8 +285,29 @@ static void acc_out(const acc* A, long long* counts, double* sums, double* viria
 typedef struct { long long i, j; double r; } pl_entry;
 typedef struct { pl_entry* e; long long n, cap; int overflow; } pl_buf;
 
+/* Sink of or_images / or_cross_images: every accepted pair-image with its
+ * displacement vector (the mapped function of Code 2 receives the two
+ * positions under the image, i.e. this vector). */
+typedef struct {
+  long long *i, *j;
+  double* rv;   /* cap * dim */
+  double* r;
+  long long n, cap;
+  int dim;
+} img_buf;
+
+static void img_put(img_buf* b, long long i, long long j, const double* rv, double r) {
+  if (b->n < b->cap) {
+    b->i[b->n] = i;
+    b->j[b->n] = j;
+    for (int a = 0; a < b->dim; ++a) b->rv[b->n * b->dim + a] = rv[a];
+    b->r[b->n] = r;
+  }
+  b->n++;
+}
+
 static int enumerate(const geom* g, long long np, const double* x, double rc, double band,
-                     long long i_lo, long long i_hi, acc* A, pl_buf* pl) {
+                     long long i_lo, long long i_hi, acc* A, pl_buf* pl, img_buf* ib) {
   const int dim = g->dim;
   const double rc_enum = rc * (1.0 + 4.0 * band);
   clist cl;
@@ -329,7 +350,9 @@ static int enumerate(const geom* g, long long np, const double* x, double rc, do
             /* integer image relative to the raw (unwrapped) input positions */
             double t[3] = {0, 0, 0};
             for (int k = 0; k < dim; ++k) t[k] = (double)T[k] - cl.fl[j * dim + k] + cl.fl[i * dim + k];
-            if (pl) {
+            if (ib) {
+              img_put(ib, i, j, rv, r);
+            } else if (pl) {
               if (pl->n == pl->cap) { pl->overflow = 1; continue; }
               pl->e[pl->n].i = i; pl->e[pl->n].j = j; pl->e[pl->n].r = r; pl->n++;
             } else {
@@ -377,7 +400,7 @@ int or_map(int dim, long long n, const double* x, const double* h, double rc, do
     if (!(rc < g.w[k])) return OR_ERR_ARG; /* a particle would see its own image */
   acc A;
   acc_init(&A, dim, rc, band, nbins, rmax, n, forces, hist_core, hist_maybe);
-  err = enumerate(&g, n, x, rc, band, i_lo, i_hi, &A, NULL);
+  err = enumerate(&g, n, x, rc, band, i_lo, i_hi, &A, NULL, NULL);
   if (err) return err;
   acc_out(&A, counts, sums, virial, dedh);
   return OR_OK;
@@ -422,7 +445,7 @@ int or_pairlist(int dim, long long n, const double* x, const double* h, double r
   pl.cap = cap + 1; pl.n = 0; pl.overflow = 0;
   pl.e = (pl_entry*)malloc(sizeof(pl_entry) * (size_t)pl.cap);
   if (!pl.e) return OR_ERR_OOM;
-  err = enumerate(&g, n, x, rc, band, 0, n, NULL, &pl);
+  err = enumerate(&g, n, x, rc, band, 0, n, NULL, &pl, NULL);
   if (err) { free(pl.e); return err; }
   return pairlist_finish(&pl, rc, band, cap, pi, pj, pd, pband, npairs);
 }
@@ -564,7 +587,7 @@ int or_neighbors(int dim, long long n, const double* x, const double* h, double 
 /* ---------------------------------------------------------- brute force -- */
 
 static int brute_walk(const geom* g, long long n, const double* x, double rc, double band,
-                      acc* A, pl_buf* pl) {
+                      acc* A, pl_buf* pl, img_buf* ib) {
   const int dim = g->dim;
   const double rce = rc * (1.0 + 4.0 * band);
   int K[3] = {0, 0, 0};
@@ -597,7 +620,9 @@ static int brute_walk(const geom* g, long long n, const double* x, double rc, do
             double r = sqrt(r2);
             double t[3] = {0, 0, 0};
             for (int k = 0; k < dim; ++k) t[k] = T[k] - fl[j * dim + k] + fl[i * dim + k];
-            if (pl) {
+            if (ib) {
+              img_put(ib, i, j, rv, r);
+            } else if (pl) {
               if (pl->n == pl->cap) { pl->overflow = 1; continue; }
               pl->e[pl->n].i = i; pl->e[pl->n].j = j; pl->e[pl->n].r = r; pl->n++;
             } else {
@@ -617,7 +642,7 @@ int or_brute_map(int dim, long long n, const double* x, const double* h, double 
   if (!(rc > 0) || n < 0 || band < 0) return OR_ERR_ARG;
   acc A;
   acc_init(&A, dim, rc, band, nbins, rmax, n, forces, hist_core, hist_maybe);
-  err = brute_walk(&g, n, x, rc, band, &A, NULL);
+  err = brute_walk(&g, n, x, rc, band, &A, NULL, NULL);
   if (err) return err;
   acc_out(&A, counts, sums, virial, dedh);
   return OR_OK;
@@ -633,7 +658,145 @@ int or_brute_pairlist(int dim, long long n, const double* x, const double* h, do
   pl.cap = cap + 1; pl.n = 0; pl.overflow = 0;
   pl.e = (pl_entry*)malloc(sizeof(pl_entry) * (size_t)pl.cap);
   if (!pl.e) return OR_ERR_OOM;
-  err = brute_walk(&g, n, x, rc, band, NULL, &pl);
+  err = brute_walk(&g, n, x, rc, band, NULL, &pl, NULL);
   if (err) { free(pl.e); return err; }
   return pairlist_finish(&pl, rc, band, cap, pi, pj, pd, pband, npairs);
+}
+
+/* ------------------------------------------------------------ pair-images */
+
+/* Every pair-image (i < j, image t) with r < rc(1 + 4 band), with its
+ * displacement rv = x_j - x_i + t.H (dim values each) and distance r, in the
+ * order the cell-list enumeration meets them. This is what the mapped
+ * function of Code 2 sees; any pair function (Code 5-7, 10) is a sum over it.
+ * Returns OR_ERR_CAPACITY with *nimg = the number needed when cap is short. */
+int or_images(int dim, long long n, const double* x, const double* h, double rc, double band, long long cap,
+              long long* pi, long long* pj, double* rv, double* pr, long long* nimg) {
+  geom g;
+  int err = geom_init(&g, dim, h);
+  if (err) return err;
+  if (!(rc > 0) || n < 0 || band < 0 || cap < 0) return OR_ERR_ARG;
+  img_buf b = {pi, pj, rv, pr, 0, cap, dim};
+  err = enumerate(&g, n, x, rc, band, 0, n, NULL, NULL, &b);
+  if (err) return err;
+  *nimg = b.n;
+  return b.n > cap ? OR_ERR_CAPACITY : OR_OK;
+}
+
+/* The same set by brute force over all i < j and image vectors (n <= ~300). */
+int or_brute_images(int dim, long long n, const double* x, const double* h, double rc, double band,
+                    long long cap, long long* pi, long long* pj, double* rv, double* pr, long long* nimg) {
+  geom g;
+  int err = geom_init(&g, dim, h);
+  if (err) return err;
+  if (!(rc > 0) || n < 0 || band < 0 || cap < 0) return OR_ERR_ARG;
+  img_buf b = {pi, pj, rv, pr, 0, cap, dim};
+  err = brute_walk(&g, n, x, rc, band, NULL, NULL, &b);
+  if (err) return err;
+  *nimg = b.n;
+  return b.n > cap ? OR_ERR_CAPACITY : OR_OK;
+}
+
+/* Cross pair-images between two sets (Code 8: a cell list of x and y):
+ *   { (a, b, t) : a < na, b < nb, |y_b - x_a + t.H| < rc },
+ * every a paired with every b (no a < b rule), displacement rv = y_b - x_a + t.H.
+ * A cell list of x on the oracle grid; every b visits the full stencil around
+ * its cell. */
+int or_cross_images(int dim, long long na, const double* xa, long long nb, const double* yb, const double* h,
+                    double rc, double band, long long cap, long long* pa, long long* pb, double* rv, double* pr,
+                    long long* nimg) {
+  geom g;
+  int err = geom_init(&g, dim, h);
+  if (err) return err;
+  if (!(rc > 0) || na < 0 || nb < 0 || band < 0 || cap < 0) return OR_ERR_ARG;
+  const double rce = rc * (1.0 + 4.0 * band);
+  clist cl;
+  err = clist_build(&cl, &g, na, xa, rce);
+  if (err) return err;
+  img_buf buf = {pa, pb, rv, pr, 0, cap, dim};
+  int span[3] = {1, 1, 1};
+  for (int k = 0; k < dim; ++k) span[k] = 2 * cl.m[k] + 1;
+  for (long long b = 0; b < nb; ++b) {
+    /* wrap y_b and find its cell on x's grid */
+    double s[3] = {0, 0, 0}, yw[3] = {0, 0, 0};
+    int cb[3] = {0, 0, 0};
+    for (int k = 0; k < dim; ++k) {
+      for (int a = 0; a < dim; ++a) s[k] += yb[b * dim + a] * g.hinv[a][k];
+      s[k] -= floor(s[k]);
+      int c = (int)floor(s[k] * cl.n[k]);
+      if (c >= cl.n[k]) c = cl.n[k] - 1;
+      if (c < 0) c = 0;
+      cb[k] = c;
+    }
+    for (int a = 0; a < dim; ++a)
+      for (int k = 0; k < dim; ++k) yw[a] += s[k] * g.h[k][a];
+    for (int oz = 0; oz < (dim == 3 ? span[2] : 1); ++oz)
+      for (int oy = 0; oy < span[1]; ++oy)
+        for (int ox = 0; ox < span[0]; ++ox) {
+          int o[3] = {ox - cl.m[0], oy - cl.m[1], dim == 3 ? oz - cl.m[2] : 0};
+          long long T[3] = {0, 0, 0}, cj = 0, stride = 1;
+          for (int k = 0; k < dim; ++k) {
+            long long u = (long long)cb[k] + o[k];
+            T[k] = floordiv_ll(u, cl.n[k]);
+            cj += (u - T[k] * cl.n[k]) * stride;
+            stride *= cl.n[k];
+          }
+          double shift[3] = {0, 0, 0};
+          for (int a = 0; a < dim; ++a)
+            for (int k = 0; k < dim; ++k) shift[a] += (double)T[k] * g.h[k][a];
+          for (long long q = cl.start[cj]; q < cl.start[cj + 1]; ++q) {
+            long long ia = cl.order[q];
+            double d[3] = {0, 0, 0}, r2 = 0;
+            for (int a = 0; a < dim; ++a) {
+              d[a] = yw[a] - (cl.xw[ia * dim + a] + shift[a]);
+              r2 += d[a] * d[a];
+            }
+            if (!(r2 < rce * rce)) continue;
+            img_put(&buf, ia, b, d, sqrt(r2));
+          }
+        }
+  }
+  clist_free(&cl);
+  *nimg = buf.n;
+  return buf.n > cap ? OR_ERR_CAPACITY : OR_OK;
+}
+
+/* The same set by brute force over all (a, b) and image vectors. */
+int or_brute_cross_images(int dim, long long na, const double* xa, long long nb, const double* yb,
+                          const double* h, double rc, double band, long long cap, long long* pa, long long* pb,
+                          double* rv, double* pr, long long* nimg) {
+  geom g;
+  int err = geom_init(&g, dim, h);
+  if (err) return err;
+  if (!(rc > 0) || na < 0 || nb < 0 || band < 0 || cap < 0) return OR_ERR_ARG;
+  const double rce = rc * (1.0 + 4.0 * band);
+  int K[3] = {0, 0, 0};
+  for (int k = 0; k < dim; ++k) K[k] = (int)ceil(rce / g.w[k]) + 1;
+  img_buf buf = {pa, pb, rv, pr, 0, cap, dim};
+  for (long long ia = 0; ia < na; ++ia)
+    for (long long b = 0; b < nb; ++b) {
+      double sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
+      for (int k = 0; k < dim; ++k) {
+        for (int a = 0; a < dim; ++a) {
+          sa[k] += xa[ia * dim + a] * g.hinv[a][k];
+          sb[k] += yb[b * dim + a] * g.hinv[a][k];
+        }
+        sa[k] -= floor(sa[k]);
+        sb[k] -= floor(sb[k]);
+      }
+      for (int tz = (dim == 3 ? -K[2] : 0); tz <= (dim == 3 ? K[2] : 0); ++tz)
+        for (int ty = -K[1]; ty <= K[1]; ++ty)
+          for (int tx = -K[0]; tx <= K[0]; ++tx) {
+            double T[3] = {tx, ty, tz};
+            double d[3] = {0, 0, 0}, r2 = 0;
+            for (int a = 0; a < dim; ++a) {
+              for (int k = 0; k < dim; ++k) d[a] += (sb[k] - sa[k] + T[k]) * g.h[k][a];
+              r2 += d[a] * d[a];
+            }
+            if (!(r2 < rce * rce)) continue;
+            img_put(&buf, ia, b, d, sqrt(r2));
+          }
+    }
+  *nimg = buf.n;
+  return buf.n > cap ? OR_ERR_CAPACITY : OR_OK;
 }
