@@ -175,6 +175,29 @@ int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, lon
                                        neighbours x home particles, own cell included); reads a counter */
 int cl_query(const cl_list* cl, int what, long long* value, void* stream);
 
+/* Mapped functions of the paper's examples, built on the compile-time functor
+ * hook (cellmap_pairfns.cuh) with one thread per cell-sorted particle. All
+ * arrays are DEVICE arrays in original particle order; scalar and histogram
+ * outputs are zeroed and then accumulated, FP64. Asynchronous on `stream`.
+ *
+ * cl_map_mass (Code 5, second example): out_dev[0] = sum over the pair-images
+ * within the cutoff of m_i m_j / r, mass_dev = n FP32 masses.
+ *
+ * cl_map_lj (Code 6, 7): energy_dev[0] = sum of 4 eps ((sigma/r)^12 -
+ * (sigma/r)^6) over the pair-images within the cutoff (not shifted); when
+ * forces_dev ((n, dim) FP32) is not NULL also the forces F = -dE/dx (the
+ * gradient of that energy). Errors: INVALID_ARG (sigma <= 0, non-finite).
+ *
+ * cl_map_velocity_hist (Code 10): for each pair-image within the cutoff, bin
+ * k = ceil(r / binstep) (1-based, closed on the right); when k <= nbins,
+ * counts_dev[k-1] += 1 and vsum_dev[k-1] += |v_i - v_j| with vel_dev (n, dim)
+ * FP32 velocities. 1 <= nbins <= CL_VHIST_MAX_BINS. */
+#define CL_VHIST_MAX_BINS 64
+int cl_map_mass(const cl_list* cl, const float* mass_dev, double* out_dev, void* stream);
+int cl_map_lj(const cl_list* cl, double eps, double sigma, double* energy_dev, float* forces_dev, void* stream);
+int cl_map_velocity_hist(const cl_list* cl, const float* vel_dev, double binstep, int nbins,
+                         unsigned long long* counts_dev, double* vsum_dev, void* stream);
+
 /* Host-only box preparation, no GPU needed: for box, fills
  * grid[3] (cells per axis, 1 for unused axes), widths[3] (face distances) and
  * stencil[2] (half-shell and full-shell offset counts). Same errors as the

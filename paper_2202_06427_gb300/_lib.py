@@ -61,6 +61,9 @@ def lib():
         L.cl_backward.argtypes = [P, P, P, P, P, P]
         L.cl_energy_grad.argtypes = [P, P, P, P, P, P, P]
         L.cl_scale.argtypes = [P, P, P, ll, P]
+        L.cl_map_mass.argtypes = [P, P, P, P]
+        L.cl_map_lj.argtypes = [P, ctypes.c_double, ctypes.c_double, P, P, P]
+        L.cl_map_velocity_hist.argtypes = [P, P, ctypes.c_double, i32, P, P, P]
         L.cl_query.argtypes = [P, i32, ctypes.POINTER(ll), P]
         L.cl_box_info.argtypes = [ctypes.POINTER(cl_box), P, P, P]
         L.cl_status.argtypes = [P, P]
@@ -71,7 +74,7 @@ def lib():
         L.cl_error_string.argtypes = [i32]
         L.cl_error_string.restype = ctypes.c_char_p
         for f in ("cl_build", "cl_update", "cl_map", "cl_backward", "cl_energy_grad", "cl_scale", "cl_query",
-                  "cl_box_info", "cl_status"):
+                  "cl_box_info", "cl_status", "cl_map_mass", "cl_map_lj", "cl_map_velocity_hist"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib

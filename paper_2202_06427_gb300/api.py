@@ -212,6 +212,52 @@ def cl_scale(scale, x, out=None, stream=None):
     return out
 
 
+def _per_particle(cl, a, cols, name):
+    a = torch.as_tensor(a, device=cl.device, dtype=torch.float32)
+    if cols:
+        a = a.reshape(cl.n, cols)
+    else:
+        a = a.reshape(cl.n)
+    if not a.is_contiguous():
+        a = a.contiguous()
+    return a
+
+
+def cl_map_mass(cl, mass, stream=None):
+    """Code 5 (second example): sum over the pair-images within the cutoff of
+    m_i m_j / r; mass: n values (cast to float32). Returns a (1,) float64 tensor."""
+    m = _per_particle(cl, mass, 0, "mass")
+    out = torch.empty(1, dtype=torch.float64, device=cl.device)
+    with torch.cuda.device(cl.device):
+        L.check(L.lib().cl_map_mass(cl.handle, _ptr(m), _ptr(out), _stream(stream)), "cl_map_mass")
+    return out
+
+
+def cl_map_lj(cl, eps, sigma, forces=True, stream=None):
+    """Code 6 and 7: Lennard-Jones energy 4 eps ((sigma/r)^12 - (sigma/r)^6) over
+    the pair-images within the cutoff (not shifted) and, with forces=True, the
+    forces -dE/dx (float32, (n, dim)). Returns (energy (1,) float64, forces or None)."""
+    e = torch.empty(1, dtype=torch.float64, device=cl.device)
+    f = torch.empty((cl.n, cl.dim), dtype=torch.float32, device=cl.device) if forces else None
+    with torch.cuda.device(cl.device):
+        L.check(L.lib().cl_map_lj(cl.handle, float(eps), float(sigma), _ptr(e), _ptr(f), _stream(stream)),
+                "cl_map_lj")
+    return e, f
+
+
+def cl_map_velocity_hist(cl, vel, binstep, nbins, stream=None):
+    """Code 10: pair counts and summed |v_i - v_j| per distance bin, bin
+    k = ceil(r / binstep) (1-based, closed on the right), k <= nbins.
+    vel: (n, dim) velocities (cast to float32). Returns (counts int64, vsum float64)."""
+    v = _per_particle(cl, vel, cl.dim, "vel")
+    counts = torch.empty(int(nbins), dtype=torch.int64, device=cl.device)
+    vsum = torch.empty(int(nbins), dtype=torch.float64, device=cl.device)
+    with torch.cuda.device(cl.device):
+        L.check(L.lib().cl_map_velocity_hist(cl.handle, _ptr(v), float(binstep), int(nbins), _ptr(counts),
+                                             _ptr(vsum), _stream(stream)), "cl_map_velocity_hist")
+    return counts, vsum
+
+
 def cl_query(cl, what, stream=None):
     v = ctypes.c_longlong(0)
     key = L.INFO[what] if isinstance(what, str) else int(what)
