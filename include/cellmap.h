@@ -175,6 +175,52 @@ int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, lon
                                        neighbours x home particles, own cell included); reads a counter */
 int cl_query(const cl_list* cl, int what, long long* value, void* stream);
 
+/* Two sets of particles (Sec. 3.2, Code 8; Sec. 4.1): set A is the cell list
+ * `cl`, set B the (nb, dim) FP64 device positions posb_dev in the same box.
+ * The pair-images are every (a, b, t) with |y_b - x_a + t.H| < cutoff (no
+ * a < b rule); a and b are 0-based indices into A and B. Each b is binned on
+ * A's grid in FP64 and sweeps the full stencil of its cell. These calls
+ * synchronize `stream` and allocate their workspace (cudaMalloc/cudaFree).
+ * Errors: INVALID_ARG, NONFINITE (a position of B), OOM, CUDA, and as noted.
+ *
+ * cl_cross_count: count_dev[0] = number of cross pair-images (u64).
+ *
+ * cl_cross_pairlist: the cross pairs as (pa, pb, pd) sorted by (b, a), pd the
+ * FP32 distance; *npairs (host) receives the number of pairs. Same capacity
+ * protocol as CL_RED_PAIRLIST (CL_ERR_CAPACITY: call again with capacity >=
+ * *npairs); requires unique images (cutoff <= w_min / 2, else
+ * CUTOFF_TOO_LARGE); UNSUPPORTED when one b has more than 1024 neighbours.
+ *
+ * cl_cross_knn: for each b its k nearest a within the cutoff, ascending by
+ * distance (ties: smaller a first): knn_a_dev[b*k + q] (a, or -1 when b has
+ * fewer than q+1 neighbours), knn_d_dev[b*k + q] (FP32 distance, +inf when
+ * empty). 1 <= k <= CL_KNN_MAX.
+ *
+ * cl_cross_topk (Code 8): the k cross pair-images of smallest distance within
+ * the cutoff, ascending: a_dev[q], b_dev[q], d_dev[q] for q < *nfound (host,
+ * min(k, number of cross pairs)); the rest hold -1, -1, +inf. 1 <= k <=
+ * CL_KNN_MAX. */
+#define CL_KNN_MAX 32
+int cl_cross_count(const cl_list* cl, const double* posb_dev, long long nb, unsigned long long* count_dev,
+                   void* stream);
+int cl_cross_pairlist(const cl_list* cl, const double* posb_dev, long long nb, long long capacity, int* pa_dev,
+                      int* pb_dev, float* pd_dev, long long* npairs, void* stream);
+int cl_cross_knn(const cl_list* cl, const double* posb_dev, long long nb, int k, int* knn_a_dev, float* knn_d_dev,
+                 void* stream);
+int cl_cross_topk(const cl_list* cl, const double* posb_dev, long long nb, int k, int* a_dev, int* b_dev,
+                  float* d_dev, long long* nfound, void* stream);
+
+/* Box for particles WITHOUT periodic boundaries (Sec. 4.1, Fig. 2): reduces
+ * the extent of the (n, dim) FP64 device positions pos_dev (and of a second set
+ * pos2_dev of n2 points, may be NULL with n2 = 0, e.g. the other set of a
+ * two-set neighbour list) on `stream`, synchronizes, and writes to *box_out an
+ * orthorhombic box whose side along each axis exceeds extent + cutoff, so that
+ * every periodic image of a pair but the direct one is at least the cutoff
+ * away: cl_build with this box maps the pairs of the open system. Errors:
+ * INVALID_ARG, NONFINITE (a coordinate is not finite), OOM, CUDA. */
+int cl_box_nonperiodic(const double* pos_dev, long long n, const double* pos2_dev, long long n2, int dim,
+                       double cutoff, int lcell, void* stream, cl_box* box_out);
+
 /* Mapped functions of the paper's examples, built on the compile-time functor
  * hook (cellmap_pairfns.cuh) with one thread per cell-sorted particle. All
  * arrays are DEVICE arrays in original particle order; scalar and histogram

@@ -10,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcellmap.so")
 
 CL_OK = 0
+CL_ERR_CAPACITY = -6
 ERRORS = {
     -1: "CL_ERR_INVALID_ARG", -2: "CL_ERR_INVALID_BOX", -3: "CL_ERR_CUTOFF_TOO_LARGE", -4: "CL_ERR_NONFINITE",
     -5: "CL_ERR_OOM", -6: "CL_ERR_CAPACITY", -7: "CL_ERR_TIMEOUT", -8: "CL_ERR_CUDA", -9: "CL_ERR_UNSUPPORTED",
@@ -64,6 +65,11 @@ def lib():
         L.cl_map_mass.argtypes = [P, P, P, P]
         L.cl_map_lj.argtypes = [P, ctypes.c_double, ctypes.c_double, P, P, P]
         L.cl_map_velocity_hist.argtypes = [P, P, ctypes.c_double, i32, P, P, P]
+        L.cl_box_nonperiodic.argtypes = [P, ll, P, ll, i32, ctypes.c_double, i32, P, ctypes.POINTER(cl_box)]
+        L.cl_cross_count.argtypes = [P, P, ll, P, P]
+        L.cl_cross_pairlist.argtypes = [P, P, ll, ll, P, P, P, ctypes.POINTER(ll), P]
+        L.cl_cross_knn.argtypes = [P, P, ll, i32, P, P, P]
+        L.cl_cross_topk.argtypes = [P, P, ll, i32, P, P, P, ctypes.POINTER(ll), P]
         L.cl_query.argtypes = [P, i32, ctypes.POINTER(ll), P]
         L.cl_box_info.argtypes = [ctypes.POINTER(cl_box), P, P, P]
         L.cl_status.argtypes = [P, P]
@@ -74,7 +80,8 @@ def lib():
         L.cl_error_string.argtypes = [i32]
         L.cl_error_string.restype = ctypes.c_char_p
         for f in ("cl_build", "cl_update", "cl_map", "cl_backward", "cl_energy_grad", "cl_scale", "cl_query",
-                  "cl_box_info", "cl_status", "cl_map_mass", "cl_map_lj", "cl_map_velocity_hist"):
+                  "cl_box_info", "cl_status", "cl_map_mass", "cl_map_lj", "cl_map_velocity_hist",
+                  "cl_box_nonperiodic", "cl_cross_count", "cl_cross_pairlist", "cl_cross_knn", "cl_cross_topk"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib

@@ -258,6 +258,90 @@ def cl_map_velocity_hist(cl, vel, binstep, nbins, stream=None):
     return counts, vsum
 
 
+def box_nonperiodic(pos, cutoff, lcell=2, pos2=None, stream=None):
+    """Box for particles without periodic boundaries (Sec. 4.1): orthorhombic,
+    each side larger than the extent of pos (and pos2) plus the cutoff, so that
+    cl_build with it maps the pairs of the open system. Returns h (dim, dim)."""
+    _check_pos(pos, pos.shape[1])
+    n2 = 0
+    if pos2 is not None:
+        _check_pos(pos2, pos.shape[1])
+        n2 = pos2.shape[0]
+    box = L.cl_box()
+    with torch.cuda.device(pos.device):
+        L.check(L.lib().cl_box_nonperiodic(_ptr(pos), pos.shape[0], _ptr(pos2) if n2 else None, n2, pos.shape[1],
+                                           float(cutoff), int(lcell), _stream(stream), ctypes.byref(box)),
+                "cl_box_nonperiodic")
+    d = box.dim
+    return np.array([[box.h[a * d + b] for b in range(d)] for a in range(d)])
+
+
+def cl_build_open(pos, cutoff, lcell=2, pos2=None, stream=None):
+    """Cell list of particles without periodic boundaries (see box_nonperiodic)."""
+    return cl_build(pos, box_nonperiodic(pos, cutoff, lcell, pos2, stream), cutoff, lcell, stream)
+
+
+def cl_cross_count(cl, posb, stream=None):
+    """Number of pair-images between set A (the cell list) and the points posb
+    within the cutoff (Code 8). Returns an int."""
+    _check_pos(posb, cl.dim)
+    out = torch.empty(1, dtype=torch.int64, device=cl.device)
+    with torch.cuda.device(cl.device):
+        L.check(L.lib().cl_cross_count(cl.handle, _ptr(posb), posb.shape[0], _ptr(out), _stream(stream)),
+                "cl_cross_count")
+    return int(out.item())
+
+
+def cl_cross_pairlist(cl, posb, capacity=None, stream=None):
+    """Cross pairs (a, b) within the cutoff sorted by (b, a), with their
+    distances: dict of int32 tensors a, b and float32 d."""
+    _check_pos(posb, cl.dim)
+    dev = cl.device
+    cap = int(capacity) if capacity is not None else 0
+    while True:
+        pa = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        pb = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        pd = torch.empty(max(cap, 1), dtype=torch.float32, device=dev)
+        n = ctypes.c_longlong(0)
+        with torch.cuda.device(dev):
+            code = L.lib().cl_cross_pairlist(cl.handle, _ptr(posb), posb.shape[0], cap, _ptr(pa), _ptr(pb), _ptr(pd),
+                                             ctypes.byref(n), _stream(stream))
+        if code == L.CL_ERR_CAPACITY and capacity is None:
+            cap = n.value
+            continue
+        L.check(code, "cl_cross_pairlist")
+        k = n.value
+        return {"a": pa[:k], "b": pb[:k], "d": pd[:k], "npairs": k}
+
+
+def cl_cross_knn(cl, posb, k, stream=None):
+    """For each point of posb its k nearest points of set A within the cutoff:
+    (a (nb, k) int32, -1 when missing; d (nb, k) float32, inf when missing)."""
+    _check_pos(posb, cl.dim)
+    nb = posb.shape[0]
+    a = torch.empty((nb, int(k)), dtype=torch.int32, device=cl.device)
+    d = torch.empty((nb, int(k)), dtype=torch.float32, device=cl.device)
+    with torch.cuda.device(cl.device):
+        L.check(L.lib().cl_cross_knn(cl.handle, _ptr(posb), nb, int(k), _ptr(a), _ptr(d), _stream(stream)),
+                "cl_cross_knn")
+    return a, d
+
+
+def cl_cross_topk(cl, posb, k, stream=None):
+    """Code 8: the k pairs (a in A, b in posb) of smallest distance within the
+    cutoff, ascending: dict a, b (int32), d (float32), n (how many exist)."""
+    _check_pos(posb, cl.dim)
+    dev = cl.device
+    a = torch.empty(int(k), dtype=torch.int32, device=dev)
+    b = torch.empty(int(k), dtype=torch.int32, device=dev)
+    d = torch.empty(int(k), dtype=torch.float32, device=dev)
+    n = ctypes.c_longlong(0)
+    with torch.cuda.device(dev):
+        L.check(L.lib().cl_cross_topk(cl.handle, _ptr(posb), posb.shape[0], int(k), _ptr(a), _ptr(b), _ptr(d),
+                                      ctypes.byref(n), _stream(stream)), "cl_cross_topk")
+    return {"a": a, "b": b, "d": d, "n": n.value}
+
+
 def cl_query(cl, what, stream=None):
     v = ctypes.c_longlong(0)
     key = L.INFO[what] if isinstance(what, str) else int(what)

@@ -410,6 +410,146 @@ int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, lon
   return clk::launch_scale(scale_dev, in_dev, out_dev, count, (cudaStream_t)stream);
 }
 
+// ---- two sets: queries of set B against the cell list of set A
+namespace {
+
+int check_query(const cl_list* c, const double* posb, long long nb) {
+  if (!c || nb < 0 || nb >= 2147483647LL || (nb > 0 && !posb)) return CL_ERR_INVALID_ARG;
+  return CL_OK;
+}
+
+// Per-call workspace of the two-set queries (allocated and freed here).
+struct QueryWs {
+  int* count = nullptr;
+  int* start = nullptr;
+  int* tiles = nullptr;
+  int* meta = nullptr;
+  int* err = nullptr;
+  unsigned long long* total = nullptr;
+  ~QueryWs() {
+    cudaFree(count);
+    cudaFree(start);
+    cudaFree(tiles);
+    cudaFree(meta);
+    cudaFree(err);
+    cudaFree(total);
+  }
+};
+
+int read_err(const int* err_dev, cudaStream_t s) {
+  int v = 0;
+  if (cudaMemcpyAsync(&v, err_dev, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return CL_ERR_CUDA;
+  return v ? CL_ERR_NONFINITE : CL_OK;
+}
+
+}  // namespace
+
+int cl_cross_count(const cl_list* cc, const double* posb_dev, long long nb, unsigned long long* count_dev,
+                   void* stream) {
+  int e = check_query(cc, posb_dev, nb);
+  if (e || !count_dev) return e ? e : CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(count_dev, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
+  size_t b = 0;
+  QueryWs w;
+  if ((e = dev_alloc(&w.err, 1, &b))) return e;
+  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  if ((e = clk::launch_cross(0, *c->full, c->geo, posb_dev, nb, 0, nullptr, count_dev, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, w.err, s)))
+    return e;
+  return read_err(w.err, s);
+}
+
+int cl_cross_pairlist(const cl_list* cc, const double* posb_dev, long long nb, long long capacity, int* pa_dev,
+                      int* pb_dev, float* pd_dev, long long* npairs, void* stream) {
+  int e = check_query(cc, posb_dev, nb);
+  if (e || !npairs || capacity < 0) return e ? e : CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  for (int k = 0; k < c->geo.dim; ++k)
+    if (!(2.0 * c->geo.rc <= c->geo.w[k])) return CL_ERR_CUTOFF_TOO_LARGE;  // unique images only
+  cudaStream_t s = (cudaStream_t)stream;
+  *npairs = 0;
+  if (nb == 0) return CL_OK;
+  size_t b = 0;
+  QueryWs w;
+  if ((e = dev_alloc(&w.count, (size_t)nb, &b)) || (e = dev_alloc(&w.start, (size_t)nb + 1, &b)) ||
+      (e = dev_alloc(&w.tiles, (size_t)clk::scan_tiles_for(nb), &b)) || (e = dev_alloc(&w.meta, 4, &b)) ||
+      (e = dev_alloc(&w.err, 1, &b)))
+    return e;
+  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  if ((e = clk::launch_cross(0, *c->full, c->geo, posb_dev, nb, 0, w.count, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, nullptr, nullptr, w.err, s)))
+    return e;
+  if ((e = clk::launch_scan(w.count, nb, w.tiles, w.start, w.meta, s))) return e;
+  int total = 0, meta[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(&total, w.start + nb, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(meta, w.meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return CL_ERR_CUDA;
+  if ((e = read_err(w.err, s))) return e;
+  *npairs = total;
+  if (meta[2] > clk::kMaxSegment) return CL_ERR_UNSUPPORTED;
+  if (total > capacity) return CL_ERR_CAPACITY;
+  if (total == 0) return CL_OK;
+  if (!pa_dev || !pb_dev || !pd_dev) return CL_ERR_INVALID_ARG;
+  if ((e = clk::launch_cross(1, *c->full, c->geo, posb_dev, nb, 0, nullptr, nullptr, w.start, pa_dev, pb_dev, pd_dev,
+                             nullptr, nullptr, w.err, s)))
+    return e;
+  if ((e = clk::launch_pairs_sort((int)nb, w.count, w.start, pa_dev, pd_dev, s))) return e;
+  return cudaStreamSynchronize(s) == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int cl_cross_knn(const cl_list* cc, const double* posb_dev, long long nb, int k, int* knn_a_dev, float* knn_d_dev,
+                 void* stream) {
+  int e = check_query(cc, posb_dev, nb);
+  if (e || k < 1 || k > CL_KNN_MAX || (nb > 0 && (!knn_a_dev || !knn_d_dev))) return e ? e : CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (nb == 0) return CL_OK;
+  size_t b = 0;
+  QueryWs w;
+  if ((e = dev_alloc(&w.err, 1, &b))) return e;
+  if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  if ((e = clk::launch_cross(2, *c->full, c->geo, posb_dev, nb, k, nullptr, nullptr, nullptr, nullptr, nullptr,
+                             nullptr, knn_a_dev, knn_d_dev, w.err, s)))
+    return e;
+  return read_err(w.err, s);
+}
+
+int cl_cross_topk(const cl_list* cc, const double* posb_dev, long long nb, int k, int* a_dev, int* b_dev,
+                  float* d_dev, long long* nfound, void* stream) {
+  int e = check_query(cc, posb_dev, nb);
+  if (e || k < 1 || k > CL_KNN_MAX || !a_dev || !b_dev || !d_dev || !nfound) return e ? e : CL_ERR_INVALID_ARG;
+  cl_list* c = const_cast<cl_list*>(cc);
+  cudaStream_t s = (cudaStream_t)stream;
+  *nfound = 0;
+  size_t b = 0;
+  QueryWs w;
+  int* la = nullptr;
+  float* ld = nullptr;
+  const size_t m = (size_t)(nb > 0 ? nb : 1) * k;
+  if ((e = dev_alloc(&w.err, 2, &b)) || (e = dev_alloc(&la, m, &b)) || (e = dev_alloc(&ld, m, &b))) {
+    cudaFree(la);
+    cudaFree(ld);
+    return e;
+  }
+  if (cudaMemsetAsync(w.err, 0, 2 * sizeof(int), s) != cudaSuccess) e = CL_ERR_CUDA;
+  if (!e && nb > 0)
+    e = clk::launch_cross(2, *c->full, c->geo, posb_dev, nb, k, nullptr, nullptr, nullptr, nullptr, nullptr,
+                          nullptr, la, ld, w.err, s);
+  if (!e) e = clk::launch_topk_merge(la, ld, nb, k, a_dev, b_dev, d_dev, w.err + 1, s);
+  int found = 0;
+  if (!e && cudaMemcpyAsync(&found, w.err + 1, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    e = CL_ERR_CUDA;
+  if (!e) e = read_err(w.err, s);
+  cudaFree(la);
+  cudaFree(ld);
+  if (!e) *nfound = found;
+  return e;
+}
+
 int cl_query(const cl_list* c, int what, long long* value, void* stream) {
   if (!c || !value) return CL_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;

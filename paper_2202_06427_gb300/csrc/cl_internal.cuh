@@ -151,6 +151,15 @@ int launch_hood(const SweepArgs& A, const HoodArgs& H, int* work, int mode, cons
                 double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
                 double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s);
 
+// Two sets (cl_cross.cu): what 0 counts per query (count may be null) and their
+// total, 1 fills the pairs of each query's segment (start), 2 the per-query k
+// nearest. err: device error latch.
+int launch_cross(int what, const SweepArgs& A, const Geo& g, const double* posb, long long nb, int k, int* count,
+                 unsigned long long* total, const int* start, int* pa, int* pb, float* pd, int* knn_a, float* knn_d,
+                 int* err, cudaStream_t s);
+int launch_topk_merge(const int* la, const float* ld, long long nb, int k, int* oa, int* ob, float* od, int* found,
+                      cudaStream_t s);
+
 // Neighbour list (cl_pairs.cu). count[n], start[n+1] (scan of count), tiles,
 // meta: workspace; outputs pair_i/j/d of capacity entries.
 constexpr int kMaxSegment = 1024;  // neighbours j > i of one particle the segment sort handles
