@@ -1,5 +1,7 @@
 // cl_api.cu -- the extern "C" boundary (cellmap.h): handle lifecycle,
 // argument checks, and dispatch of the binning, sweep and reduction kernels.
+#include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -21,7 +23,7 @@ struct cl_list {
   float2* zz2;
   int* counts;
   int* cell_start;
-  unsigned char* hflag;  // per cell: 1 when the neighbourhood sweep leaves it to the per-particle sweep
+  unsigned char* hflag;  // per cell: 1 when a staged sweep (neighbourhood or pair list) leaves it to a per-particle sweep
   int* hlist;            // cells the neighbourhood sweep takes
   int* tile_sum;
   int* meta;
@@ -200,8 +202,24 @@ int run_build(cl_list* c, cudaStream_t s) {
   return clk::launch_build(c->geo, b, s);
 }
 
+// Squared radius about a cell's centre that holds every particle within rc of
+// a point of the cell: (rc + half the longest cell diagonal + a margin)^2.
+float pairs_ball2(const clk::Geo& g) {
+  double hd = 0.0;
+  for (int corner = 0; corner < (1 << g.dim); ++corner) {
+    double v[3] = {0, 0, 0};
+    for (int k = 0; k < g.dim; ++k) {
+      const double sg = ((corner >> k) & 1) ? 0.5 : -0.5;
+      for (int a = 0; a < g.dim; ++a) v[a] += sg * g.h[k * 3 + a] / g.n[k];
+    }
+    hd = std::max(hd, std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+  }
+  const double r = g.rc + hd * (1.0 + 1e-6) + 1e-4 * (g.rc + hd);
+  return (float)(r * r);
+}
+
 // Neighbour list: count pass, scan, one synchronisation to learn the total,
-// fill pass, per-segment sort.
+// fill pass (each segment sorted as it is written).
 int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   if (!r->npairs || r->capacity < 0) return CL_ERR_INVALID_ARG;
   for (int k = 0; k < c->geo.dim; ++k)
@@ -222,7 +240,8 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
     c->bytes += b;
   }
   const int dim = c->geo.dim;
-  if ((e = clk::launch_pairs_count(*c->full, dim, c->pl_count, s))) return e;
+  const float ball2 = pairs_ball2(c->geo);
+  if ((e = clk::launch_pairs_count(*c->full, dim, ball2, c->hflag, c->pl_count, s))) return e;
   if ((e = clk::launch_scan(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
   int total = 0, meta[4] = {0, 0, 0, 0};
   if (cudaMemcpyAsync(&total, c->pl_start + c->n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -234,8 +253,8 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   if (total > r->capacity) return CL_ERR_CAPACITY;
   if (total == 0) return CL_OK;
   if (!r->pair_i || !r->pair_j || !r->pair_d) return CL_ERR_INVALID_ARG;
-  if ((e = clk::launch_pairs_fill(*c->full, dim, c->pl_start, r->pair_i, r->pair_j, r->pair_d, s))) return e;
-  return clk::launch_pairs_sort(c->n, c->pl_count, c->pl_start, r->pair_j, r->pair_d, s);
+  return clk::launch_pairs_fill(*c->full, dim, ball2, c->hflag, c->pl_count, c->pl_start, r->pair_i, r->pair_j,
+                               r->pair_d, s);
 }
 
 }  // namespace

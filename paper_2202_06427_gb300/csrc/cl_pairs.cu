@@ -1,23 +1,41 @@
 // cl_pairs.cu -- the i<j neighbour list (Sec. 4.1: "the lists of pairs of
 // particles within a cutoff"), sorted by (i, j), with the FP32 distance.
 //
-//   k_pairs_count  full-shell sweep; the thread of particle i counts its
-//                  pairs with j > i (original indices), so every pair is
-//                  counted once, by its smaller index, without atomics
+//   k_pairs_cell<COUNT>  one CTA per cell stages the cell's neighbourhood
+//                  (the particles of its full stencil that lie within
+//                  rc + half a cell diagonal of its centre) in shared memory;
+//                  one warp per home particle sweeps it and counts the pairs
+//                  with j > i (original indices), so every pair is counted
+//                  once, by its smaller index, without atomics. A cell whose
+//                  neighbourhood does not fit is flagged.
 //   (scan)         exclusive prefix sum of the counts in original order:
 //                  segment of i = [start[i], start[i] + count[i])
-//   k_pairs_fill   the same sweep writes (i, j, r) into i's segment, in the
-//                  order the stencil visits the neighbour cells
-//   k_pairs_sort   one warp per segment: bitonic sort by j in shared memory
+//   k_pairs_cell<FILL>   the same staging, then the staged list's original
+//                  indices are radix-sorted, so each particle's pairs with
+//                  j > i come out of a suffix of that order in ascending j and
+//                  are written in order with coalesced stores
+//   k_pairs_count / k_pairs_fill_sorted
+//                  the flagged cells' particles, one thread (count) or one warp
+//                  (fill) per particle straight from the sorted arrays
+//   k_pairs_sort   one warp per segment, in place, for the two-set list (its
+//                  segments are filled by a per-query sweep)
 //
-// The sweep visits the pair-images of a particle; the list is only defined
-// when each pair has at most one image within rc (rc <= w_min / 2), which the
-// host checks before launching.
+// Each particle's count and fill run the same arithmetic in the same kernel
+// family, so the fill keeps exactly count[i] pairs (the write is clamped to
+// count[i] all the same). The sweep visits the pair-images of a particle; the
+// list is only defined when each pair has at most one image within rc
+// (rc <= w_min / 2), which the host checks before launching.
 #include <climits>
 
 #include "cl_sweep.cuh"
 
 namespace clk {
+
+// Linear cell index of sorted particle p.
+__device__ __forceinline__ int cell_of(const SweepArgs& A, int p) {
+  const unsigned cc = A.cellc[p];
+  return (int)(cc & 1023u) + A.nx * ((int)((cc >> 10) & 1023u) + A.ny * (int)(cc >> 20));
+}
 
 struct RedPairCount {
   static constexpr bool kFull = true;
@@ -26,27 +44,12 @@ struct RedPairCount {
   __device__ void hit(Acc& x, float, float, float, float, int j) const { x.n += (j > x.a) ? 1 : 0; }
 };
 
-struct RedPairFill {
-  static constexpr bool kFull = true;
-  int* pi;
-  int* pj;
-  float* pd;
-  struct Acc { int a; int pos; };
-  __device__ void init(Acc&) const {}
-  __device__ void hit(Acc& x, float, float, float, float d2, int j) const {
-    if (j > x.a) {
-      pi[x.pos] = x.a;
-      pj[x.pos] = j;
-      pd[x.pos] = d2 * rsqrt_nr(d2);
-      x.pos++;
-    }
-  }
-};
-
 template <int DIM>
-__global__ void __launch_bounds__(256) k_pairs_count(const __grid_constant__ SweepArgs A, int* __restrict__ count) {
+__global__ void __launch_bounds__(256) k_pairs_count(const __grid_constant__ SweepArgs A,
+                                                     const unsigned char* __restrict__ flag, int* __restrict__ count) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= A.n) return;
+  if (flag && !flag[cell_of(A, p)]) return;
   RedPairCount red;
   RedPairCount::Acc acc;
   red.init(acc);
@@ -54,22 +57,6 @@ __global__ void __launch_bounds__(256) k_pairs_count(const __grid_constant__ Swe
   float4 pi;
   sweep_particle<DIM>(A, red, acc, p, pi);
   count[acc.a] = acc.n;
-}
-
-template <int DIM>
-__global__ void __launch_bounds__(256) k_pairs_fill(const __grid_constant__ SweepArgs A, const int* __restrict__ start,
-                                                    int* pi_out, int* pj_out, float* pd_out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= A.n) return;
-  RedPairFill red;
-  red.pi = pi_out;
-  red.pj = pj_out;
-  red.pd = pd_out;
-  RedPairFill::Acc acc;
-  acc.a = __float_as_int(A.xs[p].w);
-  acc.pos = start[acc.a];
-  float4 pi;
-  sweep_particle<DIM>(A, red, acc, p, pi);
 }
 
 constexpr int kSortWarps = 4;
@@ -126,21 +113,551 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int
   }
 }
 
+// Shared pieces of the pair-list sweeps. A warp takes the stencil 32 entries
+// at a time, one per lane: each lane finds its neighbour cell's particle
+// range, a warp scan lays the ranges end to end, and the warp walks the
+// concatenation 32 candidates per step (a shuffle binary search finds each
+// candidate's entry), so the lanes stay busy however small the cells are. The
+// kept pairs of a particle are compacted with a ballot into the warp's
+// shared-memory segment, sorted by j in registers (bitonic) and written to
+// [start[a], start[a] + count[a]) with coalesced stores. Segments are at most
+// kMaxSegment long (the host checks the counts first).
+constexpr int kFillWarps = 4;
+constexpr int kStage = 2048;  // staged neighbourhood of one cell
+constexpr int kSegPad = kMaxSegment + kMaxSegment / 32;
+
+// Segment buffer index with one pad word per 32: conflict-free both for lane i
+// at i (coalesced order) and for lane l at l * E + e (blocked order, E <= 32).
+__device__ __forceinline__ int seg_at(int i) { return i + (i >> 5); }
+
+// Bitonic sort, ascending by key, of 32 E elements held E per lane in blocked
+// order (element lane * E + e). Pairs closer than E apart are in one lane's
+// registers; farther ones are exchanged with a shuffle.
+template <int E>
+__device__ __forceinline__ void sort_blocked(int (&k)[E], float (&v)[E], int lane) {
+#pragma unroll
+  for (int size = 2; size <= 32 * E; size <<= 1) {
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= E) {
+        const int ls = stride / E;
+        const bool lower = (lane & ls) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const bool up = ((lane * E + e) & size) == 0;
+          const int ok = __shfl_xor_sync(0xffffffffu, k[e], ls);
+          const float ov = __shfl_xor_sync(0xffffffffu, v[e], ls);
+          const bool take = (lower == up) ? (ok < k[e]) : (ok > k[e]);
+          k[e] = take ? ok : k[e];
+          v[e] = take ? ov : v[e];
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if ((e & stride) == 0) {
+            const int f = e | stride;
+            const bool up = ((lane * E + e) & size) == 0;
+            const bool sw = up ? (k[e] > k[f]) : (k[e] < k[f]);
+            const int tk = k[e];
+            const float tv = v[e];
+            k[e] = sw ? k[f] : k[e];
+            v[e] = sw ? v[f] : v[e];
+            k[f] = sw ? tk : k[f];
+            v[f] = sw ? tv : v[f];
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void sort_segment_regs(int* K, float* V, int L, int lane) {
+  int k[E];
+  float v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane * E + e;
+    k[e] = i < L ? K[seg_at(i)] : INT_MAX;
+    v[e] = i < L ? V[seg_at(i)] : 0.f;
+  }
+  sort_blocked<E>(k, v, lane);
+  __syncwarp();
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int i = lane * E + e;
+    if (i < L) {
+      K[seg_at(i)] = k[e];
+      V[seg_at(i)] = v[e];
+    }
+  }
+  __syncwarp();
+}
+
+// Segments longer than 16 per lane: the same network in shared memory.
+__device__ void sort_segment_smem(int* K, float* V, int L, int lane) {
+  int P = 32;
+  while (P < L) P <<= 1;
+  for (int i = L + lane; i < P; i += 32) {
+    K[seg_at(i)] = INT_MAX;
+    V[seg_at(i)] = 0.f;
+  }
+  __syncwarp();
+  for (int size = 2; size <= P; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int t = lane; t < (P >> 1); t += 32) {
+        const int lo = 2 * stride * (t / stride) + (t % stride);
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const int ka = K[seg_at(lo)], kb = K[seg_at(hi)];
+        if ((ka > kb) == up) {
+          K[seg_at(lo)] = kb;
+          K[seg_at(hi)] = ka;
+          const float va = V[seg_at(lo)];
+          V[seg_at(lo)] = V[seg_at(hi)];
+          V[seg_at(hi)] = va;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+
+// Stencil entries k0 + lane of cell (cx, cy, cz): the lane's range [j0, j0 +
+// len) of sorted particles, its shift (stencil shift + (bx, by, bz)) and, over
+// the warp, the exclusive offsets of the ranges laid end to end and their total.
+struct Chunk {
+  int j0, len, excl, total;
+  float sx, sy, sz;
+};
+
+template <int DIM>
+__device__ __forceinline__ Chunk chunk_ranges(const SweepArgs& A, const float4* stab, int k0, int lane, int cx,
+                                              int cy, int cz, float bx, float by, float bz) {
+  Chunk ch;
+  ch.j0 = 0;
+  ch.len = 0;
+  ch.sx = ch.sy = ch.sz = 0.f;
+  const int k = k0 + lane;
+  if (k < A.noff) {
+    const float4 e = stab[k];
+    const unsigned d = __float_as_uint(e.w);
+    int x2 = cx + (int)(d & 1023u);
+    x2 -= (x2 >= A.nx) ? A.nx : 0;
+    int y2 = cy + (int)((d >> 10) & 1023u);
+    y2 -= (y2 >= A.ny) ? A.ny : 0;
+    int z2 = 0;
+    if (DIM == 3) {
+      z2 = cz + (int)(d >> 20);
+      z2 -= (z2 >= A.nz) ? A.nz : 0;
+    }
+    const int c = x2 + A.nx * (y2 + A.ny * z2);
+    ch.j0 = __ldg(A.cell_start + c);
+    ch.len = __ldg(A.cell_start + c + 1) - ch.j0;
+    ch.sx = e.x + bx;
+    ch.sy = e.y + by;
+    ch.sz = e.z + bz;
+  }
+  int inc = ch.len;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    inc += lane >= o ? u : 0;
+  }
+  ch.total = __shfl_sync(0xffffffffu, inc, 31);
+  ch.excl = inc - ch.len;
+  return ch;
+}
+
+// Candidate t of the chunk: its sorted index and the shift of its entry.
+__device__ __forceinline__ int chunk_candidate(const Chunk& ch, int t, float& ax, float& ay, float& az) {
+  int l = 0;  // last entry whose range starts at or before t
+#pragma unroll
+  for (int b = 16; b >= 1; b >>= 1) {
+    const int u = __shfl_sync(0xffffffffu, ch.excl, l + b);
+    l += (u <= t) ? b : 0;
+  }
+  ax = __shfl_sync(0xffffffffu, ch.sx, l);
+  ay = __shfl_sync(0xffffffffu, ch.sy, l);
+  az = __shfl_sync(0xffffffffu, ch.sz, l);
+  return __shfl_sync(0xffffffffu, ch.j0, l) + (t - __shfl_sync(0xffffffffu, ch.excl, l));
+}
+
+__device__ __forceinline__ void stencil_to_smem(const SweepArgs& A, float4* stab) {
+  for (int k = threadIdx.x; k < A.noff; k += blockDim.x) {
+    const Off& o = A.off[k];
+    stab[k] = make_float4(o.sx, o.sy, o.sz,
+                          __uint_as_float((unsigned)o.dx | ((unsigned)o.dy << 10) | ((unsigned)o.dz << 20)));
+  }
+}
+
+// Sorts the warp's segment of nw kept pairs by j and writes it at base.
+__device__ __forceinline__ void segment_out(int* K, float* V, int nw, int a, int base, int lane, int* pi_out,
+                                            int* pj_out, float* pd_out) {
+  if (nw <= 1) {
+  } else if (nw <= 32) {
+    sort_segment_regs<1>(K, V, nw, lane);
+  } else if (nw <= 64) {
+    sort_segment_regs<2>(K, V, nw, lane);
+  } else if (nw <= 128) {
+    sort_segment_regs<4>(K, V, nw, lane);
+  } else if (nw <= 256) {
+    sort_segment_regs<8>(K, V, nw, lane);
+  } else if (nw <= 512) {
+    sort_segment_regs<16>(K, V, nw, lane);
+  } else {
+    sort_segment_smem(K, V, nw, lane);
+  }
+  for (int i = lane; i < nw; i += 32) {
+    pi_out[base + i] = a;
+    pj_out[base + i] = K[seg_at(i)];
+    pd_out[base + i] = V[seg_at(i)];
+  }
+  __syncwarp();
+}
+
+// Flagged cells' particles, one warp per particle, straight from the sorted
+// arrays: the candidate's distance is x_j + (s_o - x_i), equal in IEEE
+// arithmetic to x_j - (x_i - s_o) of k_pairs_count (same fused multiply-adds).
+template <int DIM>
+__global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const __grid_constant__ SweepArgs A,
+                                                                          const unsigned char* __restrict__ flag,
+                                                                          const int* __restrict__ count,
+                                                                          const int* __restrict__ start,
+                                                                          int* __restrict__ pi_out,
+                                                                          int* __restrict__ pj_out,
+                                                                          float* __restrict__ pd_out) {
+  extern __shared__ float4 stab[];  // per entry: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
+  __shared__ int sk[kFillWarps][kSegPad];
+  __shared__ float sv[kFillWarps][kSegPad];
+  stencil_to_smem(A, stab);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int* K = sk[warp];
+  float* V = sv[warp];
+  for (int p = blockIdx.x * kFillWarps + warp; p < A.n; p += gridDim.x * kFillWarps) {
+    if (!flag[cell_of(A, p)]) continue;
+    const float4 pi = A.xs[p];
+    const int a = __float_as_int(pi.w);
+    const unsigned cc = A.cellc[p];
+    const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
+    int L = 0;
+    for (int k0 = 0; k0 < A.noff; k0 += 32) {
+      const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, -pi.x, -pi.y, -pi.z);
+      for (int t0 = 0; t0 < ch.total; t0 += 32) {
+        const int t = t0 + lane;
+        float ax, ay, az;
+        const int j = chunk_candidate(ch, t, ax, ay, az);
+        bool keep = false;
+        int jo = 0;
+        float d2 = 0.f;
+        if (t < ch.total) {
+          const float4 q = __ldg(&A.xs[j]);
+          jo = __float_as_int(q.w);
+          const float dx = q.x + ax, dy = q.y + ay;
+          const float dz = DIM == 3 ? q.z + az : 0.f;
+          d2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
+          keep = jo > a && d2 < A.rc2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+          const int e = L + __popc(m & lt);
+          if (e < kMaxSegment) {
+            K[seg_at(e)] = jo;
+            V[seg_at(e)] = d2 * rsqrt_nr(d2);
+          }
+        }
+        L += __popc(m);
+      }
+    }
+    __syncwarp();
+    const int nw = min(min(L, kMaxSegment), __ldg(count + a));
+    segment_out(K, V, nw, a, __ldg(start + a), lane, pi_out, pj_out, pd_out);
+  }
+}
+
+// Stable LSD radix sort (8-bit digits) of the staged list's original indices,
+// the whole CTA (W warps) taking part: keys jo - kmin with slots 0..S-1 into
+// st. Each warp ranks a fixed span of positions in order with
+// __match_any_sync, and the (digit, warp) offsets come from one exclusive scan
+// per pass, so equal digits keep their order. Returns the buffers that hold
+// the result.
+template <int W>
+__device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k0, unsigned* k1, unsigned short* s0,
+                                            unsigned short* s1, int* cnt, int* scal, unsigned*& keys,
+                                            unsigned short*& slots, int& kmin) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  if (threadIdx.x == 0) {
+    scal[1] = INT_MAX;
+    scal[2] = 0;
+  }
+  __syncthreads();
+  int lo = INT_MAX, hi = 0;
+  for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    const int jo = __float_as_int(st[i].w);
+    lo = min(lo, jo);
+    hi = max(hi, jo);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if (lane == 0) {
+    atomicMin(scal + 1, lo);
+    atomicMax(scal + 2, hi);
+  }
+  __syncthreads();
+  kmin = scal[1];
+  const unsigned range = (unsigned)(scal[2] - kmin);
+  for (int i = threadIdx.x; i < S; i += blockDim.x) {
+    k0[i] = (unsigned)(__float_as_int(st[i].w) - kmin);
+    s0[i] = (unsigned short)i;
+  }
+  __syncthreads();
+  const int bits = range ? 32 - __clz(range) : 0;
+  const int span = (((S + W - 1) / W) + 31) & ~31;
+  const int b0 = min(S, warp * span), b1 = min(S, b0 + span);
+  for (int sh = 0; sh < bits; sh += 8) {
+    for (int i = threadIdx.x; i < 256 * W; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int r = b0; r < b1; r += 32) {
+      const int i = r + lane;
+      const bool ok = i < b1;
+      const int d = ok ? (int)((k0[i] >> sh) & 255u) : 256 + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (ok && lane == __ffs(peers) - 1) cnt[d * W + warp] += __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {  // exclusive scan of cnt in (digit, warp) order; 8 entries per thread
+      const int per = 256 * W / blockDim.x;
+      int loc = 0;
+      for (int e = 0; e < per; ++e) loc += cnt[threadIdx.x * per + e];
+      int inc = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        inc += lane >= o ? u : 0;
+      }
+      if (lane == 31) scal[4 + warp] = inc;
+      __syncthreads();
+      int off = inc - loc;
+      for (int w = 0; w < warp; ++w) off += scal[4 + w];
+      for (int e = 0; e < per; ++e) {
+        const int v = cnt[threadIdx.x * per + e];
+        cnt[threadIdx.x * per + e] = off;
+        off += v;
+      }
+    }
+    __syncthreads();
+    for (int r = b0; r < b1; r += 32) {
+      const int i = r + lane;
+      const bool ok = i < b1;
+      const unsigned key = ok ? k0[i] : 0u;
+      const int d = ok ? (int)((key >> sh) & 255u) : 256 + lane;
+      const unsigned peers = __match_any_sync(0xffffffffu, d);
+      const int base = ok ? cnt[d * W + warp] : 0;
+      __syncwarp();
+      if (ok) {
+        if (lane == __ffs(peers) - 1) cnt[d * W + warp] = base + __popc(peers);
+        const int pos = base + __popc(peers & lt);
+        k1[pos] = key;
+        s1[pos] = s0[i];
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    unsigned* tk = k0;
+    k0 = k1;
+    k1 = tk;
+    unsigned short* ts = s0;
+    s0 = s1;
+    s1 = ts;
+  }
+  keys = k0;
+  slots = s0;
+}
+
+// One CTA of W warps per cell (grid-stride over the cells). The stencil
+// entries are shared among the warps 32 at a time; each warp appends the
+// particles of its entries that lie within sqrt(ball2) of the cell centre,
+// shifted to the cell's frame (x_j + s_o), to the staged list. Then warp w
+// sweeps home particles w, w + W, ... against it (distance (x_j + s_o) - x_i).
+// COUNT: count[a] = pairs with j > a; a cell whose list does not fit gets
+// flag 1 (else 0). FILL: flagged cells are skipped; the staged list is ordered
+// by original index (radix sort of its indices), so a particle's pairs with
+// j > a come from a suffix of that order in ascending j and are written in
+// order, coalesced, as the ballot finds them.
+template <int DIM, bool FILL>
+__global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
+                                                                               float ball2,
+                                                                               unsigned char* __restrict__ flag,
+                                                                               int* __restrict__ count,
+                                                                               const int* __restrict__ start,
+                                                                               int* __restrict__ pi_out,
+                                                                               int* __restrict__ pj_out,
+                                                                               float* __restrict__ pd_out) {
+  constexpr int W = FILL ? 8 : 4;
+  extern __shared__ float4 smem[];
+  float4* st = smem;           // staged neighbourhood: (x, y, z in the cell's frame, original index)
+  float4* stab = st + kStage;  // stencil: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
+  int* scal = reinterpret_cast<int*>(stab + A.noff);  // [0] staged count, [1..2] index range, [4..] warp sums
+  unsigned* rk0 = reinterpret_cast<unsigned*>(scal + 16);  // FILL: radix keys, slots, counters
+  unsigned* rk1 = rk0 + kStage;
+  int* cnt = reinterpret_cast<int*>(rk1 + kStage);
+  unsigned short* rs0 = reinterpret_cast<unsigned short*>(cnt + 256 * W);
+  unsigned short* rs1 = rs0 + kStage;
+  stencil_to_smem(A, stab);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int ncells = A.nx * A.ny * A.nz;
+  for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
+    const int h0 = __ldg(A.cell_start + c), h1 = __ldg(A.cell_start + c + 1);
+    if (h1 == h0) continue;
+    if (FILL && flag[c]) continue;
+    const int cx = c % A.nx, cy = (c / A.nx) % A.ny, cz = c / (A.nx * A.ny);
+    if (threadIdx.x == 0) scal[0] = 0;
+    __syncthreads();
+    for (int k0 = warp * 32; k0 < A.noff; k0 += 32 * W) {
+      const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, 0.f, 0.f, 0.f);
+      for (int t0 = 0; t0 < ch.total; t0 += 32) {
+        const int t = t0 + lane;
+        float ax, ay, az;
+        const int j = chunk_candidate(ch, t, ax, ay, az);
+        bool keep = false;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (t < ch.total) {
+          const float4 q = __ldg(&A.xs[j]);
+          v.x = q.x + ax;
+          v.y = q.y + ay;
+          v.z = DIM == 3 ? q.z + az : 0.f;
+          v.w = q.w;
+          keep = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)) < ball2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(scal, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+          const int e = base + __popc(m & lt);
+          if (e < kStage) st[e] = v;
+        }
+      }
+    }
+    __syncthreads();
+    const int S = scal[0];
+    if (S <= kStage) {
+      unsigned* keys = rk0;
+      unsigned short* slots = rs0;
+      int kmin = 0;
+      if (FILL) stage_radix<W>(st, S, rk0, rk1, rs0, rs1, cnt, scal, keys, slots, kmin);
+      for (int p = h0 + warp; p < h1; p += W) {
+        const float4 pi = A.xs[p];
+        const int a = __float_as_int(pi.w);
+        int first = 0;  // FILL: first position (in index order) with index > a
+        if (FILL && a >= kmin) {
+          const unsigned ka = (unsigned)(a - kmin);
+          int lo = 0, hi = S;
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (keys[mid] > ka) hi = mid;
+            else lo = mid + 1;
+          }
+          first = lo;
+        }
+        const int cnt_a = FILL ? __ldg(count + a) : 0;
+        const int base = FILL ? __ldg(start + a) : 0;
+        int L = 0;
+#pragma unroll 2
+        for (int t0 = first; t0 < S; t0 += 32) {
+          const int t = t0 + lane;
+          bool keep = false;
+          int jo = 0;
+          float d2 = 0.f;
+          if (t < S) {
+            const float4 q = st[FILL ? (int)slots[t] : t];
+            jo = __float_as_int(q.w);
+            const float dx = q.x - pi.x, dy = q.y - pi.y;
+            const float dz = DIM == 3 ? q.z - pi.z : 0.f;
+            d2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
+            keep = jo > a && d2 < A.rc2;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (FILL && keep) {
+            const int e = L + __popc(m & lt);
+            if (e < cnt_a) {
+              pi_out[base + e] = a;
+              pj_out[base + e] = jo;
+              pd_out[base + e] = d2 * rsqrt_nr(d2);
+            }
+          }
+          L += __popc(m);
+        }
+        if (!FILL && lane == 0) count[a] = L;
+      }
+    }
+    if (!FILL && threadIdx.x == 0) flag[c] = S > kStage ? 1 : 0;
+    __syncthreads();
+  }
+}
+
 static int blocks_of(int n) { return n > 0 ? (n + 255) / 256 : 1; }
 
-int launch_pairs_count(const SweepArgs& A, int dim, int* count, cudaStream_t s) {
-  if (A.n > 0) {
-    if (dim == 3) k_pairs_count<3><<<blocks_of(A.n), 256, 0, s>>>(A, count);
-    else k_pairs_count<2><<<blocks_of(A.n), 256, 0, s>>>(A, count);
+size_t pairs_cell_smem(int noff, bool fill) {
+  const size_t head = (size_t)(kStage + noff) * sizeof(float4) + 16 * sizeof(int);
+  return fill ? head + 2 * kStage * sizeof(unsigned) + 256 * 8 * sizeof(int) + 2 * kStage * sizeof(unsigned short)
+              : head;
+}
+
+template <int DIM, bool FILL>
+static int launch_cell(const SweepArgs& A, float ball2, unsigned char* flag, int* count, const int* start, int* pi,
+                       int* pj, float* pd, cudaStream_t s) {
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    int dev = 0, per = 0;
+    const int most = (int)pairs_cell_smem(kMaxOff, FILL);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k_pairs_cell<DIM, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_cell<DIM, FILL>, FILL ? 256 : 128,
+                                                      pairs_cell_smem(125, FILL)) != cudaSuccess ||
+        per < 1)
+      return CL_ERR_CUDA;
+    per_sm = per;
   }
+  long long blocks = (long long)sms * per_sm;
+  const long long ncells = (long long)A.nx * A.ny * A.nz;
+  if (blocks > ncells) blocks = ncells;
+  k_pairs_cell<DIM, FILL><<<(int)blocks, FILL ? 256 : 128, pairs_cell_smem(A.noff, FILL), s>>>(A, ball2, flag, count,
+                                                                                              start, pi, pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
-int launch_pairs_fill(const SweepArgs& A, int dim, const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
-  if (A.n > 0) {
-    if (dim == 3) k_pairs_fill<3><<<blocks_of(A.n), 256, 0, s>>>(A, start, pi, pj, pd);
-    else k_pairs_fill<2><<<blocks_of(A.n), 256, 0, s>>>(A, start, pi, pj, pd);
-  }
+int launch_pairs_count(const SweepArgs& A, int dim, float ball2, unsigned char* flag, int* count, cudaStream_t s) {
+  if (A.n <= 0) return CL_OK;
+  const int e = dim == 3 ? launch_cell<3, false>(A, ball2, flag, count, nullptr, nullptr, nullptr, nullptr, s)
+                         : launch_cell<2, false>(A, ball2, flag, count, nullptr, nullptr, nullptr, nullptr, s);
+  if (e) return e;
+  if (dim == 3) k_pairs_count<3><<<blocks_of(A.n), 256, 0, s>>>(A, flag, count);
+  else k_pairs_count<2><<<blocks_of(A.n), 256, 0, s>>>(A, flag, count);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned char* flag, const int* count,
+                      const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
+  if (A.n <= 0) return CL_OK;
+  unsigned char* fl = const_cast<unsigned char*>(flag);  // only read by the fill pass
+  int* cn = const_cast<int*>(count);                     // likewise
+  const int e = dim == 3 ? launch_cell<3, true>(A, ball2, fl, cn, start, pi, pj, pd, s)
+                         : launch_cell<2, true>(A, ball2, fl, cn, start, pi, pj, pd, s);
+  if (e) return e;
+  long long blocks = (A.n + kFillWarps - 1) / kFillWarps;
+  if (blocks > 152 * 6) blocks = 152 * 6;
+  const size_t dyn = (size_t)A.noff * sizeof(float4);
+  if (dim == 3) k_pairs_fill_sorted<3><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd);
+  else k_pairs_fill_sorted<2><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
