@@ -189,7 +189,7 @@ int cl_query(const cl_list* cl, int what, long long* value, void* stream);
  * FP32 distance; *npairs (host) receives the number of pairs. Same capacity
  * protocol as CL_RED_PAIRLIST (CL_ERR_CAPACITY: call again with capacity >=
  * *npairs); requires unique images (cutoff <= w_min / 2, else
- * CUTOFF_TOO_LARGE); UNSUPPORTED when one b has more than 1024 neighbours.
+ * CUTOFF_TOO_LARGE).
  *
  * cl_cross_knn: for each b its k nearest a within the cutoff, ascending by
  * distance (ties: smaller a first): knn_a_dev[b*k + q] (a, or -1 when b has

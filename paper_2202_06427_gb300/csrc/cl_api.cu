@@ -36,6 +36,7 @@ struct cl_list {
   int* pl_start;
   int* pl_tiles;
   int* pl_meta;
+  int* pl_long;  // particles whose segments are sorted by the long-segment pass
   // device copies of the stencils (for sweeps compiled outside the library)
   clk::Off* d_off_half;
   clk::Off* d_off_full;
@@ -94,6 +95,7 @@ void free_all(cl_list* c) {
   cudaFree(c->pl_start);
   cudaFree(c->pl_tiles);
   cudaFree(c->pl_meta);
+  cudaFree(c->pl_long);
   delete c->half;
   delete c->full;
   delete c->hood;
@@ -229,12 +231,14 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
     size_t b = 0;
     const size_t n = (size_t)c->n;
     if ((e = dev_alloc(&c->pl_count, n, &b)) || (e = dev_alloc(&c->pl_start, n + 1, &b)) ||
-        (e = dev_alloc(&c->pl_tiles, (size_t)clk::scan_tiles_for(c->n), &b)) || (e = dev_alloc(&c->pl_meta, 4, &b))) {
+        (e = dev_alloc(&c->pl_tiles, (size_t)clk::scan_tiles_for(c->n), &b)) || (e = dev_alloc(&c->pl_meta, 4, &b)) ||
+        (e = dev_alloc(&c->pl_long, n, &b))) {
       cudaFree(c->pl_count);
       cudaFree(c->pl_start);
       cudaFree(c->pl_tiles);
       cudaFree(c->pl_meta);
-      c->pl_count = c->pl_start = c->pl_tiles = c->pl_meta = nullptr;
+      cudaFree(c->pl_long);
+      c->pl_count = c->pl_start = c->pl_tiles = c->pl_meta = c->pl_long = nullptr;
       return e;
     }
     c->bytes += b;
@@ -249,12 +253,11 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
       cudaStreamSynchronize(s) != cudaSuccess)
     return CL_ERR_CUDA;
   *r->npairs = total;
-  if (meta[2] > clk::kMaxSegment) return CL_ERR_UNSUPPORTED;
   if (total > r->capacity) return CL_ERR_CAPACITY;
   if (total == 0) return CL_OK;
   if (!r->pair_i || !r->pair_j || !r->pair_d) return CL_ERR_INVALID_ARG;
   return clk::launch_pairs_fill(*c->full, dim, ball2, c->hflag, c->pl_count, c->pl_start, r->pair_i, r->pair_j,
-                               r->pair_d, s);
+                               r->pair_d, c->pl_long, c->pl_meta + 3, s);
 }
 
 }  // namespace
@@ -444,8 +447,10 @@ struct QueryWs {
   int* tiles = nullptr;
   int* meta = nullptr;
   int* err = nullptr;
+  int* longs = nullptr;
   unsigned long long* total = nullptr;
   ~QueryWs() {
+    cudaFree(longs);
     cudaFree(count);
     cudaFree(start);
     cudaFree(tiles);
@@ -496,7 +501,7 @@ int cl_cross_pairlist(const cl_list* cc, const double* posb_dev, long long nb, l
   QueryWs w;
   if ((e = dev_alloc(&w.count, (size_t)nb, &b)) || (e = dev_alloc(&w.start, (size_t)nb + 1, &b)) ||
       (e = dev_alloc(&w.tiles, (size_t)clk::scan_tiles_for(nb), &b)) || (e = dev_alloc(&w.meta, 4, &b)) ||
-      (e = dev_alloc(&w.err, 1, &b)))
+      (e = dev_alloc(&w.err, 1, &b)) || (e = dev_alloc(&w.longs, (size_t)nb, &b)))
     return e;
   if (cudaMemsetAsync(w.err, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if ((e = clk::launch_cross(0, *c->full, c->geo, posb_dev, nb, 0, w.count, nullptr, nullptr, nullptr, nullptr,
@@ -509,14 +514,13 @@ int cl_cross_pairlist(const cl_list* cc, const double* posb_dev, long long nb, l
     return CL_ERR_CUDA;
   if ((e = read_err(w.err, s))) return e;
   *npairs = total;
-  if (meta[2] > clk::kMaxSegment) return CL_ERR_UNSUPPORTED;
   if (total > capacity) return CL_ERR_CAPACITY;
   if (total == 0) return CL_OK;
   if (!pa_dev || !pb_dev || !pd_dev) return CL_ERR_INVALID_ARG;
   if ((e = clk::launch_cross(1, *c->full, c->geo, posb_dev, nb, 0, nullptr, nullptr, w.start, pa_dev, pb_dev, pd_dev,
                              nullptr, nullptr, w.err, s)))
     return e;
-  if ((e = clk::launch_pairs_sort((int)nb, w.count, w.start, pa_dev, pd_dev, s))) return e;
+  if ((e = clk::launch_pairs_sort((int)nb, w.count, w.start, pa_dev, pd_dev, w.longs, w.meta + 3, s))) return e;
   return cudaStreamSynchronize(s) == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 

@@ -16,9 +16,13 @@
 //                  are written in order with coalesced stores
 //   k_pairs_count / k_pairs_fill_sorted
 //                  the flagged cells' particles, one thread (count) or one warp
-//                  (fill) per particle straight from the sorted arrays
+//                  (fill) per particle straight from the sorted arrays; a
+//                  segment longer than kMaxSegment is written unsorted and
+//                  listed for k_pairs_sort_long
 //   k_pairs_sort   one warp per segment, in place, for the two-set list (its
-//                  segments are filled by a per-query sweep)
+//                  segments are filled by a per-query sweep); longer segments
+//                  are listed for k_pairs_sort_long
+//   k_pairs_sort_long  one CTA per listed segment, in place in global memory
 //
 // Each particle's count and fill run the same arithmetic in the same kernel
 // family, so the fill keeps exactly count[i] pairs (the write is clamped to
@@ -63,9 +67,12 @@ constexpr int kSortWarps = 4;
 
 // One warp per segment (grid-stride): bitonic sort of up to kMaxSegment keys
 // (j, distinct within a segment) with their distances, in shared memory.
+// Longer segments are appended to longs[] (counter *nlong) for
+// k_pairs_sort_long.
 __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int* __restrict__ count,
                                                                const int* __restrict__ start, int* __restrict__ pj,
-                                                               float* __restrict__ pd) {
+                                                               float* __restrict__ pd, int* __restrict__ longs,
+                                                               int* __restrict__ nlong) {
   __shared__ int sk[kSortWarps][kMaxSegment];
   __shared__ float sv[kSortWarps][kMaxSegment];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -73,7 +80,11 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int
   float* V = sv[warp];
   for (int a = blockIdx.x * kSortWarps + warp; a < n; a += gridDim.x * kSortWarps) {
     const int L = count[a];
-    if (L <= 1 || L > kMaxSegment) continue;  // the host refuses lists with longer segments
+    if (L <= 1) continue;
+    if (L > kMaxSegment) {
+      if (lane == 0) longs[atomicAdd(nlong, 1)] = a;
+      continue;
+    }
     const int base = start[a];
     int P = 32;
     while (P < L) P <<= 1;
@@ -110,6 +121,53 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int
       pd[base + k] = V[k];
     }
     __syncwarp();
+  }
+}
+
+// One CTA per listed segment (grid-stride over the *nlong entries): the
+// segment sorted by j in place in global memory by a bitonic network whose
+// compare-exchanges all put the smaller key first (each merge opens with the
+// mirrored pairing i <-> size - 1 - i of its block), padded to a power of two
+// with virtual +inf keys past the end, which never move.
+__global__ void __launch_bounds__(1024) k_pairs_sort_long(const int* __restrict__ longs,
+                                                         const int* __restrict__ nlong,
+                                                         const int* __restrict__ count,
+                                                         const int* __restrict__ start, int* __restrict__ pj,
+                                                         float* __restrict__ pd) {
+  const int m = *nlong;
+  for (int q = blockIdx.x; q < m; q += gridDim.x) {
+    const int a = longs[q];
+    const int L = count[a];
+    int* K = pj + start[a];
+    float* V = pd + start[a];
+    int P = 2;
+    while (P < L) P <<= 1;
+    for (int size = 2; size <= P; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+          int lo, hi;
+          if (stride == (size >> 1)) {
+            const int blk = t / stride, off = t - blk * stride;
+            lo = blk * size + off;
+            hi = blk * size + size - 1 - off;
+          } else {
+            lo = ((t & ~(stride - 1)) << 1) | (t & (stride - 1));
+            hi = lo + stride;
+          }
+          if (hi < L) {
+            const int ka = K[lo], kb = K[hi];
+            if (ka > kb) {
+              K[lo] = kb;
+              K[hi] = ka;
+              const float va = V[lo];
+              V[lo] = V[hi];
+              V[hi] = va;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
   }
 }
 
@@ -327,7 +385,9 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
                                                                           const int* __restrict__ start,
                                                                           int* __restrict__ pi_out,
                                                                           int* __restrict__ pj_out,
-                                                                          float* __restrict__ pd_out) {
+                                                                          float* __restrict__ pd_out,
+                                                                          int* __restrict__ longs,
+                                                                          int* __restrict__ nlong) {
   extern __shared__ float4 stab[];  // per entry: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
   __shared__ int sk[kFillWarps][kSegPad];
   __shared__ float sv[kFillWarps][kSegPad];
@@ -343,6 +403,8 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
     const int a = __float_as_int(pi.w);
     const unsigned cc = A.cellc[p];
     const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
+    const int cnt_a = __ldg(count + a), base = __ldg(start + a);
+    const bool big = cnt_a > kMaxSegment;  // written unsorted, sorted by k_pairs_sort_long
     int L = 0;
     for (int k0 = 0; k0 < A.noff; k0 += 32) {
       const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, -pi.x, -pi.y, -pi.z);
@@ -364,7 +426,13 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         if (keep) {
           const int e = L + __popc(m & lt);
-          if (e < kMaxSegment) {
+          if (big) {
+            if (e < cnt_a) {
+              pi_out[base + e] = a;
+              pj_out[base + e] = jo;
+              pd_out[base + e] = d2 * rsqrt_nr(d2);
+            }
+          } else if (e < kMaxSegment) {
             K[seg_at(e)] = jo;
             V[seg_at(e)] = d2 * rsqrt_nr(d2);
           }
@@ -373,8 +441,11 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
       }
     }
     __syncwarp();
-    const int nw = min(min(L, kMaxSegment), __ldg(count + a));
-    segment_out(K, V, nw, a, __ldg(start + a), lane, pi_out, pj_out, pd_out);
+    if (big) {
+      if (lane == 0) longs[atomicAdd(nlong, 1)] = a;
+    } else {
+      segment_out(K, V, min(min(L, kMaxSegment), cnt_a), a, base, lane, pi_out, pj_out, pd_out);
+    }
   }
 }
 
@@ -645,8 +716,14 @@ int launch_pairs_count(const SweepArgs& A, int dim, float ball2, unsigned char* 
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
+static int launch_sort_long(const int* longs, const int* nlong, const int* count, const int* start, int* pj,
+                            float* pd, cudaStream_t s) {
+  k_pairs_sort_long<<<152, 1024, 0, s>>>(longs, nlong, count, start, pj, pd);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
 int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned char* flag, const int* count,
-                      const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
+                      const int* start, int* pi, int* pj, float* pd, int* longs, int* nlong, cudaStream_t s) {
   if (A.n <= 0) return CL_OK;
   unsigned char* fl = const_cast<unsigned char*>(flag);  // only read by the fill pass
   int* cn = const_cast<int*>(count);                     // likewise
@@ -656,18 +733,24 @@ int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned c
   long long blocks = (A.n + kFillWarps - 1) / kFillWarps;
   if (blocks > 152 * 6) blocks = 152 * 6;
   const size_t dyn = (size_t)A.noff * sizeof(float4);
-  if (dim == 3) k_pairs_fill_sorted<3><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd);
-  else k_pairs_fill_sorted<2><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd);
-  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+  if (cudaMemsetAsync(nlong, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  if (dim == 3)
+    k_pairs_fill_sorted<3><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd, longs, nlong);
+  else
+    k_pairs_fill_sorted<2><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd, longs, nlong);
+  if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
+  return launch_sort_long(longs, nlong, count, start, pj, pd, s);
 }
 
-int launch_pairs_sort(int n, const int* count, const int* start, int* pj, float* pd, cudaStream_t s) {
-  if (n > 0) {
-    int blocks = (n + kSortWarps - 1) / kSortWarps;
-    if (blocks > 152 * 32) blocks = 152 * 32;
-    k_pairs_sort<<<blocks, 32 * kSortWarps, 0, s>>>(n, count, start, pj, pd);
-  }
-  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+int launch_pairs_sort(int n, const int* count, const int* start, int* pj, float* pd, int* longs, int* nlong,
+                      cudaStream_t s) {
+  if (n <= 0) return CL_OK;
+  if (cudaMemsetAsync(nlong, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  int blocks = (n + kSortWarps - 1) / kSortWarps;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_pairs_sort<<<blocks, 32 * kSortWarps, 0, s>>>(n, count, start, pj, pd, longs, nlong);
+  if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
+  return launch_sort_long(longs, nlong, count, start, pj, pd, s);
 }
 
 }  // namespace clk

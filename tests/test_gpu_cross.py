@@ -79,6 +79,32 @@ def test_cross_pairlist(cuda_ok, dim, tric, L, rc, lcell):
     assert max(abs(d[q] - rmap[key[q]]) for q in range(len(key))) <= 1e-6 * rc * 4
 
 
+def test_cross_pairlist_dense_queries(cuda_ok):
+    """Queries inside a dense cluster of A: more than 1024 neighbours each,
+    sorted by the long-segment pass."""
+    import paper_2202_06427_gb300 as P
+    rng = np.random.default_rng(811)
+    h = np.eye(3) * 30.0
+    u = rng.normal(size=(3000, 3))
+    u *= (2.0 * rng.uniform(0, 1, size=(3000, 1)) ** (1 / 3)) / np.linalg.norm(u, axis=1, keepdims=True)
+    xa = np.vstack([rng.uniform(0, 30, size=(2000, 3)), u + 15.0])
+    yb = np.vstack([rng.uniform(0, 30, size=(300, 3)), rng.normal(size=(40, 3)) + 15.0])
+    rc = 5.0
+    ref = oracle.cross_images(xa, yb, h, rc, band=BAND)
+    edge = oracle.band_mask(ref, rc, BAND)
+    core = (ref["r"] < rc) & ~edge
+    cl = P.cl_build(torch.from_numpy(xa).cuda(), h, rc, 2)
+    out = P.cl_cross_pairlist(cl, torch.from_numpy(yb).cuda())
+    a, b, d = out["a"].cpu().numpy(), out["b"].cpu().numpy(), out["d"].cpu().numpy()
+    assert np.bincount(b).max() > 1024
+    key = b.astype(np.int64) * xa.shape[0] + a
+    assert np.all(np.diff(key) > 0), "not sorted by (b, a)"
+    want = set((ref["j"][core].astype(np.int64) * xa.shape[0] + ref["i"][core]).tolist())
+    maybe = set((ref["j"][edge].astype(np.int64) * xa.shape[0] + ref["i"][edge]).tolist())
+    got = set(key.tolist())
+    assert want <= got and got <= want | maybe
+
+
 def test_open_boundaries_match_brute_force(cuda_ok):
     """No periodic boundaries (Sec. 4.1): the bounding box makes every image but
     the direct one lie beyond the cutoff, so the cell list gives exactly the

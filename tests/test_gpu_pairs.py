@@ -68,6 +68,55 @@ def test_small_pairlist_equals_oracle(cuda_ok, dim, tric, lcell):
     check_count(pl["npairs"], ref_map)  # a band pair may round differently than in the half-shell count
 
 
+def _cluster_case(n_bg, n_cl, radius, seed, tric):
+    rng = np.random.default_rng(seed)
+    L = 30.0
+    h = np.eye(3) * L
+    if tric:
+        h[1, 0], h[2, 0], h[2, 1] = 4.0, -3.0, 5.0
+    bg = rng.uniform(0, 1, size=(n_bg, 3)) @ h
+    u = rng.normal(size=(n_cl, 3))
+    u *= (radius * rng.uniform(0, 1, size=(n_cl, 1)) ** (1 / 3)) / np.linalg.norm(u, axis=1, keepdims=True)
+    x = np.vstack([bg, u + np.array([15.0, 14.0, 16.0])])
+    return x[rng.permutation(x.shape[0])], h
+
+
+def _check_against_oracle(P, x, h, rc, lcell):
+    ref = oracle.pairlist(x, h, rc, band=BAND)
+    cl = P.cl_build(torch.from_numpy(np.ascontiguousarray(x)).cuda(), h, rc, lcell)
+    pl = P.cl_map(cl, "pairlist")
+    i, j, d = check_list_structure(pl, x.shape[0], rc)
+    certain = ~ref["band"] | (ref["d"] < rc - BAND * rc)
+    gk = i.astype(np.int64) * x.shape[0] + j
+    rk = ref["i"] * x.shape[0] + ref["j"]
+    assert np.isin(rk[certain & (ref["d"] < rc)], gk).all()
+    pos = np.searchsorted(rk, gk)
+    assert np.array_equal(rk[np.minimum(pos, len(rk) - 1)], gk)
+    assert np.all(np.abs(d - ref["d"][pos]) <= BAND * rc)
+    return np.bincount(i, minlength=x.shape[0])
+
+
+@pytest.mark.parametrize("tric,lcell", [(False, 1), (True, 2)])
+def test_pairlist_dense_cluster(cuda_ok, tric, lcell):
+    """A dense cluster in a sparse background: the cells around the cluster
+    hold more neighbours than one cell's staging area (they take the
+    per-particle path) and its particles have segments longer than one warp
+    sorts in shared memory (they take the long-segment sort)."""
+    P = _P()
+    x, h = _cluster_case(4000, 2500, 2.5, 71 + lcell, tric)
+    seg = _check_against_oracle(P, x, h, 6.0, lcell)
+    assert seg.max() > 2000
+
+
+def test_pairlist_long_segments_in_staged_cells(cuda_ok):
+    """A cluster whose neighbourhood still fits the staging area: segments
+    longer than 1024 written directly by the staged sweep."""
+    P = _P()
+    x, h = _cluster_case(800, 1500, 2.0, 77, False)
+    seg = _check_against_oracle(P, x, h, 6.0, 1)
+    assert seg.max() > 1024
+
+
 def test_pairlist_capacity_protocol(cuda_ok):
     import ctypes
     from paper_2202_06427_gb300 import _lib
