@@ -12,10 +12,13 @@ and backward of a differentiable energy:
 value = pairs within the cutoff per step * ranks / time per step.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload w1_lattice_1m|w4_clustered_16m]
+                       [--workload w1_lattice_1m|w4_clustered_16m|w2_triclinic_1m]
 The default workload is the 1M lattice the metric is quoted on; the 16M
 clustered set (box 600, rc 8, 2,000 Gaussian clusters + 20 % background) runs
-the same step for the strongly inhomogeneous case.
+the same step for the strongly inhomogeneous case. w2_triclinic_1m (rows
+(220,0,0), (30,215,0), (20,25,210), rc 10) runs binning + the sorted i<j pair
+list + a 200-bin histogram per step instead (GPU arm only, no e2e or serving
+legs).
 N > 1 runs under torchrun, one rank per GPU; each rank runs its own replica
 of the workload (the path has no exchange step: replicas only), and the step
 time is the maximum over ranks.
@@ -58,7 +61,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
-    p.add_argument("--workload", choices=["w1_lattice_1m", "w4_clustered_16m"], default=WORKLOAD)
+    p.add_argument("--workload", choices=["w1_lattice_1m", "w4_clustered_16m", "w2_triclinic_1m"],
+                   default=WORKLOAD)
     return p.parse_args()
 
 
@@ -153,6 +157,8 @@ def gpu_id(dev):
 
 def load_workload(name):
     import synth
+    if name == "w2_triclinic_1m":
+        return synth.w2_triclinic()
     return synth.w1_lattice() if name == "w1_lattice_1m" else synth.w4_clustered()
 
 
@@ -205,7 +211,82 @@ def run_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_pairlist(args, rank, world, local):
+    """w2_triclinic_1m: binning, the sorted i<j pair list (count pass, one
+    synchronisation for the total, fill pass) and the 200-bin histogram."""
+    import torch
+    import paper_2202_06427_gb300 as P
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = load_workload("w2_triclinic_1m")
+    x = torch.from_numpy(w["x"]).to(dev)
+    h, rc, nbins = w["h"], w["rc"], w["nbins"]
+    n = x.shape[0]
+    stream = torch.cuda.current_stream(dev)
+    cl = P.cl_build(x, h, rc, LCELL)
+    pairs = P.cl_map(cl, "pairlist")["npairs"]
+    bufs = (torch.empty(pairs, dtype=torch.int32, device=dev), torch.empty(pairs, dtype=torch.int32, device=dev),
+            torch.empty(pairs, dtype=torch.float32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(ev=None):
+        P.cl_update(cl, x)
+        if ev is not None:
+            ev[0].record(stream)
+        got = P.cl_map(cl, "pairlist", out=bufs)["npairs"]
+        if ev is not None:
+            ev[1].record(stream)
+        P.cl_map(cl, "hist", nbins=nbins)
+        return got
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(gpu_id(dev))
+    sampler.start()
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        assert step(kev[k]) == pairs
+        ends[k].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    sampler.stop()
+    ms = reduce_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, world, dev)
+    kms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    # algorithmic bytes of the list passes: 12 B written per pair, the sorted float4
+    # particles and cell offsets read once per pass
+    nbytes = 12 * pairs + 2 * 16 * n
+    achieved = nbytes / (kms / 1e3) / 1e9
+    return {"metric": METRIC, "value": pairs * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "w2_triclinic_1m", "n": n, "cutoff": rc, "lcell": LCELL, "pairs_per_step": pairs,
+                       "step": "binning + sorted i<j pair list (count, scan, fill) + 200-bin histogram",
+                       "l2": "flushed between steps by a 256 MB write outside the timed events",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            # bin, 3 scan, scatter, pair pack; cell count, listed-cell count, 3 scan, cell fill,
+            # listed-cell fill, long-segment sort; histogram sweep
+            "gpu_launches": 15 * args.steps,
+            "clocks": sampler.summary(),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                         "kernel": "pair-list passes (k_pairs_cell count and fill, scan, per-particle paths)",
+                         "kernel_ms": kms, "bytes_per_launch": nbytes,
+                         "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"}}
+
+
 def run_ours(args, rank, world, local):
+    if getattr(args, "workload", WORKLOAD) == "w2_triclinic_1m":
+        return run_pairlist(args, rank, world, local)
     import torch
     import paper_2202_06427_gb300 as P
     import synth

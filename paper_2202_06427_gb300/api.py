@@ -107,9 +107,13 @@ def cl_update(cl, pos, h=None, cutoff=None, lcell=None, stream=None):
         cl.h, cl.cutoff, cl.lcell = np.array(nh, dtype=np.float64), float(nc), int(nl)
 
 
-def cl_map(cl, reduction, nbins=0, rmax=0.0, capacity=None, stream=None):
-    """Run one built-in reduction; returns a dict of device tensors."""
+def cl_map(cl, reduction, nbins=0, rmax=0.0, capacity=None, stream=None, out=None):
+    """Run one built-in reduction; returns a dict of device tensors. For the
+    pair list, out may hold preallocated (i, j, d) tensors (int32, int32,
+    float32) whose common length is the capacity."""
     red = REDUCTIONS[reduction] if isinstance(reduction, str) else int(reduction)
+    if red == CL_RED_PAIRLIST:
+        return _pairlist(cl, capacity, stream, out)
     dev = cl.device
     res = L.cl_result()
     out = {}
@@ -131,8 +135,6 @@ def cl_map(cl, reduction, nbins=0, rmax=0.0, capacity=None, stream=None):
     elif red == CL_RED_HIST:
         out["hist"] = torch.zeros(int(nbins), dtype=torch.int64, device=dev)
         res.hist = out["hist"].data_ptr()
-    elif red == CL_RED_PAIRLIST:
-        return _pairlist(cl, capacity, stream)
     params = L.cl_params()
     params.nbins = int(nbins)
     params.rmax = float(rmax)
@@ -141,14 +143,22 @@ def cl_map(cl, reduction, nbins=0, rmax=0.0, capacity=None, stream=None):
     return out
 
 
-def _pairlist(cl, capacity, stream):
+def _pairlist(cl, capacity, stream, bufs=None):
     dev = cl.device
+    if bufs is not None:
+        pi, pj, pd = bufs
+        if not (pi.dtype == pj.dtype == torch.int32 and pd.dtype == torch.float32 and
+                pi.is_contiguous() and pj.is_contiguous() and pd.is_contiguous() and
+                pi.numel() == pj.numel() == pd.numel() and pi.device == pj.device == pd.device == dev):
+            raise ValueError("out: contiguous (int32, int32, float32) tensors of one length on the list's device")
+        capacity = pi.numel()
     cap = int(capacity) if capacity is not None else max(1024, cl.n * 8)
     lib = L.lib()
     while True:
-        pi = torch.empty(cap, dtype=torch.int32, device=dev)
-        pj = torch.empty(cap, dtype=torch.int32, device=dev)
-        pd = torch.empty(cap, dtype=torch.float32, device=dev)
+        if bufs is None:
+            pi = torch.empty(cap, dtype=torch.int32, device=dev)
+            pj = torch.empty(cap, dtype=torch.int32, device=dev)
+            pd = torch.empty(cap, dtype=torch.float32, device=dev)
         npairs = ctypes.c_longlong(0)
         res = L.cl_result()
         res.pair_i, res.pair_j, res.pair_d = pi.data_ptr(), pj.data_ptr(), pd.data_ptr()

@@ -231,7 +231,7 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
     size_t b = 0;
     const size_t n = (size_t)c->n;
     if ((e = dev_alloc(&c->pl_count, n, &b)) || (e = dev_alloc(&c->pl_start, n + 1, &b)) ||
-        (e = dev_alloc(&c->pl_tiles, (size_t)clk::scan_tiles_for(c->n), &b)) || (e = dev_alloc(&c->pl_meta, 4, &b)) ||
+        (e = dev_alloc(&c->pl_tiles, (size_t)clk::scan_tiles_for(c->n), &b)) || (e = dev_alloc(&c->pl_meta, 8, &b)) ||
         (e = dev_alloc(&c->pl_long, n, &b))) {
       cudaFree(c->pl_count);
       cudaFree(c->pl_start);
@@ -245,7 +245,9 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   }
   const int dim = c->geo.dim;
   const float ball2 = pairs_ball2(c->geo);
-  if ((e = clk::launch_pairs_count(*c->full, dim, ball2, c->hflag, c->pl_count, s))) return e;
+  // hflag / hlist: per-cell flags and the flagged cells (shared with the
+  // neighbourhood sweep, which rewrites them on every launch); pl_meta[4]: their number
+  if ((e = clk::launch_pairs_count(*c->full, dim, ball2, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, s))) return e;
   if ((e = clk::launch_scan(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
   int total = 0, meta[4] = {0, 0, 0, 0};
   if (cudaMemcpyAsync(&total, c->pl_start + c->n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -256,8 +258,8 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   if (total > r->capacity) return CL_ERR_CAPACITY;
   if (total == 0) return CL_OK;
   if (!r->pair_i || !r->pair_j || !r->pair_d) return CL_ERR_INVALID_ARG;
-  return clk::launch_pairs_fill(*c->full, dim, ball2, c->hflag, c->pl_count, c->pl_start, r->pair_i, r->pair_j,
-                               r->pair_d, c->pl_long, c->pl_meta + 3, s);
+  return clk::launch_pairs_fill(*c->full, dim, ball2, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, c->pl_start,
+                               r->pair_i, r->pair_j, r->pair_d, c->pl_long, c->pl_meta + 3, s);
 }
 
 }  // namespace

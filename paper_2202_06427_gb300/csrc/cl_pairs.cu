@@ -7,7 +7,7 @@
 //                  one warp per home particle sweeps it and counts the pairs
 //                  with j > i (original indices), so every pair is counted
 //                  once, by its smaller index, without atomics. A cell whose
-//                  neighbourhood does not fit is flagged.
+//                  neighbourhood does not fit is flagged and listed.
 //   (scan)         exclusive prefix sum of the counts in original order:
 //                  segment of i = [start[i], start[i] + count[i])
 //   k_pairs_cell<FILL>   the same staging, then the staged list's original
@@ -15,7 +15,7 @@
 //                  j > i come out of a suffix of that order in ascending j and
 //                  are written in order with coalesced stores
 //   k_pairs_count / k_pairs_fill_sorted
-//                  the flagged cells' particles, one thread (count) or one warp
+//                  the listed cells' particles, one thread (count) or one warp
 //                  (fill) per particle straight from the sorted arrays; a
 //                  segment longer than kMaxSegment is written unsorted and
 //                  listed for k_pairs_sort_long
@@ -35,11 +35,6 @@
 
 namespace clk {
 
-// Linear cell index of sorted particle p.
-__device__ __forceinline__ int cell_of(const SweepArgs& A, int p) {
-  const unsigned cc = A.cellc[p];
-  return (int)(cc & 1023u) + A.nx * ((int)((cc >> 10) & 1023u) + A.ny * (int)(cc >> 20));
-}
 
 struct RedPairCount {
   static constexpr bool kFull = true;
@@ -48,19 +43,25 @@ struct RedPairCount {
   __device__ void hit(Acc& x, float, float, float, float, int j) const { x.n += (j > x.a) ? 1 : 0; }
 };
 
+// The particles of the listed cells (cells[0, *ncells)), one thread each.
 template <int DIM>
 __global__ void __launch_bounds__(256) k_pairs_count(const __grid_constant__ SweepArgs A,
-                                                     const unsigned char* __restrict__ flag, int* __restrict__ count) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= A.n) return;
-  if (flag && !flag[cell_of(A, p)]) return;
-  RedPairCount red;
-  RedPairCount::Acc acc;
-  red.init(acc);
-  acc.a = __float_as_int(A.xs[p].w);
-  float4 pi;
-  sweep_particle<DIM>(A, red, acc, p, pi);
-  count[acc.a] = acc.n;
+                                                     const int* __restrict__ cells, const int* __restrict__ ncells,
+                                                     int* __restrict__ count) {
+  const int m = *ncells;
+  for (int q = blockIdx.x; q < m; q += gridDim.x) {
+    const int c = cells[q];
+    const int p1 = A.cell_start[c + 1];
+    for (int p = A.cell_start[c] + threadIdx.x; p < p1; p += blockDim.x) {
+      RedPairCount red;
+      RedPairCount::Acc acc;
+      red.init(acc);
+      acc.a = __float_as_int(A.xs[p].w);
+      float4 pi;
+      sweep_particle<DIM>(A, red, acc, p, pi);
+      count[acc.a] = acc.n;
+    }
+  }
 }
 
 constexpr int kSortWarps = 4;
@@ -375,12 +376,13 @@ __device__ __forceinline__ void segment_out(int* K, float* V, int nw, int a, int
   __syncwarp();
 }
 
-// Flagged cells' particles, one warp per particle, straight from the sorted
+// The listed cells' particles, one warp per particle, straight from the sorted
 // arrays: the candidate's distance is x_j + (s_o - x_i), equal in IEEE
 // arithmetic to x_j - (x_i - s_o) of k_pairs_count (same fused multiply-adds).
 template <int DIM>
 __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const __grid_constant__ SweepArgs A,
-                                                                          const unsigned char* __restrict__ flag,
+                                                                          const int* __restrict__ cells,
+                                                                          const int* __restrict__ ncells,
                                                                           const int* __restrict__ count,
                                                                           const int* __restrict__ start,
                                                                           int* __restrict__ pi_out,
@@ -397,54 +399,58 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
   const unsigned lt = (1u << lane) - 1u;
   int* K = sk[warp];
   float* V = sv[warp];
-  for (int p = blockIdx.x * kFillWarps + warp; p < A.n; p += gridDim.x * kFillWarps) {
-    if (!flag[cell_of(A, p)]) continue;
-    const float4 pi = A.xs[p];
-    const int a = __float_as_int(pi.w);
-    const unsigned cc = A.cellc[p];
-    const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
-    const int cnt_a = __ldg(count + a), base = __ldg(start + a);
-    const bool big = cnt_a > kMaxSegment;  // written unsorted, sorted by k_pairs_sort_long
-    int L = 0;
-    for (int k0 = 0; k0 < A.noff; k0 += 32) {
-      const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, -pi.x, -pi.y, -pi.z);
-      for (int t0 = 0; t0 < ch.total; t0 += 32) {
-        const int t = t0 + lane;
-        float ax, ay, az;
-        const int j = chunk_candidate(ch, t, ax, ay, az);
-        bool keep = false;
-        int jo = 0;
-        float d2 = 0.f;
-        if (t < ch.total) {
-          const float4 q = __ldg(&A.xs[j]);
-          jo = __float_as_int(q.w);
-          const float dx = q.x + ax, dy = q.y + ay;
-          const float dz = DIM == 3 ? q.z + az : 0.f;
-          d2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
-          keep = jo > a && d2 < A.rc2;
-        }
-        const unsigned m = __ballot_sync(0xffffffffu, keep);
-        if (keep) {
-          const int e = L + __popc(m & lt);
-          if (big) {
-            if (e < cnt_a) {
-              pi_out[base + e] = a;
-              pj_out[base + e] = jo;
-              pd_out[base + e] = d2 * rsqrt_nr(d2);
-            }
-          } else if (e < kMaxSegment) {
-            K[seg_at(e)] = jo;
-            V[seg_at(e)] = d2 * rsqrt_nr(d2);
+  const int mc = *ncells;
+  for (int q = blockIdx.x; q < mc; q += gridDim.x) {
+    const int cq = cells[q];
+    const int pend = A.cell_start[cq + 1];
+    for (int p = A.cell_start[cq] + warp; p < pend; p += kFillWarps) {
+      const float4 pi = A.xs[p];
+      const int a = __float_as_int(pi.w);
+      const unsigned cc = A.cellc[p];
+      const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
+      const int cnt_a = __ldg(count + a), base = __ldg(start + a);
+      const bool big = cnt_a > kMaxSegment;  // written unsorted, sorted by k_pairs_sort_long
+      int L = 0;
+      for (int k0 = 0; k0 < A.noff; k0 += 32) {
+        const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, -pi.x, -pi.y, -pi.z);
+        for (int t0 = 0; t0 < ch.total; t0 += 32) {
+          const int t = t0 + lane;
+          float ax, ay, az;
+          const int j = chunk_candidate(ch, t, ax, ay, az);
+          bool keep = false;
+          int jo = 0;
+          float d2 = 0.f;
+          if (t < ch.total) {
+            const float4 q = __ldg(&A.xs[j]);
+            jo = __float_as_int(q.w);
+            const float dx = q.x + ax, dy = q.y + ay;
+            const float dz = DIM == 3 ? q.z + az : 0.f;
+            d2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
+            keep = jo > a && d2 < A.rc2;
           }
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (keep) {
+            const int e = L + __popc(m & lt);
+            if (big) {
+              if (e < cnt_a) {
+                pi_out[base + e] = a;
+                pj_out[base + e] = jo;
+                pd_out[base + e] = d2 * rsqrt_nr(d2);
+              }
+            } else if (e < kMaxSegment) {
+              K[seg_at(e)] = jo;
+              V[seg_at(e)] = d2 * rsqrt_nr(d2);
+            }
+          }
+          L += __popc(m);
         }
-        L += __popc(m);
       }
-    }
-    __syncwarp();
-    if (big) {
-      if (lane == 0) longs[atomicAdd(nlong, 1)] = a;
-    } else {
-      segment_out(K, V, min(min(L, kMaxSegment), cnt_a), a, base, lane, pi_out, pj_out, pd_out);
+      __syncwarp();
+      if (big) {
+        if (lane == 0) longs[atomicAdd(nlong, 1)] = a;
+      } else {
+        segment_out(K, V, min(min(L, kMaxSegment), cnt_a), a, base, lane, pi_out, pj_out, pd_out);
+      }
     }
   }
 }
@@ -556,7 +562,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
 // shifted to the cell's frame (x_j + s_o), to the staged list. Then warp w
 // sweeps home particles w, w + W, ... against it (distance (x_j + s_o) - x_i).
 // COUNT: count[a] = pairs with j > a; a cell whose list does not fit gets
-// flag 1 (else 0). FILL: flagged cells are skipped; the staged list is ordered
+// flag 1 (else 0) and is listed in fcells. FILL: flagged cells are skipped; the staged list is ordered
 // by original index (radix sort of its indices), so a particle's pairs with
 // j > a come from a suffix of that order in ascending j and are written in
 // order, coalesced, as the ballot finds them.
@@ -564,6 +570,8 @@ template <int DIM, bool FILL>
 __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
                                                                                float ball2,
                                                                                unsigned char* __restrict__ flag,
+                                                                               int* __restrict__ fcells,
+                                                                               int* __restrict__ nfcells,
                                                                                int* __restrict__ count,
                                                                                const int* __restrict__ start,
                                                                                int* __restrict__ pi_out,
@@ -668,12 +676,13 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
         if (!FILL && lane == 0) count[a] = L;
       }
     }
-    if (!FILL && threadIdx.x == 0) flag[c] = S > kStage ? 1 : 0;
+    if (!FILL && threadIdx.x == 0) {
+      flag[c] = S > kStage ? 1 : 0;
+      if (S > kStage) fcells[atomicAdd(nfcells, 1)] = c;
+    }
     __syncthreads();
   }
 }
-
-static int blocks_of(int n) { return n > 0 ? (n + 255) / 256 : 1; }
 
 size_t pairs_cell_smem(int noff, bool fill) {
   const size_t head = (size_t)(kStage + noff) * sizeof(float4) + 16 * sizeof(int);
@@ -682,8 +691,8 @@ size_t pairs_cell_smem(int noff, bool fill) {
 }
 
 template <int DIM, bool FILL>
-static int launch_cell(const SweepArgs& A, float ball2, unsigned char* flag, int* count, const int* start, int* pi,
-                       int* pj, float* pd, cudaStream_t s) {
+static int launch_cell(const SweepArgs& A, float ball2, unsigned char* flag, int* fcells, int* nfcells, int* count,
+                       const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
   static int per_sm = 0, sms = 0;
   if (!per_sm) {
     int dev = 0, per = 0;
@@ -701,18 +710,22 @@ static int launch_cell(const SweepArgs& A, float ball2, unsigned char* flag, int
   long long blocks = (long long)sms * per_sm;
   const long long ncells = (long long)A.nx * A.ny * A.nz;
   if (blocks > ncells) blocks = ncells;
-  k_pairs_cell<DIM, FILL><<<(int)blocks, FILL ? 256 : 128, pairs_cell_smem(A.noff, FILL), s>>>(A, ball2, flag, count,
+  k_pairs_cell<DIM, FILL><<<(int)blocks, FILL ? 256 : 128, pairs_cell_smem(A.noff, FILL), s>>>(A, ball2, flag, fcells,
+                                                                                                 nfcells, count,
                                                                                               start, pi, pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
-int launch_pairs_count(const SweepArgs& A, int dim, float ball2, unsigned char* flag, int* count, cudaStream_t s) {
+int launch_pairs_count(const SweepArgs& A, int dim, float ball2, unsigned char* flag, int* fcells, int* nfcells,
+                       int* count, cudaStream_t s) {
   if (A.n <= 0) return CL_OK;
-  const int e = dim == 3 ? launch_cell<3, false>(A, ball2, flag, count, nullptr, nullptr, nullptr, nullptr, s)
-                         : launch_cell<2, false>(A, ball2, flag, count, nullptr, nullptr, nullptr, nullptr, s);
+  if (cudaMemsetAsync(nfcells, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  const int e =
+      dim == 3 ? launch_cell<3, false>(A, ball2, flag, fcells, nfcells, count, nullptr, nullptr, nullptr, nullptr, s)
+               : launch_cell<2, false>(A, ball2, flag, fcells, nfcells, count, nullptr, nullptr, nullptr, nullptr, s);
   if (e) return e;
-  if (dim == 3) k_pairs_count<3><<<blocks_of(A.n), 256, 0, s>>>(A, flag, count);
-  else k_pairs_count<2><<<blocks_of(A.n), 256, 0, s>>>(A, flag, count);
+  if (dim == 3) k_pairs_count<3><<<152 * 4, 256, 0, s>>>(A, fcells, nfcells, count);
+  else k_pairs_count<2><<<152 * 4, 256, 0, s>>>(A, fcells, nfcells, count);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
@@ -722,22 +735,23 @@ static int launch_sort_long(const int* longs, const int* nlong, const int* count
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
-int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned char* flag, const int* count,
-                      const int* start, int* pi, int* pj, float* pd, int* longs, int* nlong, cudaStream_t s) {
+int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned char* flag, const int* fcells,
+                      const int* nfcells, const int* count, const int* start, int* pi, int* pj, float* pd, int* longs,
+                      int* nlong, cudaStream_t s) {
   if (A.n <= 0) return CL_OK;
   unsigned char* fl = const_cast<unsigned char*>(flag);  // only read by the fill pass
   int* cn = const_cast<int*>(count);                     // likewise
-  const int e = dim == 3 ? launch_cell<3, true>(A, ball2, fl, cn, start, pi, pj, pd, s)
-                         : launch_cell<2, true>(A, ball2, fl, cn, start, pi, pj, pd, s);
+  const int e = dim == 3 ? launch_cell<3, true>(A, ball2, fl, nullptr, nullptr, cn, start, pi, pj, pd, s)
+                         : launch_cell<2, true>(A, ball2, fl, nullptr, nullptr, cn, start, pi, pj, pd, s);
   if (e) return e;
-  long long blocks = (A.n + kFillWarps - 1) / kFillWarps;
-  if (blocks > 152 * 6) blocks = 152 * 6;
   const size_t dyn = (size_t)A.noff * sizeof(float4);
   if (cudaMemsetAsync(nlong, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if (dim == 3)
-    k_pairs_fill_sorted<3><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd, longs, nlong);
+    k_pairs_fill_sorted<3><<<152 * 6, 32 * kFillWarps, dyn, s>>>(A, fcells, nfcells, count, start, pi, pj, pd, longs,
+                                                                nlong);
   else
-    k_pairs_fill_sorted<2><<<(int)blocks, 32 * kFillWarps, dyn, s>>>(A, flag, count, start, pi, pj, pd, longs, nlong);
+    k_pairs_fill_sorted<2><<<152 * 6, 32 * kFillWarps, dyn, s>>>(A, fcells, nfcells, count, start, pi, pj, pd, longs,
+                                                                nlong);
   if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
   return launch_sort_long(longs, nlong, count, start, pj, pd, s);
 }
