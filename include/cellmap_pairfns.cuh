@@ -16,8 +16,11 @@
  * CUDA translation unit; libcellmap exports C entry points built from them
  * (cl_map_mass, cl_map_lj, cl_map_velocity_hist in cellmap.h). Per-particle
  * arrays (masses, velocities, forces) are indexed by the original particle
- * index. Scalar outputs are FP64 and accumulated with one atomic add per
- * particle (they must be zeroed first); pair terms are FP32.
+ * index. Scalar outputs are FP64 (they must be zeroed first): each thread's
+ * FP32 sum is added in FP64 over the lanes of its warp that finish together,
+ * and one lane adds that to the output with an atomic (one atomic per warp
+ * and output instead of one per particle: the outputs are a few adjacent
+ * addresses that every thread hits). Pair terms are FP32.
  */
 #ifndef CELLMAP_PAIRFNS_CUH
 #define CELLMAP_PAIRFNS_CUH
@@ -26,6 +29,26 @@
 
 namespace cellmap {
 namespace pairfn {
+
+namespace detail {
+
+// Sum of v over the lanes that call this together (FP64), added to *out by
+// the lowest of them. Any subset of a warp may call it; each lane's value is
+// added once.
+__device__ __forceinline__ void warp_add(double* out, double v) {
+  const unsigned m = __activemask();
+  double s = 0.0;
+  for (unsigned r = m; r; r &= r - 1) s += __shfl_sync(m, v, __ffs(r) - 1);
+  if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && s != 0.0) atomicAdd(out, s);
+}
+
+__device__ __forceinline__ void warp_add(unsigned long long* out, unsigned v) {
+  const unsigned m = __activemask();
+  const unsigned s = __reduce_add_sync(m, v);
+  if ((int)(threadIdx.x & 31) == __ffs(m) - 1 && s != 0u) atomicAdd(out, (unsigned long long)s);
+}
+
+}  // namespace detail
 
 struct MassPotential {
   static constexpr bool kFullShell = false;
@@ -36,9 +59,7 @@ struct MassPotential {
   __device__ void pair(Acc& a, int i, int j, float, float, float, float d2) const {
     a.s = fmaf(__ldg(mass + i) * __ldg(mass + j), rsqrtf(d2), a.s);
   }
-  __device__ void finish(const Acc& a, int) const {
-    if (a.s != 0.f) atomicAdd(out, (double)a.s);
-  }
+  __device__ void finish(const Acc& a, int) const { detail::warp_add(out, (double)a.s); }
 };
 
 struct LennardJones {
@@ -51,9 +72,7 @@ struct LennardJones {
     const float q = s2 / d2, q3 = q * q * q;
     a.e = fmaf(eps4, q3 * q3 - q3, a.e);
   }
-  __device__ void finish(const Acc& a, int) const {
-    if (a.e != 0.f) atomicAdd(out, (double)a.e);
-  }
+  __device__ void finish(const Acc& a, int) const { detail::warp_add(out, (double)a.e); }
 };
 
 // F_i = sum_j u'(r) r_ij / r with r_ij = x_j - x_i: u'(r)/r = -24 eps (2 q6^2 - q6)/d2,
@@ -79,11 +98,16 @@ struct LennardJonesForces {
     forces[(size_t)i * dim + 0] = a.fx;
     forces[(size_t)i * dim + 1] = a.fy;
     if (dim == 3) forces[(size_t)i * 3 + 2] = a.fz;
-    if (energy && a.e != 0.f) atomicAdd(energy, 0.5 * (double)a.e);
+    if (energy) detail::warp_add(energy, 0.5 * (double)a.e);
   }
 };
 
-// NB: compile-time bound on the number of bins (the bins live in registers).
+// NB: compile-time bound on the number of bins. The bins are indexed by the
+// pair's bin, so they live in the thread's local memory (L1), one load and one
+// store per counted pair instead of a compare chain over every bin; v_i is
+// loaded once per particle (at its first counted pair) and kept in Acc; r and
+// |v_i - v_j| come from the hardware reciprocal square root (relative error
+// about 1e-7).
 template <int NB>
 struct VelocityHistogram {
   static constexpr bool kFullShell = false;
@@ -93,39 +117,40 @@ struct VelocityHistogram {
   unsigned long long* counts;
   double* vsum;
   struct Acc {
+    int i;           // particle whose velocity vi holds (-1: none yet)
+    float vi[3];
     unsigned c[NB];
     float v[NB];
   };
   __device__ void init(Acc& a) const {
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
+    a.i = -1;
+    for (int b = 0; b < nbins; ++b) {
       a.c[b] = 0u;
       a.v[b] = 0.f;
     }
   }
   __device__ void pair(Acc& a, int i, int j, float, float, float, float d2) const {
-    const int k = (int)ceilf(sqrtf(d2) * inv_binstep);  // 1-based bin
+    const float r = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+    const int k = (int)ceilf(r * inv_binstep);  // 1-based bin
     if (k < 1 || k > nbins) return;
-    float s = 0.f;
-    for (int q = 0; q < dim; ++q) {
-      const float t = __ldg(vel + (size_t)i * dim + q) - __ldg(vel + (size_t)j * dim + q);
-      s = fmaf(t, t, s);
+    if (a.i != i) {
+      a.i = i;
+      a.vi[0] = __ldg(vel + (size_t)i * dim);
+      a.vi[1] = __ldg(vel + (size_t)i * dim + 1);
+      a.vi[2] = dim == 3 ? __ldg(vel + (size_t)i * dim + 2) : 0.f;
     }
-    const float dv = sqrtf(s);
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-      if (k == b + 1) {
-        a.c[b] += 1u;
-        a.v[b] += dv;
-      }
+    const float* vj = vel + (size_t)j * dim;
+    const float t0 = a.vi[0] - __ldg(vj), t1 = a.vi[1] - __ldg(vj + 1);
+    const float t2 = dim == 3 ? a.vi[2] - __ldg(vj + 2) : 0.f;
+    const float s = fmaf(t0, t0, fmaf(t1, t1, t2 * t2));
+    a.c[k - 1] += 1u;
+    a.v[k - 1] += s > 0.f ? s * rsqrtf(s) : 0.f;
   }
   __device__ void finish(const Acc& a, int) const {
-#pragma unroll
-    for (int b = 0; b < NB; ++b)
-      if (a.c[b]) {
-        atomicAdd(counts + b, (unsigned long long)a.c[b]);
-        atomicAdd(vsum + b, (double)a.v[b]);
-      }
+    for (int b = 0; b < nbins; ++b) {
+      detail::warp_add(counts + b, a.c[b]);
+      detail::warp_add(vsum + b, (double)a.v[b]);
+    }
   }
 };
 
