@@ -14,9 +14,15 @@
 //                  ("vector of lists ... an immutable copy of the particle
 //                  coordinates and index", Sec. 2.8).
 //
-// FP64 is kept for the wrap and the cell assignment. On this GPU FP64 issues
-// at about 1/74 of the FP32 rate, so the kernel uses one FP64 multiply per
-// axis for diagonal boxes and works in integers for the periodic cell index.
+// FP64 is kept for the position in cell units. On this GPU FP64 issues at
+// about 1/74 of the FP32 rate, so per axis the kernel spends one FP64
+// multiply (diagonal boxes; three FMAs otherwise) and one conversion: M is
+// scaled by 2^32 (exact), and floor(t 2^32) as a 64-bit integer holds the
+// cell coordinate in its high word and the fraction in cell units, to 2^-32,
+// in its low word. Periodic wrapping is integer work. Positions 2^30 cells or
+// more from the origin, and non-finite ones, take the plain FP64 floor path.
+#include <cmath>
+
 #include "cl_internal.cuh"
 
 namespace clk {
@@ -49,7 +55,7 @@ __global__ void __launch_bounds__(256) k_bin(const __grid_constant__ BinArgs a) 
   float u[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int k = 0; k < DIM; ++k) {
-    double t;
+    double t;  // position in cell units times 2^32
     if (ORTHO) {
       t = x[k] * a.m[k * 3 + k];
     } else {
@@ -57,9 +63,19 @@ __global__ void __launch_bounds__(256) k_bin(const __grid_constant__ BinArgs a) 
 #pragma unroll
       for (int q = 0; q < DIM; ++q) t = fma(x[q], a.m[q * 3 + k], t);
     }
-    const double f = floor(t);
-    const double frac = t - f;  // exact, in [0, 1)
-    long long ci = finite ? (long long)f : 0;
+    long long ci;
+    float frac;  // in [0, 1)
+    if (((__double2hiint(t) >> 20) & 0x7ff) < 1023 + 62) {  // |t| < 2^62, finite
+      const long long ti = __double2ll_rd(t);
+      ci = ti >> 32;
+      frac = (float)(unsigned)(ti & 0xffffffffLL) * 0x1p-32f;
+      frac = frac < 1.0f ? frac : 0x1.fffffep-1f;  // a fraction that rounds up to 1
+    } else {
+      const double tc = t * 0x1p-32;
+      const double f = floor(tc);
+      frac = (float)(tc - f);
+      ci = finite ? (long long)f : 0;
+    }
     int cm;
     if (ci >= 0 && ci < nk[k]) {
       cm = (int)ci;  // inside the box: the common case
@@ -69,7 +85,7 @@ __global__ void __launch_bounds__(256) k_bin(const __grid_constant__ BinArgs a) 
       cm = (int)r;
     }
     c[k] = cm;
-    u[k] = (float)frac - 0.5f;  // centred, in [-0.5, 0.5]
+    u[k] = frac - 0.5f;  // centred, in [-0.5, 0.5]
   }
   float4 o;
   o.x = 0.f; o.y = 0.f; o.z = 0.f;
@@ -241,7 +257,10 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
   a.pos = b.pos;
   a.n = b.n;
   a.nx = g.n[0]; a.ny = g.n[1]; a.nz = g.n[2];
-  for (int k = 0; k < 9; ++k) { a.m[k] = g.m[k]; a.g[k] = g.g[k]; }
+  for (int k = 0; k < 9; ++k) {
+    a.m[k] = std::ldexp(g.m[k], 32);  // exact: t 2^32 = x (M 2^32)
+    a.g[k] = g.g[k];
+  }
   a.packed = b.packed; a.slot = b.slot; a.xl = b.xl; a.counts = b.counts; a.err = b.meta;
   const int blocks = (b.n + 255) / 256;
   if (b.n > 0) {
