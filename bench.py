@@ -40,6 +40,10 @@ METRIC = "pairs-within-cutoff/sec at 1M particles"
 UNIT = "pairs/s"
 WORKLOAD = "w1_lattice_1m"
 LCELL = 2
+# cells per cutoff length by workload: two on the homogeneous sets; one on the
+# clustered set, where larger cells keep fewer particles in sparse cells and
+# fewer cells over the staging limits (measured: fused sweep 37 ms at 1, 57 ms at 2)
+LCELL_BY_WORKLOAD = {"w1_lattice_1m": 2, "w2_triclinic_1m": 2, "w4_clustered_16m": 1}
 # FP32 arithmetic per candidate pair and per ordered pair-image within the cutoff
 # (FMA = 2 FLOP, 1/r = 1) of the fused energy-and-gradient sweep:
 FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j' - x_i|^2
@@ -298,7 +302,8 @@ def run_ours(args, rank, world, local):
     h, rc = w["h"], w["rc"]
     n = x.shape[0]
     stream = torch.cuda.current_stream(dev)
-    cl = P.cl_build(x, h, rc, LCELL)
+    lcell = LCELL_BY_WORKLOAD.get(getattr(args, "workload", WORKLOAD), LCELL)
+    cl = P.cl_build(x, h, rc, lcell)
     pairs = int(P.cl_map(cl, "count")["count"].item())
     cand_half = P.cl_query(cl, "candidates")
     g = torch.ones(1, dtype=torch.float64, device=dev)
@@ -363,7 +368,7 @@ def run_ours(args, rank, world, local):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": getattr(args, "workload", WORKLOAD), "n": n, "box": float(h[0][0]), "cutoff": rc, "lcell": LCELL,
+            "config": {"workload": getattr(args, "workload", WORKLOAD), "n": n, "box": float(h[0][0]), "cutoff": rc, "lcell": lcell,
                        "pairs_per_step": pairs, "candidates_sweep": cand, "candidates_half_shell_stencil": cand_half,
                        "step": "binning + fused energy/forces/box-gradient sweep (forward) + chain rule (backward)",
                        "l2": "flushed between steps by a 256 MB write outside the timed events",

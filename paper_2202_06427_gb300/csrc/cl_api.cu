@@ -25,6 +25,7 @@ struct cl_list {
   int* cell_start;
   unsigned char* hflag;  // per cell: 1 when a staged sweep (neighbourhood or pair list) leaves it to a per-particle sweep
   int* hlist;            // cells the neighbourhood sweep takes
+  int* hdense;           // cells the dense-cell sweep takes
   int* tile_sum;
   int* meta;
   double* partials;
@@ -69,6 +70,8 @@ void free_cells(cl_list* c) {
   cudaFree(c->hflag);
   cudaFree(c->hlist);
   c->hlist = nullptr;
+  cudaFree(c->hdense);
+  c->hdense = nullptr;
   c->counts = nullptr;
   c->cell_start = nullptr;
   c->tile_sum = nullptr;
@@ -109,6 +112,7 @@ int alloc_cells(cl_list* c, long long ncells) {
   if ((e = dev_alloc(&c->tile_sum, (size_t)clk::scan_tiles_for(ncells), &b))) return e;
   if ((e = dev_alloc(&c->hflag, (size_t)ncells, &b))) return e;
   if ((e = dev_alloc(&c->hlist, (size_t)ncells, &b))) return e;
+  if ((e = dev_alloc(&c->hdense, (size_t)ncells, &b))) return e;
   c->ncells_alloc = ncells;
   c->bytes += b;
   return CL_OK;
@@ -176,6 +180,7 @@ int set_geometry(cl_list* c, const cl_box* box) {
   *c->hood = *hood;
   c->hood->flag = c->hflag;
   c->hood->list = c->hlist;
+  c->hood->dense = c->hdense;
   delete hood;
   c->half->noff = nh;
   c->full->noff = nf;
@@ -337,7 +342,8 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
-  if (!e) e = dev_alloc(&c->work, 4, &b);  // [0] work counter, [1] list length, [2..3] candidate counter
+  if (!e) e = dev_alloc(&c->work, 6, &b);  // [0] work counter, [1] list length, [2..3] candidate counter,
+                                           // [4] dense cells, [5] their work counter
   if (!e) e = dev_alloc(&c->u64, 8, &b);
   if (!e) e = dev_alloc(&c->d_off_half, (size_t)clk::kMaxOff, &b);
   if (!e) e = dev_alloc(&c->d_off_full, (size_t)clk::kMaxOff, &b);

@@ -30,11 +30,14 @@
 // growing from the far end of the buffer, and add fsn r (x) r directly. Every
 // path of this file computes the same per-particle share, so their sums agree.
 //
-// Home cells that do not pay for the staging (fewer than kMinHome particles) or
-// do not fit (more than kHome particles, or more than kCap staged neighbours)
-// are flagged and swept afterwards by a companion kernel,
-// one thread per particle over the stencil (k_hood_rest), with the same
-// per-particle virial share; both write per-CTA partials to one buffer.
+// Home cells that do not pay for the staging (fewer than kMinHome particles)
+// are swept afterwards by a companion kernel, one thread per particle over the
+// stencil (k_hood_rest), as are all cells when the stencil is larger than the
+// table; cells that do not fit (more than kHome particles, or more than kCap
+// staged neighbours) by the dense-cell sweep (k_hood_dense), one
+// thread per home particle against windows of the staged neighbourhood. All
+// three compute the same per-particle virial share and write per-CTA partials
+// to one buffer.
 #include <cmath>
 #include <cstring>
 
@@ -541,25 +544,36 @@ __device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs&
   return ncand;
 }
 
-// Work list of the neighbourhood sweep: cells with kMinHome..kHome particles
-// (and a stencil that fits the table) are listed; every other cell is flagged
-// for the per-particle companion (empty cells are not). A cell whose staged
-// neighbourhood overflows is flagged later by the sweep itself.
+// Work lists: cells with kMinHome..kHome particles (and a stencil that fits
+// the table) go to the neighbourhood sweep (list, work[1] of them); cells with
+// more than kHome particles are flagged 2 and listed for the dense-cell sweep
+// (dense, *ndense of them); the other non-empty cells (fewer particles, or a
+// stencil larger than the table) are flagged 1 for the per-particle companion.
+// A cell whose staged neighbourhood overflows is moved to the dense list by
+// the sweep itself.
 __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_start, int ncells, int noff,
                                                    int* __restrict__ work, int* __restrict__ list,
-                                                   unsigned char* __restrict__ flag) {
+                                                   unsigned char* __restrict__ flag, int* __restrict__ dense,
+                                                   int* __restrict__ ndense) {
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  bool take = false;
+  const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
+  bool take = false, big = false;
   if (h < ncells) {
     const int nh = cell_start[h + 1] - cell_start[h];
     take = nh >= kMinHome && nh <= kHome && noff <= kTab;
-    flag[h] = (nh > 0 && !take) ? 1 : 0;
+    big = nh > kHome;
+    flag[h] = (nh > 0 && !take) ? (big ? 2 : 1) : 0;
   }
-  const unsigned m = __ballot_sync(0xffffffffu, take);
-  int base = 0;
-  if ((threadIdx.x & 31) == 0 && m) base = atomicAdd(work + 1, __popc(m));
+  const unsigned m = __ballot_sync(0xffffffffu, take), mb = __ballot_sync(0xffffffffu, big);
+  int base = 0, bbase = 0;
+  if ((threadIdx.x & 31) == 0) {
+    if (m) base = atomicAdd(work + 1, __popc(m));
+    if (mb) bbase = atomicAdd(ndense, __popc(mb));
+  }
   base = __shfl_sync(0xffffffffu, base, 0);
-  if (take) list[base + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = h;
+  bbase = __shfl_sync(0xffffffffu, bbase, 0);
+  if (take) list[base + __popc(m & lt)] = h;
+  if (big) dense[bbase + __popc(mb & lt)] = h;
 }
 
 // Per-CTA partials from the per-thread outputs (layout of the other sweeps).
@@ -585,8 +599,7 @@ __device__ __forceinline__ void store_partials(const ThreadOut& T, double* __res
 }
 
 // Companion of the neighbourhood sweep: one thread per particle of the cells
-// it left (flag set: more than kHome particles, more than kCap staged
-// neighbours, or a stencil larger than the table).
+// flagged 1 (fewer than kMinHome particles, or a stencil larger than the table).
 template <int MODE>
 __global__ void __launch_bounds__(256) k_hood_rest(const __grid_constant__ SweepArgs A,
                                                    const __grid_constant__ HoodArgs H, float* __restrict__ forces,
@@ -609,7 +622,7 @@ __global__ void __launch_bounds__(256) k_hood_rest(const __grid_constant__ Sweep
     cx = (int)(cc & 1023u);
     cy = (int)((cc >> 10) & 1023u);
     cz = (int)(cc >> 20);
-    mine = H.flag[cx + A.nx * (cy + A.ny * cz)] != 0;
+    mine = H.flag[cx + A.nx * (cy + A.ny * cz)] == 1;
   }
   if (!__syncthreads_or(mine)) {  // nothing left here: zero partials, no reduction
     if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
@@ -619,6 +632,243 @@ __global__ void __launch_bounds__(256) k_hood_rest(const __grid_constant__ Sweep
 #pragma unroll
   for (int o = 16; o; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
   if ((threadIdx.x & 31) == 0 && ncand) atomicAdd(H.cand, ncand);
+  store_partials<MODE>(T, partials + (size_t)blockIdx.x * hood_nv(MODE));
+}
+
+// ------------------------------------------------------------ dense cells
+// Cells the neighbourhood sweep cannot stage (more than kHome particles, or a
+// staged ball over kCap entries): one CTA
+// per cell, one thread per home particle (groups of kDenseThreads). The
+// stencil's particles are taken in windows of kWin - 2: each thread loads
+// candidates of the flattened neighbour ranges (a binary search over the
+// entries' offsets), shifts them into the home frame, keeps those within
+// rc + d_max of the centre, and compacts them into shared memory, T = 0
+// from the front and T != 0 from the back, pairs interleaved as in the
+// neighbourhood sweep; then every thread sweeps the window for its own
+// particle, two candidates per step in packed f32x2 (the loads are
+// broadcasts), with the per-particle virial share of RedFallback. Warps
+// without a home particle only load.
+// The particle itself is masked by its index; with the half stencil (energy
+// only) an own-cell pair counts when the neighbour's index is the larger.
+constexpr int kDenseThreads = 256;
+constexpr int kWin = 2048;  // window entries in shared memory (even)
+
+__host__ __device__ constexpr size_t dense_smem_bytes(int noff) {
+  return (size_t)(kWin / 2) * (sizeof(float4) + sizeof(float2)) + (size_t)kWin * sizeof(int) +
+         (size_t)noff * sizeof(float4) + (size_t)(2 * noff) * sizeof(int);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kDenseThreads, 3) k_hood_dense(const __grid_constant__ SweepArgs A,
+                                                                const __grid_constant__ HoodArgs H,
+                                                                float* __restrict__ forces, double* __restrict__ grad,
+                                                                const double* __restrict__ gE,
+                                                                const double* __restrict__ pos,
+                                                                double* __restrict__ partials) {
+  constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1, HALF = MODE == 2;
+  constexpr bool GRAD = MODE == 1 || MODE == 3;
+  extern __shared__ __align__(16) unsigned char dsm[];
+  float4* txy = reinterpret_cast<float4*>(dsm);             // window pairs (x_2k, x_2k+1, y_2k, y_2k+1)
+  float2* tzz = reinterpret_cast<float2*>(txy + kWin / 2);  // (z_2k, z_2k+1)
+  int* tix = reinterpret_cast<int*>(tzz + kWin / 2);        // original index (complemented: own cell, half stencil)
+  float* txyf = reinterpret_cast<float*>(txy);
+  float* tzzf = reinterpret_cast<float*>(tzz);
+  float4* stab = reinterpret_cast<float4*>(tix + kWin);     // stencil: (shift, unwrapped offset bits)
+  int* e_start = reinterpret_cast<int*>(stab + A.noff);  // flattened offset of each entry
+  int* e_j0 = e_start + A.noff;                           // first sorted particle of each entry
+  __shared__ int s_nf, s_nb, s_item, s_run;
+  __shared__ int s_wsum[kDenseThreads / 32];
+  __shared__ float s_wmax[kDenseThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const float g = GRAD ? (float)*gE : 0.f;
+  for (int k = tid; k < A.noff; k += kDenseThreads) {
+    const Off& o = A.off[k];
+    stab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[HALF ? 1 : 0][k]));
+  }
+  ThreadOut T;
+  T.es = T.ec = 0.f;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) T.v[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) T.x[k] = 0.f;
+  unsigned long long ncand = 0;
+  RedFallback<ENERGY, FORCE> red;
+  red.irc = A.irc;
+  red.irc2 = A.irc2;
+  const int nd = *H.ndense;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(H.work + 5, 1);
+    __syncthreads();
+    const int q = s_item;
+    if (q >= nd) break;
+    const int h = H.dense[q];
+    const int hs = A.cell_start[h], nh = A.cell_start[h + 1] - hs;
+    const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
+    float cc[3];  // centre of the home cell (wrapped absolute frame), FP32
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      cc[a] = fmaf((float)cx + 0.5f, H.gf[a], fmaf((float)cy + 0.5f, H.gf[3 + a], ((float)cz + 0.5f) * H.gf[6 + a]));
+    // entries: sorted ranges laid end to end
+    if (tid == 0) s_run = 0;
+    __syncthreads();
+    for (int k0 = 0; k0 < A.noff; k0 += kDenseThreads) {
+      const int k = k0 + tid;
+      int len = 0;
+      if (k < A.noff) {
+        int ox, oy, oz;
+        unpack_off(__float_as_int(stab[k].w), ox, oy, oz);
+        int x2 = (cx + ox) % A.nx, y2 = (cy + oy) % A.ny, z2 = (cz + oz) % A.nz;
+        x2 += x2 < 0 ? A.nx : 0;
+        y2 += y2 < 0 ? A.ny : 0;
+        z2 += z2 < 0 ? A.nz : 0;
+        const int c = x2 + A.nx * (y2 + A.ny * z2);
+        e_j0[k] = A.cell_start[c];
+        len = A.cell_start[c + 1] - e_j0[k];
+      }
+      int inc = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        inc += lane >= o ? u : 0;
+      }
+      if (lane == 31) s_wsum[warp] = inc;
+      __syncthreads();
+      int off = s_run;
+      for (int w = 0; w < warp; ++w) off += s_wsum[w];
+      if (k < A.noff) e_start[k] = off + inc - len;
+      __syncthreads();
+      if (tid == kDenseThreads - 1) s_run = off + inc;
+      __syncthreads();
+    }
+    const int C = s_run;
+    for (int g0 = 0; g0 < nh; g0 += kDenseThreads) {
+      const bool own = g0 + tid < nh;
+      const int p = hs + g0 + tid;
+      const float4 pi = own ? A.xs[p] : make_float4(-kFar, -kFar, -kFar, __int_as_float(-1));
+      const int i = __float_as_int(pi.w);
+      const bool busy = __any_sync(0xffffffffu, own);  // warps without a home particle only load
+      float d = own ? fminf(sqrtf(fmaf(pi.x, pi.x, fmaf(pi.y, pi.y, pi.z * pi.z))), H.hd) : 0.f;
+#pragma unroll
+      for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+      if (lane == 0) s_wmax[warp] = d;
+      __syncthreads();
+      float dmax = s_wmax[0];
+#pragma unroll
+      for (int w = 1; w < kDenseThreads / 32; ++w) dmax = fmaxf(dmax, s_wmax[w]);
+      const float top = H.rc + dmax + H.eps, top2 = top * top;
+      typename RedFallback<ENERGY, FORCE>::Acc acc;
+      red.init(acc);
+      for (int w0 = 0; w0 < C; w0 += kWin - 2) {
+        const int w1 = min(C, w0 + kWin - 2);
+        if (tid == 0) {
+          s_nf = 0;
+          s_nb = 0;
+        }
+        __syncthreads();
+        for (int r0 = w0; r0 < w1; r0 += kDenseThreads) {
+          const int t = r0 + tid;
+          bool kf = false, kb = false;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (t < w1) {
+            int lo = 0, hi = A.noff;  // last entry whose range starts at or before t
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (e_start[mid] <= t) lo = mid;
+              else hi = mid;
+            }
+            const float4 e = stab[lo];
+            const float4 qj = __ldg(&A.xs[e_j0[lo] + (t - e_start[lo])]);
+            v.x = qj.x + e.x;
+            v.y = qj.y + e.y;
+            v.z = qj.z + e.z;
+            const int jo = __float_as_int(qj.w);
+            v.w = __int_as_float(HALF && lo == 0 ? ~jo : jo);  // own cell marked by the complement
+            bool wrap = false;
+            if (FORCE) {
+              int ox, oy, oz;
+              unpack_off(__float_as_int(e.w), ox, oy, oz);
+              wrap = (cx + ox < 0) || (cx + ox >= A.nx) || (cy + oy < 0) || (cy + oy >= A.ny) || (cz + oz < 0) ||
+                     (cz + oz >= A.nz);
+            }
+            const bool keep = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)) < top2;
+            kf = keep && !wrap;
+            kb = keep && wrap;
+          }
+          const unsigned mf = __ballot_sync(0xffffffffu, kf), mb = __ballot_sync(0xffffffffu, kb);
+          int bf = 0, bb = 0;
+          if (lane == 0) {
+            if (mf) bf = atomicAdd(&s_nf, __popc(mf));
+            if (mb) bb = atomicAdd(&s_nb, __popc(mb));
+          }
+          bf = __shfl_sync(0xffffffffu, bf, 0);
+          bb = __shfl_sync(0xffffffffu, bb, 0);
+          if (kf || kb) {
+            const int e = kf ? bf + __popc(mf & lt) : kWin - 1 - (bb + __popc(mb & lt));
+            txyf[(e >> 1) * 4 + (e & 1)] = v.x;
+            txyf[(e >> 1) * 4 + 2 + (e & 1)] = v.y;
+            tzzf[(e >> 1) * 2 + (e & 1)] = v.z;
+            tix[e] = __float_as_int(v.w);
+          }
+        }
+        __syncthreads();
+        const int nf = s_nf, nb = s_nb;
+        if (tid < 2 && ((tid == 0 ? nf : nb) & 1)) {  // padding after an odd segment
+          const int e = tid == 0 ? nf : kWin - 1 - nb;
+          txyf[(e >> 1) * 4 + (e & 1)] = kFar;
+          txyf[(e >> 1) * 4 + 2 + (e & 1)] = kFar;
+          tzzf[(e >> 1) * 2 + (e & 1)] = kFar;
+          tix[e] = -1;
+        }
+        __syncthreads();
+        if (own) ncand += (unsigned long long)(nf + nb);
+        if (busy) {
+          const float2 nx = f2(-pi.x), ny = f2(-pi.y), nz = f2(-pi.z);
+#pragma unroll
+          for (int seg = 0; seg < 2; ++seg) {
+            acc.wrap = seg == 1;
+            const int t0 = seg == 0 ? 0 : kWin - ((nb + 1) & ~1);
+            const int t1 = seg == 0 ? ((nf + 1) & ~1) : kWin;
+            for (int t = t0; t < t1; t += 2) {
+              const float4 xy = txy[t >> 1];
+              const float2 zz = tzz[t >> 1];
+              const int2 jj = *reinterpret_cast<const int2*>(tix + t);
+              const float2 dx = __fadd2_rn(make_float2(xy.x, xy.y), nx);
+              const float2 dy = __fadd2_rn(make_float2(xy.z, xy.w), ny);
+              const float2 dz = __fadd2_rn(zz, nz);
+              const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+              bool h0, h1;
+              if (HALF) {
+                h0 = jj.x >= 0 || ~jj.x > i;
+                h1 = jj.y >= 0 || ~jj.y > i;
+              } else {
+                h0 = jj.x != i;
+                h1 = jj.y != i;
+              }
+              h0 = h0 && d2.x < A.rc2;
+              h1 = h1 && d2.y < A.rc2;
+              red.hit2(acc, dx, dy, dz, d2, h0, h1);
+            }
+            red.cell_done(acc);
+          }
+        }
+        __syncthreads();
+      }
+      if (own) {
+        if (ENERGY) T.add_energy(acc.e.x + acc.e.y);
+        if (FORCE) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) T.v[k] += acc.w[k].x + acc.w[k].y;
+          hood_particle_out<MODE>(T, i, pi.x, pi.y, pi.z, cc, acc.tx, acc.ty, acc.tz, acc.ax, acc.ay, acc.az, forces,
+                                  grad, g, pos);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+  if (lane == 0 && ncand) atomicAdd(H.cand, ncand);
   store_partials<MODE>(T, partials + (size_t)blockIdx.x * hood_nv(MODE));
 }
 
@@ -717,8 +967,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     stage_warp(A, S, mine, nmine, top * top);
     __syncthreads();
     const int nf = S.nf, nb = S.nb;
-    if (nf + nb + 2 > kCap) {  // left to the per-particle companion sweep
-      if (tid == 0) H.flag[h] = 1;
+    if (nf + nb + 2 > kCap) {  // left to the dense-cell sweep
+      if (tid == 0) {
+        H.flag[h] = 2;
+        H.dense[atomicAdd(H.ndense, 1)] = h;
+      }
       continue;
     }
     if (tid == 0) H.flag[h] = 0;
@@ -874,6 +1127,34 @@ int hood_grid(int mode) {
 
 size_t hood_smem_bytes() { return sizeof(Smem); }
 
+// Persistent CTAs of the dense-cell sweep (all resident), per mode.
+int dense_grid(int mode) {
+  static int cached[4] = {0, 0, 0, 0};
+  if (mode < 0 || mode > 3) return 0;
+  if (cached[mode]) return cached[mode];
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const int most = (int)dense_smem_bytes(kMaxOff);
+  cudaError_t e;
+  if (mode == 0) {
+    e = cudaFuncSetAttribute(k_hood_dense<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_dense<0>, kDenseThreads, most);
+  } else if (mode == 1) {
+    e = cudaFuncSetAttribute(k_hood_dense<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_dense<1>, kDenseThreads, most);
+  } else if (mode == 2) {
+    e = cudaFuncSetAttribute(k_hood_dense<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_dense<2>, kDenseThreads, most);
+  } else {
+    e = cudaFuncSetAttribute(k_hood_dense<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_dense<3>, kDenseThreads, most);
+  }
+  if (e != cudaSuccess || per < 1) return 0;
+  cached[mode] = sms * per;
+  return cached[mode];
+}
+
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
                    HoodArgs* H) {
   std::memset(H, 0, sizeof(*H));
@@ -907,34 +1188,43 @@ int launch_hood(const SweepArgs& A, const HoodArgs& Hin, int* work, int mode, co
                 double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s) {
   const int NV = hood_nv(mode);
   const int nrest = (A.n + 255) / 256;  // CTAs of the companion sweep
+  const int ndc = dense_grid(mode);     // CTAs of the dense-cell sweep
   int nb = hood_grid(mode);
-  if (nb <= 0) return CL_ERR_CUDA;
+  if (nb <= 0 || ndc <= 0) return CL_ERR_CUDA;
   if (nb > Hin.ncells) nb = Hin.ncells;
-  const long long room = partials_cap / NV - nrest;
+  const long long room = partials_cap / NV - nrest - ndc;
   if (nb > room) nb = (int)room;
   if (nb < 1) return CL_ERR_INVALID_ARG;
   HoodArgs H = Hin;
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
-  if (cudaMemsetAsync(work, 0, 4 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
-  k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag);
+  H.ndense = work + 4;
+  if (cudaMemsetAsync(work, 0, 6 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
+                                                     H.ndense);
   const size_t smem = sizeof(Smem);
   double* rest = partials + (size_t)nb * NV;
+  double* dpart = rest + (size_t)nrest * NV;
+  const size_t dsmem = dense_smem_bytes(A.noff);
   if (mode == 0) {
     k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<0><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+    k_hood_dense<0><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else if (mode == 1) {
     k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<1><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+    k_hood_dense<1><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else if (mode == 2) {
     k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<2><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+    k_hood_dense<2><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else {
     k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<3><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
+    k_hood_dense<3><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   }
   const int final_mode = mode == 2 ? 1 : (mode == 0 ? 2 : (mode == 1 ? 3 : 4));
-  return finish_reduction(final_mode, 3, hinv, nb + nrest, NV, partials, sums, energy, virial, gradbox, gE, s);
+  return finish_reduction(final_mode, 3, hinv, nb + nrest + ndc, NV, partials, sums, energy, virial, gradbox, gE, s);
 }
 
 }  // namespace clk

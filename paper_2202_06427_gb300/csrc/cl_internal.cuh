@@ -136,10 +136,13 @@ struct HoodArgs {
   float hd;           // largest distance of a cell point from the cell centre
   float eps;          // rounding margin of the staging radius
   int ncells;
-  int* work;          // [0] work counter, [1] list length; zeroed by the launcher
+  int* work;          // [0] work counter, [1] list length, [4] dense cells, [5] their work counter;
+                      // zeroed by the launcher
   int* list;          // cells the neighbourhood sweep takes (ncells capacity)
   unsigned long long* cand;  // candidate pairs evaluated (work[2..3] of the same buffer), zeroed by the launcher
-  unsigned char* flag;       // per cell: 1 when the cell is left to the per-particle companion sweep
+  unsigned char* flag;       // per cell: 1 per-particle companion sweep, 2 dense-cell sweep
+  int* dense;                // cells of the dense-cell sweep (ncells capacity)
+  int* ndense;               // their number (work[4])
 };
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
                    HoodArgs* H);

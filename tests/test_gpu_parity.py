@@ -57,12 +57,50 @@ for dim in (2, 3):
 
 @pytest.mark.parametrize("dim,tric,lcell,rc_frac", SMALL)
 def test_small_all_reductions(cuda_ok, dim, tric, lcell, rc_frac):
-    P = _P()
     n_side, L, rc = _regime(dim, rc_frac)
     seed = 100 + dim * 1000 + tric * 100 + lcell * 10 + int(rc_frac * 100)
     x, h = _lattice_set(dim, tric, n_side, L, seed)
     w = oracle.geom_info(h, 1.0)["w"]
     assert rc < w.min()
+    _check_all_reductions(x, h, rc, lcell)
+
+
+def _dense_clusters(tric, seed):
+    """Sparse jittered lattice (spacing 2) in a box of side 40 with two dense
+    spheres (radius 3, lattice spacing 0.5, jitter 0.1: density 8, nearest
+    pairs 0.3 apart) replacing it locally."""
+    rng = np.random.default_rng(seed)
+    L = 40.0
+    h = np.eye(3) * L
+    if tric:
+        h[1, 0], h[2, 0], h[2, 1] = 6.0, -5.0, 4.0
+    s = (np.stack(np.meshgrid(*[np.arange(20)] * 3, indexing="ij"), -1).reshape(-1, 3) + 0.5) / 20.0
+    bg = (s + rng.uniform(-0.2, 0.2, size=s.shape) / 20.0) @ h
+    centres = np.array([[12.0, 14.0, 13.0], [27.0, 25.0, 26.0]])
+    g = np.stack(np.meshgrid(*[np.arange(-6, 7) * 0.5] * 3, indexing="ij"), -1).reshape(-1, 3)
+    g = g[np.linalg.norm(g, axis=1) <= 3.0]
+    parts = [bg[np.min(np.linalg.norm(bg[:, None, :] - centres[None], axis=2), axis=1) > 3.5]]
+    for c in centres:
+        parts.append(c + g + rng.uniform(-0.1, 0.1, size=g.shape))
+    x = np.vstack(parts)
+    return np.ascontiguousarray(x[rng.permutation(x.shape[0])]), h
+
+
+@pytest.mark.parametrize("tric,lcell", [(False, 1), (True, 1), (False, 2), (True, 3)])
+def test_dense_cells_all_reductions(cuda_ok, tric, lcell):
+    """Cells with hundreds of particles and neighbourhoods far beyond the
+    staging buffer (the dense-cell sweep, in groups of home particles), next to
+    sparse cells (the per-particle companion) and ordinary ones."""
+    P = _P()
+    x, h = _dense_clusters(tric, 300 + lcell + 10 * tric)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, 4.0, lcell)
+    if lcell == 1:
+        assert P.cl_query(cl, "max_occupancy") > 256
+    _check_all_reductions(x, h, 4.0, lcell)
+
+
+def _check_all_reductions(x, h, rc, lcell):
+    P = _P()
     nbins = 37
     ref = oracle.pair_map(x, h, rc, band=BAND, nbins=nbins)
     pos = torch.from_numpy(x).cuda()
