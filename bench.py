@@ -373,8 +373,9 @@ def run_ours(args, rank, world, local):
                        "step": "binning + fused energy/forces/box-gradient sweep (forward) + chain rule (backward)",
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            # bin, 3 scan, scatter, pair pack; cell list, sweep, per-particle companion, 2 reduce; 2 scale
-            "gpu_launches": 13 * args.steps,
+            # bin, 3 scan, scatter, pair pack; cell list, sweep, per-particle companion, dense-cell sweep,
+            # 2 reduce; 2 scale
+            "gpu_launches": 14 * args.steps,
             "clocks": clocks, "roofline": roofline}
 
     if not args.no_e2e:
