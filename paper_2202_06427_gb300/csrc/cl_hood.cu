@@ -681,6 +681,11 @@ __global__ void __launch_bounds__(kDenseThreads, 3) k_hood_dense(const __grid_co
   __shared__ float s_wmax[kDenseThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
+  const int nd = *H.ndense;
+  if ((int)blockIdx.x >= nd) {  // the first nd CTAs take every dense cell through the counter
+    if (tid < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + tid] = 0.0;
+    return;
+  }
   const float g = GRAD ? (float)*gE : 0.f;
   for (int k = tid; k < A.noff; k += kDenseThreads) {
     const Off& o = A.off[k];
@@ -696,7 +701,6 @@ __global__ void __launch_bounds__(kDenseThreads, 3) k_hood_dense(const __grid_co
   RedFallback<ENERGY, FORCE> red;
   red.irc = A.irc;
   red.irc2 = A.irc2;
-  const int nd = *H.ndense;
   for (;;) {
     __syncthreads();
     if (tid == 0) s_item = atomicAdd(H.work + 5, 1);
