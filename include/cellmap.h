@@ -28,6 +28,10 @@
  *    it synchronizes. Device pointers passed in are owned by the caller and
  *    must stay valid until the work on the stream has completed. The cl_list
  *    handle and its device workspace are owned by the library.
+ *  - The calls on one handle share its workspace (cell arrays, work lists,
+ *    partial sums): their GPU work must not overlap, so issue them on one
+ *    stream, or order the streams. Different handles are independent; a
+ *    process may drive several devices (launch parameters are kept per device).
  *  - Return value: CL_OK (0) or a negative error code; cl_error_string()
  *    names it. A failed call leaves the handle usable unless it says
  *    otherwise. Errors detected on the device (non-finite positions) are

@@ -1113,11 +1113,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
 }  // namespace
 
 int hood_grid(int mode) {
-  static int cached[4] = {0, 0, 0, 0};
+  static DevCache cached[4];
   if (mode < 0 || mode > 3) return 0;
-  if (cached[mode]) return cached[mode];
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (const int c = cached[mode].get(dev)) return c;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   cudaError_t e;
   if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<0>, kThreads, sizeof(Smem));
@@ -1125,19 +1125,20 @@ int hood_grid(int mode) {
   else if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<2>, kThreads, sizeof(Smem));
   else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<3>, kThreads, sizeof(Smem));
   if (e != cudaSuccess || per < 1) return 0;
-  cached[mode] = sms * per;
-  return cached[mode];
+  cached[mode].put(dev, sms * per);
+  return sms * per;
 }
 
 size_t hood_smem_bytes() { return sizeof(Smem); }
 
-// Persistent CTAs of the dense-cell sweep (all resident), per mode.
+// Persistent CTAs of the dense-cell sweep (all resident), per mode; also
+// raises the kernels' shared-memory limit on the current device.
 int dense_grid(int mode) {
-  static int cached[4] = {0, 0, 0, 0};
+  static DevCache cached[4];
   if (mode < 0 || mode > 3) return 0;
-  if (cached[mode]) return cached[mode];
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (const int c = cached[mode].get(dev)) return c;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   const int most = (int)dense_smem_bytes(kMaxOff);
   cudaError_t e;
@@ -1155,8 +1156,8 @@ int dense_grid(int mode) {
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_dense<3>, kDenseThreads, most);
   }
   if (e != cudaSuccess || per < 1) return 0;
-  cached[mode] = sms * per;
-  return cached[mode];
+  cached[mode].put(dev, sms * per);
+  return sms * per;
 }
 
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,

@@ -22,9 +22,23 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "cellmap.h"
 
 namespace clk {
+
+// Launch parameters worked out once per device (occupancy, opt-in shared
+// memory, which cudaFuncSetAttribute sets for the current device only): one
+// slot per device, 0 until known. Devices past the table are not cached.
+constexpr int kCacheDevices = 64;
+struct DevCache {
+  std::atomic<int> v[kCacheDevices];
+  int get(int dev) const { return dev >= 0 && dev < kCacheDevices ? v[dev].load(std::memory_order_relaxed) : 0; }
+  void put(int dev, int x) {
+    if (dev >= 0 && dev < kCacheDevices) v[dev].store(x, std::memory_order_relaxed);
+  }
+};
 
 constexpr int kMaxOff = 768;      // stencil entries (9^3 = 729 plus margin)
 constexpr int kMaxAxis = 1023;    // cells per axis (10-bit packing)

@@ -693,26 +693,28 @@ size_t pairs_cell_smem(int noff, bool fill) {
 template <int DIM, bool FILL>
 static int launch_cell(const SweepArgs& A, float ball2, unsigned char* flag, int* fcells, int* nfcells, int* count,
                        const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
-  static int per_sm = 0, sms = 0;
-  if (!per_sm) {
-    int dev = 0, per = 0;
+  static DevCache grid;  // resident CTAs per device (shared-memory limit raised on first use)
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return CL_ERR_CUDA;
+  int blocks = grid.get(dev);
+  if (!blocks) {
+    int sms = 0, per = 0;
     const int most = (int)pairs_cell_smem(kMaxOff, FILL);
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         cudaFuncSetAttribute(k_pairs_cell<DIM, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
             cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_cell<DIM, FILL>, FILL ? 256 : 128,
                                                       pairs_cell_smem(125, FILL)) != cudaSuccess ||
         per < 1)
       return CL_ERR_CUDA;
-    per_sm = per;
+    blocks = sms * per;
+    grid.put(dev, blocks);
   }
-  long long blocks = (long long)sms * per_sm;
   const long long ncells = (long long)A.nx * A.ny * A.nz;
-  if (blocks > ncells) blocks = ncells;
-  k_pairs_cell<DIM, FILL><<<(int)blocks, FILL ? 256 : 128, pairs_cell_smem(A.noff, FILL), s>>>(A, ball2, flag, fcells,
-                                                                                                 nfcells, count,
-                                                                                              start, pi, pj, pd);
+  if (blocks > ncells) blocks = (int)ncells;
+  k_pairs_cell<DIM, FILL><<<blocks, FILL ? 256 : 128, pairs_cell_smem(A.noff, FILL), s>>>(A, ball2, flag, fcells,
+                                                                                           nfcells, count, start, pi,
+                                                                                           pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
