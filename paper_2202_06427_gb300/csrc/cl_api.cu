@@ -225,6 +225,23 @@ float pairs_ball2(const clk::Geo& g) {
   return (float)(r * r);
 }
 
+// Staged entries per cell for the pair list: the particles of the staging ball
+// at the box's mean density, with 30 % to spare, in steps of 256 (1,024 to
+// 3,072). Denser cells overflow and take the per-particle path.
+int pairs_stage_cap(const clk::Geo& g, long long n, float ball2) {
+  double vol = 1.0;
+  if (g.dim == 3)
+    vol = std::fabs(g.h[0] * (g.h[4] * g.h[8] - g.h[5] * g.h[7]) - g.h[1] * (g.h[3] * g.h[8] - g.h[5] * g.h[6]) +
+                    g.h[2] * (g.h[3] * g.h[7] - g.h[4] * g.h[6]));
+  else
+    vol = std::fabs(g.h[0] * g.h[4] - g.h[1] * g.h[3]);
+  const double r = std::sqrt((double)ball2);
+  const double ball = g.dim == 3 ? 4.18879020478639 * r * r * r : 3.14159265358979 * r * r;
+  const double est = (vol > 0 ? (double)n / vol : 0.0) * ball * 1.3 + 64.0;
+  int cap = (int)std::ceil(est / 256.0) * 256;
+  return std::min(3072, std::max(1024, cap));
+}
+
 // Neighbour list: count pass, scan, one synchronisation to learn the total,
 // fill pass (each segment sorted as it is written).
 int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
@@ -252,7 +269,9 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   const float ball2 = pairs_ball2(c->geo);
   // hflag / hlist: per-cell flags and the flagged cells (shared with the
   // neighbourhood sweep, which rewrites them on every launch); pl_meta[4]: their number
-  if ((e = clk::launch_pairs_count(*c->full, dim, ball2, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, s))) return e;
+  const int cap = pairs_stage_cap(c->geo, c->n, ball2);
+  if ((e = clk::launch_pairs_count(*c->full, dim, ball2, cap, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, s)))
+    return e;
   if ((e = clk::launch_scan(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
   int total = 0, meta[4] = {0, 0, 0, 0};
   if (cudaMemcpyAsync(&total, c->pl_start + c->n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -263,7 +282,7 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   if (total > r->capacity) return CL_ERR_CAPACITY;
   if (total == 0) return CL_OK;
   if (!r->pair_i || !r->pair_j || !r->pair_d) return CL_ERR_INVALID_ARG;
-  return clk::launch_pairs_fill(*c->full, dim, ball2, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, c->pl_start,
+  return clk::launch_pairs_fill(*c->full, dim, ball2, cap, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, c->pl_start,
                                r->pair_i, r->pair_j, r->pair_d, c->pl_long, c->pl_meta + 3, s);
 }
 

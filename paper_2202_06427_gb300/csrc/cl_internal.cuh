@@ -183,15 +183,16 @@ constexpr int kMaxSegment = 1024;  // segments up to this length are sorted by o
 // Count pass of the pair list: per-cell staged sweep, then the per-particle
 // sweep for the cells it flags (flag: ncells bytes; fcells: ncells ints, the
 // flagged cells, *nfcells of them; all written here).
-int launch_pairs_count(const SweepArgs& A, int dim, float ball2, unsigned char* flag, int* fcells, int* nfcells,
-                       int* count, cudaStream_t s);
+// cap: staged entries per cell (32..3072), the same for the count and fill passes.
+int launch_pairs_count(const SweepArgs& A, int dim, float ball2, int cap, unsigned char* flag, int* fcells,
+                       int* nfcells, int* count, cudaStream_t s);
 // Sorts each segment [start[a], start[a] + count[a]) of pj (carrying pd) by pj;
 // longs (n ints) and nlong (1 int) are workspace.
 int launch_pairs_sort(int n, const int* count, const int* start, int* pj, float* pd, int* longs, int* nlong,
                       cudaStream_t s);
 // Fill pass: the same two sweeps, each segment sorted by j and written.
 // longs (n ints) and nlong (1 int): workspace for segments longer than kMaxSegment.
-int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned char* flag, const int* fcells,
+int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, int cap, const unsigned char* flag, const int* fcells,
                       const int* nfcells, const int* count, const int* start, int* pi, int* pj, float* pd, int* longs,
                       int* nlong, cudaStream_t s);
 

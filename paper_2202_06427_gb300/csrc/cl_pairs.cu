@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(1024) k_pairs_sort_long(const int* __restrict_
 // [start[a], start[a] + count[a]) with coalesced stores. Segments are at most
 // kMaxSegment long (the host checks the counts first).
 constexpr int kFillWarps = 4;
-constexpr int kStage = 2048;  // staged neighbourhood of one cell
+constexpr int kStageMax = 3072;  // largest staged neighbourhood of one cell (the launch picks its capacity)
 constexpr int kSegPad = kMaxSegment + kMaxSegment / 32;
 
 // Segment buffer index with one pad word per 32: conflict-free both for lane i
@@ -568,7 +568,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
 // order, coalesced, as the ballot finds them.
 template <int DIM, bool FILL>
 __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
-                                                                               float ball2,
+                                                                               float ball2, int cap,
                                                                                unsigned char* __restrict__ flag,
                                                                                int* __restrict__ fcells,
                                                                                int* __restrict__ nfcells,
@@ -580,13 +580,13 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
   constexpr int W = FILL ? 8 : 4;
   extern __shared__ float4 smem[];
   float4* st = smem;           // staged neighbourhood: (x, y, z in the cell's frame, original index)
-  float4* stab = st + kStage;  // stencil: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
+  float4* stab = st + cap;     // stencil: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
   int* scal = reinterpret_cast<int*>(stab + A.noff);  // [0] staged count, [1..2] index range, [4..] warp sums
   unsigned* rk0 = reinterpret_cast<unsigned*>(scal + 16);  // FILL: radix keys, slots, counters
-  unsigned* rk1 = rk0 + kStage;
-  int* cnt = reinterpret_cast<int*>(rk1 + kStage);
+  unsigned* rk1 = rk0 + cap;
+  int* cnt = reinterpret_cast<int*>(rk1 + cap);
   unsigned short* rs0 = reinterpret_cast<unsigned short*>(cnt + 256 * W);
-  unsigned short* rs1 = rs0 + kStage;
+  unsigned short* rs1 = rs0 + cap;
   stencil_to_smem(A, stab);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -620,13 +620,13 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
         base = __shfl_sync(0xffffffffu, base, 0);
         if (keep) {
           const int e = base + __popc(m & lt);
-          if (e < kStage) st[e] = v;
+          if (e < cap) st[e] = v;
         }
       }
     }
     __syncthreads();
     const int S = scal[0];
-    if (S <= kStage) {
+    if (S <= cap) {
       unsigned* keys = rk0;
       unsigned short* slots = rs0;
       int kmin = 0;
@@ -677,54 +677,55 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
       }
     }
     if (!FILL && threadIdx.x == 0) {
-      flag[c] = S > kStage ? 1 : 0;
-      if (S > kStage) fcells[atomicAdd(nfcells, 1)] = c;
+      flag[c] = S > cap ? 1 : 0;
+      if (S > cap) fcells[atomicAdd(nfcells, 1)] = c;
     }
     __syncthreads();
   }
 }
 
-size_t pairs_cell_smem(int noff, bool fill) {
-  const size_t head = (size_t)(kStage + noff) * sizeof(float4) + 16 * sizeof(int);
-  return fill ? head + 2 * kStage * sizeof(unsigned) + 256 * 8 * sizeof(int) + 2 * kStage * sizeof(unsigned short)
+size_t pairs_cell_smem(int noff, bool fill, int cap) {
+  const size_t head = (size_t)(cap + noff) * sizeof(float4) + 16 * sizeof(int);
+  return fill ? head + 2 * (size_t)cap * sizeof(unsigned) + 256 * 8 * sizeof(int) +
+                    2 * (size_t)cap * sizeof(unsigned short)
               : head;
 }
 
 template <int DIM, bool FILL>
-static int launch_cell(const SweepArgs& A, float ball2, unsigned char* flag, int* fcells, int* nfcells, int* count,
-                       const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
-  static DevCache grid;  // resident CTAs per device (shared-memory limit raised on first use)
-  int dev = 0;
+static int launch_cell(const SweepArgs& A, float ball2, int cap, unsigned char* flag, int* fcells, int* nfcells,
+                       int* count, const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
+  static DevCache ready;  // shared-memory limit raised on this device
+  if (cap < 32 || cap > kStageMax) return CL_ERR_INVALID_ARG;
+  int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return CL_ERR_CUDA;
-  int blocks = grid.get(dev);
-  if (!blocks) {
-    int sms = 0, per = 0;
-    const int most = (int)pairs_cell_smem(kMaxOff, FILL);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaFuncSetAttribute(k_pairs_cell<DIM, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize, most) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_cell<DIM, FILL>, FILL ? 256 : 128,
-                                                      pairs_cell_smem(125, FILL)) != cudaSuccess ||
-        per < 1)
+  if (!ready.get(dev)) {
+    if (cudaFuncSetAttribute(k_pairs_cell<DIM, FILL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)pairs_cell_smem(kMaxOff, FILL, kStageMax)) != cudaSuccess)
       return CL_ERR_CUDA;
-    blocks = sms * per;
-    grid.put(dev, blocks);
+    ready.put(dev, 1);
   }
+  const size_t smem = pairs_cell_smem(A.noff, FILL, cap);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_cell<DIM, FILL>, FILL ? 256 : 128, smem) !=
+          cudaSuccess ||
+      per < 1)
+    return CL_ERR_CUDA;
+  long long blocks = (long long)sms * per;
   const long long ncells = (long long)A.nx * A.ny * A.nz;
-  if (blocks > ncells) blocks = (int)ncells;
-  k_pairs_cell<DIM, FILL><<<blocks, FILL ? 256 : 128, pairs_cell_smem(A.noff, FILL), s>>>(A, ball2, flag, fcells,
-                                                                                           nfcells, count, start, pi,
-                                                                                           pj, pd);
+  if (blocks > ncells) blocks = ncells;
+  k_pairs_cell<DIM, FILL><<<(int)blocks, FILL ? 256 : 128, smem, s>>>(A, ball2, cap, flag, fcells, nfcells, count,
+                                                                      start, pi, pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
-int launch_pairs_count(const SweepArgs& A, int dim, float ball2, unsigned char* flag, int* fcells, int* nfcells,
-                       int* count, cudaStream_t s) {
+int launch_pairs_count(const SweepArgs& A, int dim, float ball2, int cap, unsigned char* flag, int* fcells,
+                       int* nfcells, int* count, cudaStream_t s) {
   if (A.n <= 0) return CL_OK;
   if (cudaMemsetAsync(nfcells, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
-  const int e =
-      dim == 3 ? launch_cell<3, false>(A, ball2, flag, fcells, nfcells, count, nullptr, nullptr, nullptr, nullptr, s)
-               : launch_cell<2, false>(A, ball2, flag, fcells, nfcells, count, nullptr, nullptr, nullptr, nullptr, s);
+  const int e = dim == 3 ? launch_cell<3, false>(A, ball2, cap, flag, fcells, nfcells, count, nullptr, nullptr,
+                                                 nullptr, nullptr, s)
+                         : launch_cell<2, false>(A, ball2, cap, flag, fcells, nfcells, count, nullptr, nullptr,
+                                                 nullptr, nullptr, s);
   if (e) return e;
   if (dim == 3) k_pairs_count<3><<<152 * 4, 256, 0, s>>>(A, fcells, nfcells, count);
   else k_pairs_count<2><<<152 * 4, 256, 0, s>>>(A, fcells, nfcells, count);
@@ -737,14 +738,14 @@ static int launch_sort_long(const int* longs, const int* nlong, const int* count
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
-int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, const unsigned char* flag, const int* fcells,
+int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, int cap, const unsigned char* flag, const int* fcells,
                       const int* nfcells, const int* count, const int* start, int* pi, int* pj, float* pd, int* longs,
                       int* nlong, cudaStream_t s) {
   if (A.n <= 0) return CL_OK;
   unsigned char* fl = const_cast<unsigned char*>(flag);  // only read by the fill pass
   int* cn = const_cast<int*>(count);                     // likewise
-  const int e = dim == 3 ? launch_cell<3, true>(A, ball2, fl, nullptr, nullptr, cn, start, pi, pj, pd, s)
-                         : launch_cell<2, true>(A, ball2, fl, nullptr, nullptr, cn, start, pi, pj, pd, s);
+  const int e = dim == 3 ? launch_cell<3, true>(A, ball2, cap, fl, nullptr, nullptr, cn, start, pi, pj, pd, s)
+                         : launch_cell<2, true>(A, ball2, cap, fl, nullptr, nullptr, cn, start, pi, pj, pd, s);
   if (e) return e;
   const size_t dyn = (size_t)A.noff * sizeof(float4);
   if (cudaMemsetAsync(nlong, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
