@@ -50,8 +50,8 @@ FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j' - x_i|^2
 FLOP_PER_HIT_FUSED = 16     # 1/r (1); fsn = y (y^2 - 1/rc^2) (3); force 3 fma (6); r = d2 y (1),
                             # t = 1 - r/rc (2), t^2 (1), e += t^2 y (2)
 # DRAM bytes per launch of the fused sweep (k_hood<3>, 1M lattice, lcell 2), from
-# ncu --set full: dram__bytes_read.sum + dram__bytes_write.sum = 40.77 MB + 1.22 MB.
-SWEEP_DRAM_BYTES = 41.99e6
+# ncu --set full: dram__bytes_read.sum + dram__bytes_write.sum = 40.71 MB + 1.21 MB.
+SWEEP_DRAM_BYTES = 41.93e6
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128
 
