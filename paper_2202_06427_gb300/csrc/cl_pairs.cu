@@ -631,7 +631,41 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
       unsigned short* slots = rs0;
       int kmin = 0;
       if (FILL) stage_radix<W>(st, S, rk0, rk1, rs0, rs1, cnt, scal, keys, slots, kmin);
-      for (int p = h0 + warp; p < h1; p += W) {
+      if (!FILL) {
+        // COUNT: two home particles per warp share each staged load; the
+        // distance of each (particle, candidate) is computed as in the fill pass.
+        for (int p = h0 + 2 * warp; p < h1; p += 2 * W) {
+          const bool two = p + 1 < h1;
+          const float4 pa = A.xs[p];
+          const float4 pb = two ? A.xs[p + 1] : pa;
+          const int a0 = __float_as_int(pa.w), a1 = two ? __float_as_int(pb.w) : INT_MAX;
+          int L0 = 0, L1 = 0;
+#pragma unroll 2
+          for (int t0 = 0; t0 < S; t0 += 32) {
+            const int t = t0 + lane;
+            bool k0 = false, k1 = false;
+            if (t < S) {
+              const float4 q = st[t];
+              const int jo = __float_as_int(q.w);
+              const float dx0 = q.x - pa.x, dy0 = q.y - pa.y;
+              const float dz0 = DIM == 3 ? q.z - pa.z : 0.f;
+              const float d20 = DIM == 3 ? fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0)) : fmaf(dx0, dx0, dy0 * dy0);
+              const float dx1 = q.x - pb.x, dy1 = q.y - pb.y;
+              const float dz1 = DIM == 3 ? q.z - pb.z : 0.f;
+              const float d21 = DIM == 3 ? fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1)) : fmaf(dx1, dx1, dy1 * dy1);
+              k0 = jo > a0 && d20 < A.rc2;
+              k1 = jo > a1 && d21 < A.rc2;
+            }
+            L0 += __popc(__ballot_sync(0xffffffffu, k0));
+            L1 += __popc(__ballot_sync(0xffffffffu, k1));
+          }
+          if (lane == 0) {
+            count[a0] = L0;
+            if (two) count[a1] = L1;
+          }
+        }
+      }
+      for (int p = h0 + warp; p < (FILL ? h1 : h0); p += W) {
         const float4 pi = A.xs[p];
         const int a = __float_as_int(pi.w);
         int first = 0;  // FILL: first position (in index order) with index > a
