@@ -665,49 +665,78 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
           }
         }
       }
-      for (int p = h0 + warp; p < (FILL ? h1 : h0); p += W) {
-        const float4 pi = A.xs[p];
-        const int a = __float_as_int(pi.w);
-        int first = 0;  // FILL: first position (in index order) with index > a
-        if (FILL && a >= kmin) {
-          const unsigned ka = (unsigned)(a - kmin);
-          int lo = 0, hi = S;
-          while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (keys[mid] > ka) hi = mid;
-            else lo = mid + 1;
-          }
-          first = lo;
-        }
-        const int cnt_a = FILL ? __ldg(count + a) : 0;
-        const int base = FILL ? __ldg(start + a) : 0;
-        int L = 0;
-#pragma unroll 2
-        for (int t0 = first; t0 < S; t0 += 32) {
-          const int t = t0 + lane;
-          bool keep = false;
-          int jo = 0;
-          float d2 = 0.f;
-          if (t < S) {
-            const float4 q = st[FILL ? (int)slots[t] : t];
-            jo = __float_as_int(q.w);
-            const float dx = q.x - pi.x, dy = q.y - pi.y;
-            const float dz = DIM == 3 ? q.z - pi.z : 0.f;
-            d2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
-            keep = jo > a && d2 < A.rc2;
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, keep);
-          if (FILL && keep) {
-            const int e = L + __popc(m & lt);
-            if (e < cnt_a) {
-              pi_out[base + e] = a;
-              pj_out[base + e] = jo;
-              pd_out[base + e] = d2 * rsqrt_nr(d2);
+      if (FILL) {
+        // FILL: two home particles per warp; the sweep starts at the earlier of
+        // their suffixes (entries before a particle's own suffix fail j > i) and
+        // each particle's kept pairs are written in order from its own ballot.
+        for (int p = h0 + 2 * warp; p < h1; p += 2 * W) {
+          const bool two = p + 1 < h1;
+          const float4 pa = A.xs[p];
+          const float4 pb = two ? A.xs[p + 1] : pa;
+          const int a0 = __float_as_int(pa.w), a1 = two ? __float_as_int(pb.w) : INT_MAX;
+          int f0 = 0, f1 = S;  // first position (in index order) with index > a0, a1
+          {
+            const unsigned ka = a0 >= kmin ? (unsigned)(a0 - kmin) : 0u;
+            int lo = 0, hi = S;
+            while (a0 >= kmin && lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (keys[mid] > ka) hi = mid;
+              else lo = mid + 1;
             }
+            f0 = a0 >= kmin ? lo : 0;
           }
-          L += __popc(m);
+          if (two) {
+            const unsigned kb = a1 >= kmin ? (unsigned)(a1 - kmin) : 0u;
+            int lo = 0, hi = S;
+            while (a1 >= kmin && lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (keys[mid] > kb) hi = mid;
+              else lo = mid + 1;
+            }
+            f1 = a1 >= kmin ? lo : 0;
+          }
+          const int c0 = __ldg(count + a0), b0 = __ldg(start + a0);
+          const int c1 = two ? __ldg(count + a1) : 0, b1 = two ? __ldg(start + a1) : 0;
+          int L0 = 0, L1 = 0;
+#pragma unroll 2
+          for (int t0 = min(f0, f1); t0 < S; t0 += 32) {
+            const int t = t0 + lane;
+            bool k0 = false, k1 = false;
+            int jo = 0;
+            float d20 = 0.f, d21 = 0.f;
+            if (t < S) {
+              const float4 q = st[(int)slots[t]];
+              jo = __float_as_int(q.w);
+              const float dx0 = q.x - pa.x, dy0 = q.y - pa.y;
+              const float dz0 = DIM == 3 ? q.z - pa.z : 0.f;
+              d20 = DIM == 3 ? fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0)) : fmaf(dx0, dx0, dy0 * dy0);
+              const float dx1 = q.x - pb.x, dy1 = q.y - pb.y;
+              const float dz1 = DIM == 3 ? q.z - pb.z : 0.f;
+              d21 = DIM == 3 ? fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1)) : fmaf(dx1, dx1, dy1 * dy1);
+              k0 = jo > a0 && d20 < A.rc2;
+              k1 = jo > a1 && d21 < A.rc2;
+            }
+            const unsigned m0 = __ballot_sync(0xffffffffu, k0), m1 = __ballot_sync(0xffffffffu, k1);
+            if (k0) {
+              const int e = L0 + __popc(m0 & lt);
+              if (e < c0) {
+                pi_out[b0 + e] = a0;
+                pj_out[b0 + e] = jo;
+                pd_out[b0 + e] = d20 * rsqrt_nr(d20);
+              }
+            }
+            if (k1) {
+              const int e = L1 + __popc(m1 & lt);
+              if (e < c1) {
+                pi_out[b1 + e] = a1;
+                pj_out[b1 + e] = jo;
+                pd_out[b1 + e] = d21 * rsqrt_nr(d21);
+              }
+            }
+            L0 += __popc(m0);
+            L1 += __popc(m1);
+          }
         }
-        if (!FILL && lane == 0) count[a] = L;
       }
     }
     if (!FILL && threadIdx.x == 0) {
