@@ -1,7 +1,11 @@
 """Helpers shared by the GPU parity tests: tolerances, comparison rules and a
 spawn-based pool that runs the (single-threaded) oracle on index ranges.
 
-Tolerances (derived in DESIGN.md, "Parity rules"):
+Tolerances. A pair whose FP64 distance lies within BAND * rc of the cutoff (or
+of a bin edge) may be decided either way by a correct FP32 path; the oracle
+counts such band pairs apart. The floating-point rules follow from FP32 pair
+terms on cell-centred coordinates (relative error of order 1e-7 per term)
+summed in FP64:
   counts       exact outside the band: oracle count - band_in <= gpu <= count + band_out
   histograms   exact outside the band: core[k] <= gpu[k] <= core[k] + maybe[k]
   sum 1/r      relative 1e-6, plus 1/rc for every band pair that may flip
