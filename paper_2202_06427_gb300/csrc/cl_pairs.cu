@@ -456,15 +456,15 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
 }
 
 // Stable LSD radix sort (8-bit digits) of the staged list's original indices,
-// the whole CTA (W warps) taking part: keys jo - kmin with slots 0..S-1 into
-// st. Each warp ranks a fixed span of positions in order with
+// the whole CTA (W warps) taking part: the slots 0..S-1 into st are sorted by
+// the key jo - kmin, read through the slot (no key array, so that four CTAs
+// fit per SM). Each warp ranks a fixed span of positions in order with
 // __match_any_sync, and the (digit, warp) offsets come from one exclusive scan
-// per pass, so equal digits keep their order. Returns the buffers that hold
-// the result.
+// per pass, so equal digits keep their order. Returns the buffer that holds
+// the sorted slots.
 template <int W>
-__device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k0, unsigned* k1, unsigned short* s0,
-                                            unsigned short* s1, int* cnt, int* scal, unsigned*& keys,
-                                            unsigned short*& slots, int& kmin) {
+__device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned short* s0, unsigned short* s1, int* cnt,
+                                            int* scal, unsigned short*& slots, int& kmin) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) {
@@ -487,10 +487,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
   __syncthreads();
   kmin = scal[1];
   const unsigned range = (unsigned)(scal[2] - kmin);
-  for (int i = threadIdx.x; i < S; i += blockDim.x) {
-    k0[i] = (unsigned)(__float_as_int(st[i].w) - kmin);
-    s0[i] = (unsigned short)i;
-  }
+  for (int i = threadIdx.x; i < S; i += blockDim.x) s0[i] = (unsigned short)i;
   __syncthreads();
   const int bits = range ? 32 - __clz(range) : 0;
   const int span = (((S + W - 1) / W) + 31) & ~31;
@@ -501,7 +498,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
     for (int r = b0; r < b1; r += 32) {
       const int i = r + lane;
       const bool ok = i < b1;
-      const int d = ok ? (int)((k0[i] >> sh) & 255u) : 256 + lane;
+      const int d = ok ? (int)(((unsigned)(__float_as_int(st[s0[i]].w) - kmin) >> sh) & 255u) : 256 + lane;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
       if (ok && lane == __ffs(peers) - 1) cnt[d * W + warp] += __popc(peers);
       __syncwarp();
@@ -531,7 +528,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
     for (int r = b0; r < b1; r += 32) {
       const int i = r + lane;
       const bool ok = i < b1;
-      const unsigned key = ok ? k0[i] : 0u;
+      const unsigned key = ok ? (unsigned)(__float_as_int(st[s0[i]].w) - kmin) : 0u;
       const int d = ok ? (int)((key >> sh) & 255u) : 256 + lane;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
       const int base = ok ? cnt[d * W + warp] : 0;
@@ -539,20 +536,15 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
       if (ok) {
         if (lane == __ffs(peers) - 1) cnt[d * W + warp] = base + __popc(peers);
         const int pos = base + __popc(peers & lt);
-        k1[pos] = key;
         s1[pos] = s0[i];
       }
       __syncwarp();
     }
     __syncthreads();
-    unsigned* tk = k0;
-    k0 = k1;
-    k1 = tk;
     unsigned short* ts = s0;
     s0 = s1;
     s1 = ts;
   }
-  keys = k0;
   slots = s0;
 }
 
@@ -567,7 +559,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned* k
 // j > a come from a suffix of that order in ascending j and are written in
 // order, coalesced, as the ballot finds them.
 template <int DIM, bool FILL>
-__global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
+__global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 4 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
                                                                                float ball2, int cap,
                                                                                unsigned char* __restrict__ flag,
                                                                                int* __restrict__ fcells,
@@ -582,9 +574,7 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
   float4* st = smem;           // staged neighbourhood: (x, y, z in the cell's frame, original index)
   float4* stab = st + cap;     // stencil: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
   int* scal = reinterpret_cast<int*>(stab + A.noff);  // [0] staged count, [1..2] index range, [4..] warp sums
-  unsigned* rk0 = reinterpret_cast<unsigned*>(scal + 16);  // FILL: radix keys, slots, counters
-  unsigned* rk1 = rk0 + cap;
-  int* cnt = reinterpret_cast<int*>(rk1 + cap);
+  int* cnt = scal + 16;  // FILL: radix counters and slots
   unsigned short* rs0 = reinterpret_cast<unsigned short*>(cnt + 256 * W);
   unsigned short* rs1 = rs0 + cap;
   stencil_to_smem(A, stab);
@@ -627,10 +617,9 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
     __syncthreads();
     const int S = scal[0];
     if (S <= cap) {
-      unsigned* keys = rk0;
       unsigned short* slots = rs0;
       int kmin = 0;
-      if (FILL) stage_radix<W>(st, S, rk0, rk1, rs0, rs1, cnt, scal, keys, slots, kmin);
+      if (FILL) stage_radix<W>(st, S, rs0, rs1, cnt, scal, slots, kmin);
       if (!FILL) {
         // COUNT: two home particles per warp share each staged load; the
         // distance of each (particle, candidate) is computed as in the fill pass.
@@ -680,7 +669,7 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
             int lo = 0, hi = S;
             while (a0 >= kmin && lo < hi) {
               const int mid = (lo + hi) >> 1;
-              if (keys[mid] > ka) hi = mid;
+              if ((unsigned)(__float_as_int(st[slots[mid]].w) - kmin) > ka) hi = mid;
               else lo = mid + 1;
             }
             f0 = a0 >= kmin ? lo : 0;
@@ -690,7 +679,7 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
             int lo = 0, hi = S;
             while (a1 >= kmin && lo < hi) {
               const int mid = (lo + hi) >> 1;
-              if (keys[mid] > kb) hi = mid;
+              if ((unsigned)(__float_as_int(st[slots[mid]].w) - kmin) > kb) hi = mid;
               else lo = mid + 1;
             }
             f1 = a1 >= kmin ? lo : 0;
@@ -749,9 +738,7 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 3 : 6) k_pairs_cell(c
 
 size_t pairs_cell_smem(int noff, bool fill, int cap) {
   const size_t head = (size_t)(cap + noff) * sizeof(float4) + 16 * sizeof(int);
-  return fill ? head + 2 * (size_t)cap * sizeof(unsigned) + 256 * 8 * sizeof(int) +
-                    2 * (size_t)cap * sizeof(unsigned short)
-              : head;
+  return fill ? head + 256 * 8 * sizeof(int) + 2 * (size_t)cap * sizeof(unsigned short) : head;
 }
 
 template <int DIM, bool FILL>
