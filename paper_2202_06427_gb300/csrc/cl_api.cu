@@ -226,7 +226,7 @@ float pairs_ball2(const clk::Geo& g) {
 }
 
 // Staged entries per cell for the pair list: the particles of the staging ball
-// at the box's mean density, with 30 % to spare, in steps of 256 (1,024 to
+// at the box's mean density, with 30 % to spare, in steps of 128 (1,024 to
 // 3,072). Denser cells overflow and take the per-particle path.
 int pairs_stage_cap(const clk::Geo& g, long long n, float ball2) {
   double vol = 1.0;
@@ -238,7 +238,7 @@ int pairs_stage_cap(const clk::Geo& g, long long n, float ball2) {
   const double r = std::sqrt((double)ball2);
   const double ball = g.dim == 3 ? 4.18879020478639 * r * r * r : 3.14159265358979 * r * r;
   const double est = (vol > 0 ? (double)n / vol : 0.0) * ball * 1.3 + 64.0;
-  int cap = (int)std::ceil(est / 256.0) * 256;
+  int cap = (int)std::ceil(est / 128.0) * 128;
   return std::min(3072, std::max(1024, cap));
 }
 

@@ -463,7 +463,8 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
 // per pass, so equal digits keep their order. Returns the buffer that holds
 // the sorted slots.
 template <int W>
-__device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned short* s0, unsigned short* s1, int* cnt,
+__device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned short* s0, unsigned short* s1,
+                                            unsigned short* cnt,
                                             int* scal, unsigned short*& slots, int& kmin) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -500,7 +501,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
       const bool ok = i < b1;
       const int d = ok ? (int)(((unsigned)(__float_as_int(st[s0[i]].w) - kmin) >> sh) & 255u) : 256 + lane;
       const unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (ok && lane == __ffs(peers) - 1) cnt[d * W + warp] += __popc(peers);
+      if (ok && lane == __ffs(peers) - 1) cnt[d * W + warp] += (unsigned short)__popc(peers);
       __syncwarp();
     }
     __syncthreads();
@@ -520,7 +521,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
       for (int w = 0; w < warp; ++w) off += scal[4 + w];
       for (int e = 0; e < per; ++e) {
         const int v = cnt[threadIdx.x * per + e];
-        cnt[threadIdx.x * per + e] = off;
+        cnt[threadIdx.x * per + e] = (unsigned short)off;
         off += v;
       }
     }
@@ -534,7 +535,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
       const int base = ok ? cnt[d * W + warp] : 0;
       __syncwarp();
       if (ok) {
-        if (lane == __ffs(peers) - 1) cnt[d * W + warp] = base + __popc(peers);
+        if (lane == __ffs(peers) - 1) cnt[d * W + warp] = (unsigned short)(base + __popc(peers));
         const int pos = base + __popc(peers & lt);
         s1[pos] = s0[i];
       }
@@ -559,7 +560,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
 // j > a come from a suffix of that order in ascending j and are written in
 // order, coalesced, as the ballot finds them.
 template <int DIM, bool FILL>
-__global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 4 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
+__global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 5 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
                                                                                float ball2, int cap,
                                                                                unsigned char* __restrict__ flag,
                                                                                int* __restrict__ fcells,
@@ -574,8 +575,8 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 4 : 6) k_pairs_cell(c
   float4* st = smem;           // staged neighbourhood: (x, y, z in the cell's frame, original index)
   float4* stab = st + cap;     // stencil: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
   int* scal = reinterpret_cast<int*>(stab + A.noff);  // [0] staged count, [1..2] index range, [4..] warp sums
-  int* cnt = scal + 16;  // FILL: radix counters and slots
-  unsigned short* rs0 = reinterpret_cast<unsigned short*>(cnt + 256 * W);
+  unsigned short* cnt = reinterpret_cast<unsigned short*>(scal + 16);  // FILL: radix counters and slots
+  unsigned short* rs0 = cnt + 256 * W;
   unsigned short* rs1 = rs0 + cap;
   stencil_to_smem(A, stab);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -738,7 +739,7 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 4 : 6) k_pairs_cell(c
 
 size_t pairs_cell_smem(int noff, bool fill, int cap) {
   const size_t head = (size_t)(cap + noff) * sizeof(float4) + 16 * sizeof(int);
-  return fill ? head + 256 * 8 * sizeof(int) + 2 * (size_t)cap * sizeof(unsigned short) : head;
+  return fill ? head + 256 * 8 * sizeof(unsigned short) + 2 * (size_t)cap * sizeof(unsigned short) : head;
 }
 
 template <int DIM, bool FILL>
