@@ -560,7 +560,7 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
 // j > a come from a suffix of that order in ascending j and are written in
 // order, coalesced, as the ballot finds them.
 template <int DIM, bool FILL>
-__global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 5 : 6) k_pairs_cell(const __grid_constant__ SweepArgs A,
+__global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ SweepArgs A,
                                                                                float ball2, int cap,
                                                                                unsigned char* __restrict__ flag,
                                                                                int* __restrict__ fcells,
@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(FILL ? 256 : 128, FILL ? 5 : 6) k_pairs_cell(c
                                                                                int* __restrict__ pi_out,
                                                                                int* __restrict__ pj_out,
                                                                                float* __restrict__ pd_out) {
-  constexpr int W = FILL ? 8 : 4;
+  constexpr int W = 8;
   extern __shared__ float4 smem[];
   float4* st = smem;           // staged neighbourhood: (x, y, z in the cell's frame, original index)
   float4* stab = st + cap;     // stencil: (s_x, s_y, s_z, dx | dy << 10 | dz << 20)
@@ -757,14 +757,14 @@ static int launch_cell(const SweepArgs& A, float ball2, int cap, unsigned char* 
   }
   const size_t smem = pairs_cell_smem(A.noff, FILL, cap);
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_cell<DIM, FILL>, FILL ? 256 : 128, smem) !=
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pairs_cell<DIM, FILL>, 256, smem) !=
           cudaSuccess ||
       per < 1)
     return CL_ERR_CUDA;
   long long blocks = (long long)sms * per;
   const long long ncells = (long long)A.nx * A.ny * A.nz;
   if (blocks > ncells) blocks = ncells;
-  k_pairs_cell<DIM, FILL><<<(int)blocks, FILL ? 256 : 128, smem, s>>>(A, ball2, cap, flag, fcells, nfcells, count,
+  k_pairs_cell<DIM, FILL><<<(int)blocks, 256, smem, s>>>(A, ball2, cap, flag, fcells, nfcells, count,
                                                                       start, pi, pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
