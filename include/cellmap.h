@@ -128,8 +128,9 @@ int cl_update(cl_list* cl, const double* pos_dev, const cl_box* box, void* strea
  * summed; here per-CTA FP64 partials are summed in a fixed order).
  * Asynchronous except CL_RED_PAIRLIST, which synchronizes `stream` once to
  * learn the pair count and returns CL_ERR_CAPACITY (with *npairs set) when it
- * exceeds result->capacity; call again with more room. params may be NULL
- * except for CL_RED_HIST. */
+ * exceeds result->capacity; call again with more room. The pair count and the
+ * list's offsets are 64-bit: a list may hold more than 2^31 pairs (indices
+ * stay int32, since n < 2^31). params may be NULL except for CL_RED_HIST. */
 int cl_map(const cl_list* cl, cl_reduction red, const cl_params* params, cl_result* result, void* stream);
 
 /* Adjoint of the shifted-force energy (Sec. 3.3, Code 9: the pair sum is

@@ -34,8 +34,8 @@ struct cl_list {
   unsigned long long* u64;
   // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
   int* pl_count;
-  int* pl_start;
-  int* pl_tiles;
+  long long* pl_start;  // 64-bit: a list may pass 2^31 pairs
+  long long* pl_tiles;
   int* pl_meta;
   int* pl_long;  // particles whose segments are sorted by the long-segment pass
   // device copies of the stencils (for sweeps compiled outside the library)
@@ -260,7 +260,8 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
       cudaFree(c->pl_tiles);
       cudaFree(c->pl_meta);
       cudaFree(c->pl_long);
-      c->pl_count = c->pl_start = c->pl_tiles = c->pl_meta = c->pl_long = nullptr;
+      c->pl_count = c->pl_meta = c->pl_long = nullptr;
+      c->pl_start = c->pl_tiles = nullptr;
       return e;
     }
     c->bytes += b;
@@ -272,9 +273,10 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   const int cap = pairs_stage_cap(c->geo, c->n, ball2);
   if ((e = clk::launch_pairs_count(*c->full, dim, ball2, cap, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, s)))
     return e;
-  if ((e = clk::launch_scan(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
-  int total = 0, meta[4] = {0, 0, 0, 0};
-  if (cudaMemcpyAsync(&total, c->pl_start + c->n, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if ((e = clk::launch_scan64(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
+  long long total = 0;
+  int meta[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(&total, c->pl_start + c->n, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(meta, c->pl_meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return CL_ERR_CUDA;
@@ -470,8 +472,8 @@ int check_query(const cl_list* c, const double* posb, long long nb) {
 // Per-call workspace of the two-set queries (allocated and freed here).
 struct QueryWs {
   int* count = nullptr;
-  int* start = nullptr;
-  int* tiles = nullptr;
+  long long* start = nullptr;  // 64-bit offsets of the cross list
+  long long* tiles = nullptr;
   int* meta = nullptr;
   int* err = nullptr;
   int* longs = nullptr;
@@ -534,9 +536,10 @@ int cl_cross_pairlist(const cl_list* cc, const double* posb_dev, long long nb, l
   if ((e = clk::launch_cross(0, *c->full, c->geo, posb_dev, nb, 0, w.count, nullptr, nullptr, nullptr, nullptr,
                              nullptr, nullptr, nullptr, w.err, s)))
     return e;
-  if ((e = clk::launch_scan(w.count, nb, w.tiles, w.start, w.meta, s))) return e;
-  int total = 0, meta[4] = {0, 0, 0, 0};
-  if (cudaMemcpyAsync(&total, w.start + nb, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if ((e = clk::launch_scan64(w.count, nb, w.tiles, w.start, w.meta, s))) return e;
+  long long total = 0;
+  int meta[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(&total, w.start + nb, sizeof(long long), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaMemcpyAsync(meta, w.meta, sizeof(meta), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return CL_ERR_CUDA;
   if ((e = read_err(w.err, s))) return e;

@@ -114,26 +114,28 @@ constexpr int kScanThreads = 256;
 constexpr int kScanPer = 8;
 constexpr int kScanTile = kScanThreads * kScanPer;
 
-__device__ __forceinline__ int warp_incl_scan(int v) {
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, v, off);
+    T t = __shfl_up_sync(0xffffffffu, v, off);
     if (lane >= off) v += t;
   }
   return v;
 }
 
 // Exclusive scan of one value per thread across the block.
-__device__ void block_excl_scan(int v, int* out_excl) {
-  __shared__ int wsum[kScanThreads / 32];
+template <class T>
+__device__ void block_excl_scan(T v, T* out_excl) {
+  __shared__ T wsum[kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = warp_incl_scan(v);
+  T incl = warp_incl_scan(v);
   if (lane == 31) wsum[warp] = incl;
   __syncthreads();
   if (warp == 0) {
-    int w = (lane < kScanThreads / 32) ? wsum[lane] : 0;
-    int wi = warp_incl_scan(w);
+    T w = (lane < kScanThreads / 32) ? wsum[lane] : T(0);
+    T wi = warp_incl_scan(w);
     if (lane < kScanThreads / 32) wsum[lane] = wi - w;
   }
   __syncthreads();
@@ -141,11 +143,15 @@ __device__ void block_excl_scan(int v, int* out_excl) {
   __syncthreads();  // wsum is reused by the next call
 }
 
-// Per tile: sum of counts, non-empty cells, largest count.
+// Per tile: sum of counts, non-empty cells, largest count. T is the offset
+// type: int for cell offsets (at most n < 2^31 particles), long long for the
+// pair list, whose total may pass 2^31.
+template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restrict__ counts, long long ncells,
-                                                             int* __restrict__ tile_sum, int* __restrict__ meta) {
+                                                             T* __restrict__ tile_sum, int* __restrict__ meta) {
   const long long base = (long long)blockIdx.x * kScanTile;
-  int s = 0, ne = 0, mx = 0;
+  T s = 0;
+  int ne = 0, mx = 0;
   for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
     long long c = base + k;
     if (c < ncells) {
@@ -161,13 +167,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restr
     ne += __shfl_down_sync(0xffffffffu, ne, off);
     mx = max(mx, __shfl_down_sync(0xffffffffu, mx, off));
   }
-  __shared__ int sm[3][kScanThreads / 32];
+  __shared__ T ssum[kScanThreads / 32];
+  __shared__ int sm[2][kScanThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) { sm[0][warp] = s; sm[1][warp] = ne; sm[2][warp] = mx; }
+  if (lane == 0) { ssum[warp] = s; sm[0][warp] = ne; sm[1][warp] = mx; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    int S = 0, NE = 0, MX = 0;
-    for (int w = 0; w < kScanThreads / 32; ++w) { S += sm[0][w]; NE += sm[1][w]; MX = max(MX, sm[2][w]); }
+    T S = 0;
+    int NE = 0, MX = 0;
+    for (int w = 0; w < kScanThreads / 32; ++w) { S += ssum[w]; NE += sm[0][w]; MX = max(MX, sm[1][w]); }
     tile_sum[blockIdx.x] = S;
     atomicAdd(&meta[1], NE);
     atomicMax(&meta[2], MX);
@@ -175,17 +183,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restr
 }
 
 // One block: exclusive scan of the tile sums in place; cell_start[ncells] = total.
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int* __restrict__ tile_sum, int ntiles,
-                                                            int* __restrict__ cell_start, long long ncells) {
-  __shared__ int carry;
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(T* __restrict__ tile_sum, int ntiles,
+                                                            T* __restrict__ cell_start, long long ncells) {
+  __shared__ T carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (int base = 0; base < ntiles; base += kScanThreads) {
     const int t = base + threadIdx.x;
-    const int v = (t < ntiles) ? tile_sum[t] : 0;
-    int excl;
+    const T v = (t < ntiles) ? tile_sum[t] : T(0);
+    T excl;
     block_excl_scan(v, &excl);
-    const int c0 = carry;
+    const T c0 = carry;
     if (t < ntiles) tile_sum[t] = c0 + excl;
     __syncthreads();
     if (threadIdx.x == kScanThreads - 1) carry = c0 + excl + v;
@@ -195,20 +204,21 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tiles(int* __restrict__ t
 }
 
 // Per tile: rescan the counts with the tile's offset -> cell_start.
+template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int* __restrict__ counts, long long ncells,
-                                                            const int* __restrict__ tile_off,
-                                                            int* __restrict__ cell_start) {
+                                                            const T* __restrict__ tile_off,
+                                                            T* __restrict__ cell_start) {
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
   int v[kScanPer];
-  int s = 0;
+  T s = 0;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
     v[k] = (base + k < ncells) ? counts[base + k] : 0;
     s += v[k];
   }
-  int excl;
+  T excl;
   block_excl_scan(s, &excl);
-  int run = tile_off[blockIdx.x] + excl;
+  T run = tile_off[blockIdx.x] + excl;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
     if (base + k < ncells) cell_start[base + k] = run;
@@ -272,9 +282,9 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
       else k_bin<2, false><<<blocks, 256, 0, s>>>(a);
     }
   }
-  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.meta);
-  k_scan_tiles<<<1, kScanThreads, 0, s>>>(b.tile_sum, ntiles, b.cell_start, nc);
-  k_scan_final<<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
+  k_scan_reduce<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.meta);
+  k_scan_tiles<int><<<1, kScanThreads, 0, s>>>(b.tile_sum, ntiles, b.cell_start, nc);
+  k_scan_final<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
   if (b.n > 0)
     k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.packed, b.slot, b.xl, b.cell_start, b.xs, b.cellc);
   if (b.n > 0 && b.xy2 && b.zz2) k_pack_pairs<<<blocks, 256, 0, s>>>(b.n, b.xs, b.xy2, b.zz2);
@@ -285,15 +295,16 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
 
 namespace clk {
 
-// Exclusive scan of n int counts into start[n + 1] (start[n] = total), with
-// the same three kernels as the cell offsets; meta receives the number of
-// non-zero counts and the largest one.
-int launch_scan(const int* counts, long long n, int* tile_sum, int* start, int* meta, cudaStream_t s) {
+// Exclusive scan of n int counts into 64-bit start[n + 1] (start[n] = total),
+// with the same three kernels as the cell offsets; meta receives the number of
+// non-zero counts and the largest one. The pair list's offsets and total are
+// 64-bit: a list may hold more than 2^31 pairs.
+int launch_scan64(const int* counts, long long n, long long* tile_sum, long long* start, int* meta, cudaStream_t s) {
   const int ntiles = scan_tiles_for(n);
   if (cudaMemsetAsync(meta + 1, 0, sizeof(int) * 2, s) != cudaSuccess) return CL_ERR_CUDA;
-  k_scan_reduce<<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, meta);
-  k_scan_tiles<<<1, kScanThreads, 0, s>>>(tile_sum, ntiles, start, n);
-  k_scan_final<<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, start);
+  k_scan_reduce<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, meta);
+  k_scan_tiles<long long><<<1, kScanThreads, 0, s>>>(tile_sum, ntiles, start, n);
+  k_scan_final<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, start);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_cross_count(const __grid_constant__ Swe
 }
 
 __global__ void __launch_bounds__(256) k_cross_fill(const __grid_constant__ SweepArgs A,
-                                                    const __grid_constant__ QueryArgs Q, const int* __restrict__ start,
+                                                    const __grid_constant__ QueryArgs Q, const long long* __restrict__ start,
                                                     int* __restrict__ pa, int* __restrict__ pb,
                                                     float* __restrict__ pd) {
   const long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) k_cross_fill(const __grid_constant__ Swee
   int cx, cy, cz;
   float px, py, pz;
   if (!bin_query(A, Q, b, cx, cy, cz, px, py, pz)) return;
-  int pos = start[b];
+  long long pos = start[b];
   query_sweep(A, cx, cy, cz, px, py, pz, [&](int a, float d2) {
     pa[pos] = a;
     pb[pos] = (int)b;
@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(1024) k_topk_merge(const int* __restrict__ la,
 }  // namespace
 
 int launch_cross(int what, const SweepArgs& A, const Geo& g, const double* posb, long long nb, int k, int* count,
-                 unsigned long long* total, const int* start, int* pa, int* pb, float* pd, int* knn_a, float* knn_d,
+                 unsigned long long* total, const long long* start, int* pa, int* pb, float* pd, int* knn_a, float* knn_d,
                  int* err, cudaStream_t s) {
   QueryArgs Q;
   Q.pos = posb;

@@ -121,7 +121,7 @@ struct BuildBufs {
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
-int launch_scan(const int* counts, long long n, int* tile_sum, int* start, int* meta, cudaStream_t s);
+int launch_scan64(const int* counts, long long n, long long* tile_sum, long long* start, int* meta, cudaStream_t s);
 
 // Sweeps and reductions (cl_sweep.cu).
 int sweep_partials_needed(int n);
@@ -172,13 +172,14 @@ int launch_hood(const SweepArgs& A, const HoodArgs& H, int* work, int mode, cons
 // total, 1 fills the pairs of each query's segment (start), 2 the per-query k
 // nearest. err: device error latch.
 int launch_cross(int what, const SweepArgs& A, const Geo& g, const double* posb, long long nb, int k, int* count,
-                 unsigned long long* total, const int* start, int* pa, int* pb, float* pd, int* knn_a, float* knn_d,
+                 unsigned long long* total, const long long* start, int* pa, int* pb, float* pd, int* knn_a, float* knn_d,
                  int* err, cudaStream_t s);
 int launch_topk_merge(const int* la, const float* ld, long long nb, int k, int* oa, int* ob, float* od, int* found,
                       cudaStream_t s);
 
-// Neighbour list (cl_pairs.cu). count[n], start[n+1] (scan of count), tiles,
-// meta: workspace; outputs pair_i/j/d of capacity entries.
+// Neighbour list (cl_pairs.cu). count[n] (int: one particle's pairs), start[n+1]
+// (64-bit scan of count: the list may pass 2^31 pairs), tiles, meta:
+// workspace; outputs pair_i/j/d of capacity entries.
 constexpr int kMaxSegment = 1024;  // segments up to this length are sorted by one warp in shared memory
 // Count pass of the pair list: per-cell staged sweep, then the per-particle
 // sweep for the cells it flags (flag: ncells bytes; fcells: ncells ints, the
@@ -188,12 +189,12 @@ int launch_pairs_count(const SweepArgs& A, int dim, float ball2, int cap, unsign
                        int* nfcells, int* count, cudaStream_t s);
 // Sorts each segment [start[a], start[a] + count[a]) of pj (carrying pd) by pj;
 // longs (n ints) and nlong (1 int) are workspace.
-int launch_pairs_sort(int n, const int* count, const int* start, int* pj, float* pd, int* longs, int* nlong,
+int launch_pairs_sort(int n, const int* count, const long long* start, int* pj, float* pd, int* longs, int* nlong,
                       cudaStream_t s);
 // Fill pass: the same two sweeps, each segment sorted by j and written.
 // longs (n ints) and nlong (1 int): workspace for segments longer than kMaxSegment.
 int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, int cap, const unsigned char* flag, const int* fcells,
-                      const int* nfcells, const int* count, const int* start, int* pi, int* pj, float* pd, int* longs,
+                      const int* nfcells, const int* count, const long long* start, int* pi, int* pj, float* pd, int* longs,
                       int* nlong, cudaStream_t s);
 
 }  // namespace clk

@@ -71,7 +71,7 @@ constexpr int kSortWarps = 4;
 // Longer segments are appended to longs[] (counter *nlong) for
 // k_pairs_sort_long.
 __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int* __restrict__ count,
-                                                               const int* __restrict__ start, int* __restrict__ pj,
+                                                               const long long* __restrict__ start, int* __restrict__ pj,
                                                                float* __restrict__ pd, int* __restrict__ longs,
                                                                int* __restrict__ nlong) {
   __shared__ int sk[kSortWarps][kMaxSegment];
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int
       if (lane == 0) longs[atomicAdd(nlong, 1)] = a;
       continue;
     }
-    const int base = start[a];
+    const long long base = start[a];
     int P = 32;
     while (P < L) P <<= 1;
     for (int k = lane; k < P; k += 32) {
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(32 * kSortWarps) k_pairs_sort(int n, const int
 __global__ void __launch_bounds__(1024) k_pairs_sort_long(const int* __restrict__ longs,
                                                          const int* __restrict__ nlong,
                                                          const int* __restrict__ count,
-                                                         const int* __restrict__ start, int* __restrict__ pj,
+                                                         const long long* __restrict__ start, int* __restrict__ pj,
                                                          float* __restrict__ pd) {
   const int m = *nlong;
   for (int q = blockIdx.x; q < m; q += gridDim.x) {
@@ -352,7 +352,7 @@ __device__ __forceinline__ void stencil_to_smem(const SweepArgs& A, float4* stab
 }
 
 // Sorts the warp's segment of nw kept pairs by j and writes it at base.
-__device__ __forceinline__ void segment_out(int* K, float* V, int nw, int a, int base, int lane, int* pi_out,
+__device__ __forceinline__ void segment_out(int* K, float* V, int nw, int a, long long base, int lane, int* pi_out,
                                             int* pj_out, float* pd_out) {
   if (nw <= 1) {
   } else if (nw <= 32) {
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
                                                                           const int* __restrict__ cells,
                                                                           const int* __restrict__ ncells,
                                                                           const int* __restrict__ count,
-                                                                          const int* __restrict__ start,
+                                                                          const long long* __restrict__ start,
                                                                           int* __restrict__ pi_out,
                                                                           int* __restrict__ pj_out,
                                                                           float* __restrict__ pd_out,
@@ -408,7 +408,8 @@ __global__ void __launch_bounds__(32 * kFillWarps, 6) k_pairs_fill_sorted(const 
       const int a = __float_as_int(pi.w);
       const unsigned cc = A.cellc[p];
       const int cx = (int)(cc & 1023u), cy = (int)((cc >> 10) & 1023u), cz = (int)(cc >> 20);
-      const int cnt_a = __ldg(count + a), base = __ldg(start + a);
+      const int cnt_a = __ldg(count + a);
+      const long long base = __ldg(start + a);
       const bool big = cnt_a > kMaxSegment;  // written unsorted, sorted by k_pairs_sort_long
       int L = 0;
       for (int k0 = 0; k0 < A.noff; k0 += 32) {
@@ -566,7 +567,7 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
                                                                                int* __restrict__ fcells,
                                                                                int* __restrict__ nfcells,
                                                                                int* __restrict__ count,
-                                                                               const int* __restrict__ start,
+                                                                               const long long* __restrict__ start,
                                                                                int* __restrict__ pi_out,
                                                                                int* __restrict__ pj_out,
                                                                                float* __restrict__ pd_out) {
@@ -685,8 +686,8 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
             }
             f1 = a1 >= kmin ? lo : 0;
           }
-          const int c0 = __ldg(count + a0), b0 = __ldg(start + a0);
-          const int c1 = two ? __ldg(count + a1) : 0, b1 = two ? __ldg(start + a1) : 0;
+          const int c0 = __ldg(count + a0), c1 = two ? __ldg(count + a1) : 0;
+          const long long b0 = __ldg(start + a0), b1 = two ? __ldg(start + a1) : 0;
           int L0 = 0, L1 = 0;
 #pragma unroll 2
           for (int t0 = min(f0, f1); t0 < S; t0 += 32) {
@@ -744,7 +745,7 @@ size_t pairs_cell_smem(int noff, bool fill, int cap) {
 
 template <int DIM, bool FILL>
 static int launch_cell(const SweepArgs& A, float ball2, int cap, unsigned char* flag, int* fcells, int* nfcells,
-                       int* count, const int* start, int* pi, int* pj, float* pd, cudaStream_t s) {
+                       int* count, const long long* start, int* pi, int* pj, float* pd, cudaStream_t s) {
   static DevCache ready;  // shared-memory limit raised on this device
   if (cap < 32 || cap > kStageMax) return CL_ERR_INVALID_ARG;
   int dev = 0, sms = 0, per = 0;
@@ -783,14 +784,14 @@ int launch_pairs_count(const SweepArgs& A, int dim, float ball2, int cap, unsign
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
-static int launch_sort_long(const int* longs, const int* nlong, const int* count, const int* start, int* pj,
+static int launch_sort_long(const int* longs, const int* nlong, const int* count, const long long* start, int* pj,
                             float* pd, cudaStream_t s) {
   k_pairs_sort_long<<<152, 1024, 0, s>>>(longs, nlong, count, start, pj, pd);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
 int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, int cap, const unsigned char* flag, const int* fcells,
-                      const int* nfcells, const int* count, const int* start, int* pi, int* pj, float* pd, int* longs,
+                      const int* nfcells, const int* count, const long long* start, int* pi, int* pj, float* pd, int* longs,
                       int* nlong, cudaStream_t s) {
   if (A.n <= 0) return CL_OK;
   unsigned char* fl = const_cast<unsigned char*>(flag);  // only read by the fill pass
@@ -810,7 +811,7 @@ int launch_pairs_fill(const SweepArgs& A, int dim, float ball2, int cap, const u
   return launch_sort_long(longs, nlong, count, start, pj, pd, s);
 }
 
-int launch_pairs_sort(int n, const int* count, const int* start, int* pj, float* pd, int* longs, int* nlong,
+int launch_pairs_sort(int n, const int* count, const long long* start, int* pj, float* pd, int* longs, int* nlong,
                       cudaStream_t s) {
   if (n <= 0) return CL_OK;
   if (cudaMemsetAsync(nlong, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;

@@ -222,6 +222,11 @@ def test_all_in_one_cell_and_multi_image(cuda_ok):
     cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, 1)
     assert P.cl_query(cl, "ncells") == 1
     check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    # more than 2^31 pairs: the pair list's offsets and total are 64-bit, so a
+    # call with a small buffer reports CL_ERR_CAPACITY and the exact total
+    total = pairlist_total(P, cl)
+    assert total > 2 ** 31
+    check_count(total, ref)
     check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
     efv = P.cl_map(cl, "energy_forces_virial")
     check_forces(efv["forces"].cpu().numpy(), ref["forces"])
@@ -270,6 +275,27 @@ def test_update_matches_fresh_build(cuda_ok):
     check_count(int(P.cl_map(cl, "count")["count"].item()), ref3)
 
 
+def pairlist_total(P, cl, capacity=16):
+    """cl_map(CL_RED_PAIRLIST) through the C ABI with a buffer of `capacity`
+    pairs: returns the total the call reports (CL_ERR_CAPACITY when it does
+    not fit, CL_OK otherwise)."""
+    import ctypes
+    from paper_2202_06427_gb300 import _lib as L
+    pi = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    pj = torch.empty(capacity, dtype=torch.int32, device="cuda")
+    pd = torch.empty(capacity, dtype=torch.float32, device="cuda")
+    npairs = ctypes.c_longlong(-1)
+    res = L.cl_result()
+    res.pair_i, res.pair_j, res.pair_d = pi.data_ptr(), pj.data_ptr(), pd.data_ptr()
+    res.capacity = capacity
+    res.npairs = ctypes.pointer(npairs)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    code = L.lib().cl_map(cl.handle, L.CL_RED_PAIRLIST, None, ctypes.byref(res), stream)
+    assert code in (L.CL_OK, L.CL_ERR_CAPACITY), code
+    assert (code == L.CL_ERR_CAPACITY) == (npairs.value > capacity)
+    return int(npairs.value)
+
+
 @pytest.mark.slow
 def test_workload_clustered_16m(cuda_ok):
     """3D clustered, 16M particles in a cubic box of side 600 (2,000 Gaussian
@@ -288,6 +314,11 @@ def test_workload_clustered_16m(cuda_ok):
     cl = P.cl_build(pos, h, rc, 1)
     assert P.cl_query(cl, "max_occupancy") > 10 * n / P.cl_query(cl, "ncells")  # strongly inhomogeneous
     check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    # more than 2^31 pairs: the pair list's offsets and total are 64-bit, so a
+    # call with a small buffer reports CL_ERR_CAPACITY and the exact total
+    total = pairlist_total(P, cl)
+    assert total > 2 ** 31
+    check_count(total, ref)
     check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
     efv = P.cl_map(cl, "energy_forces_virial")
     check_energy(efv["energy"].item(), ref["energy"])
