@@ -69,7 +69,8 @@ int cl_serve_create(long long arena_bytes, int max_inflight, int device, cl_serv
 int cl_serve_submit(cl_server* s, const cl_request* req, long long* ticket);
 
 /* Status of a ticket: 1 = pending, 0 = done, negative = failed with that
- * error code. Non-blocking. */
+ * error code (CL_ERR_CUDA when a copy or kernel launch of its batch failed).
+ * Non-blocking. */
 int cl_serve_poll(cl_server* s, long long ticket);
 
 /* Wait up to timeout_s seconds for a ticket; returns its status (1 on timeout). */
@@ -85,6 +86,14 @@ int cl_serve_stats(cl_server* s, long long* stats);
 
 /* The server's steady clock now, in seconds (same origin as cl_serve_times). */
 double cl_serve_clock(cl_server* s);
+
+/* Forget a finished ticket. A ticket's status and timestamps (under 1 KB
+ * of host memory; its CUDA event is freed when it completes) are kept until
+ * this call or cl_serve_free, so a long-running server should release each
+ * ticket once it has read them. Returns CL_OK, 1 when the ticket is still
+ * pending (nothing is released), or CL_ERR_INVALID_ARG for an unknown or
+ * already released ticket, which later calls also report. */
+int cl_serve_release(cl_server* s, long long ticket);
 
 /* Stop the thread after the queued work completes and release everything. */
 void cl_serve_free(cl_server* s);

@@ -243,6 +243,7 @@ struct Batch {
   int* h_latch = nullptr;          // pinned, one per request of the batch
   cudaEvent_t done = nullptr;
   bool busy = false;
+  int err = CL_OK;                 // CL_ERR_CUDA when a copy or launch of the batch failed
 };
 
 }  // namespace
@@ -297,6 +298,13 @@ size_t request_bytes(const Req& q) {
 }  // namespace
 
 void cl_server::finish(Req* q, int status) {
+  // the request's work is over: its event and stencil copy are no longer
+  // needed, only the status and timestamps stay until the ticket is released
+  if (q->built) {
+    cudaEventDestroy(q->built);
+    q->built = nullptr;
+  }
+  std::vector<clk::Off>().swap(q->off);
   {
     std::lock_guard<std::mutex> g(mu);
     q->status = status;
@@ -377,6 +385,12 @@ bool cl_server::admit_one(Req* q) {
 void cl_server::launch_batch(Batch& b) {
   b.reqs.swap(ready);
   ready.clear();
+  b.err = CL_OK;
+  // every enqueue is checked; after the first failure nothing more is
+  // launched and complete() fails the batch's requests with CL_ERR_CUDA
+  auto ok = [&b](cudaError_t r) {
+    if (r != cudaSuccess && !b.err) b.err = CL_ERR_CUDA;
+  };
   int items = 0, maxbins = 0;
   const double tl = now();
   for (size_t k = 0; k < b.reqs.size(); ++k) {
@@ -411,33 +425,45 @@ void cl_server::launch_batch(Batch& b) {
     D.virial = q->d_virial;
     items += q->nitems;
     if (q->r.task == CL_TASK_HIST) maxbins = std::max(maxbins, q->r.nbins);
-    cudaStreamWaitEvent(main, q->built, 0);
+    ok(cudaStreamWaitEvent(main, q->built, 0));
   }
   const int nreq = (int)b.reqs.size();
-  cudaMemcpyAsync(b.d_desc, b.h_desc, sizeof(clk::ReqDesc) * nreq, cudaMemcpyHostToDevice, main);
-  cudaMemsetAsync(b.d_counter, 0, sizeof(int), main);
-  if (items > 0) {
+  ok(cudaMemcpyAsync(b.d_desc, b.h_desc, sizeof(clk::ReqDesc) * nreq, cudaMemcpyHostToDevice, main));
+  ok(cudaMemsetAsync(b.d_counter, 0, sizeof(int), main));
+  if (items > 0 && !b.err) {
     int grid = std::min(items, sm_count * ctas_per_sm);
     clk::k_serve_sweep<<<grid, clk::kServeThreads, sizeof(unsigned) * maxbins, main>>>(b.d_desc, nreq, items,
                                                                                        b.d_counter);
+    ok(cudaGetLastError());
   }
-  clk::k_serve_finalize<<<nreq, 256, 0, main>>>(b.d_desc);
-  for (int k = 0; k < nreq; ++k) {
+  if (!b.err) {
+    clk::k_serve_finalize<<<nreq, 256, 0, main>>>(b.d_desc);
+    ok(cudaGetLastError());
+  }
+  for (int k = 0; k < nreq && !b.err; ++k) {
     Req* q = b.reqs[k];
     const size_t n = (size_t)q->r.n, d = (size_t)q->geo.dim;
     if (q->r.task != CL_TASK_HIST && q->r.energy_host)
-      cudaMemcpyAsync(q->r.energy_host, q->d_energy, 8, cudaMemcpyDeviceToHost, main);
+      ok(cudaMemcpyAsync(q->r.energy_host, q->d_energy, 8, cudaMemcpyDeviceToHost, main));
     if (q->r.task == CL_TASK_FORCES) {
       if (q->r.forces_host && n)
-        cudaMemcpyAsync(q->r.forces_host, q->d_forces, n * d * 4, cudaMemcpyDeviceToHost, main);
-      if (q->r.virial_host) cudaMemcpyAsync(q->r.virial_host, q->d_virial, d * d * 8, cudaMemcpyDeviceToHost, main);
+        ok(cudaMemcpyAsync(q->r.forces_host, q->d_forces, n * d * 4, cudaMemcpyDeviceToHost, main));
+      if (q->r.virial_host)
+        ok(cudaMemcpyAsync(q->r.virial_host, q->d_virial, d * d * 8, cudaMemcpyDeviceToHost, main));
     }
     if (q->r.task == CL_TASK_HIST && q->r.hist_host)
-      cudaMemcpyAsync(q->r.hist_host, q->d_hist, (size_t)q->r.nbins * 8, cudaMemcpyDeviceToHost, main);
-    cudaMemcpyAsync(b.h_latch + k, q->bufs.meta, sizeof(int), cudaMemcpyDeviceToHost, main);
+      ok(cudaMemcpyAsync(q->r.hist_host, q->d_hist, (size_t)q->r.nbins * 8, cudaMemcpyDeviceToHost, main));
+    ok(cudaMemcpyAsync(b.h_latch + k, q->bufs.meta, sizeof(int), cudaMemcpyDeviceToHost, main));
   }
-  cudaEventRecord(b.done, main);
-  b.busy = true;
+  if (cudaEventRecord(b.done, main) != cudaSuccess) {
+    // no event to poll: wait for what was queued, then finish the batch now
+    b.err = CL_ERR_CUDA;
+    cudaStreamSynchronize(main);
+    b.busy = true;
+    complete(b);
+  } else {
+    b.busy = true;
+  }
   std::lock_guard<std::mutex> g(mu);
   stats[0]++;
   stats[3] = std::max<long long>(stats[3], nreq);
@@ -448,10 +474,11 @@ void cl_server::complete(Batch& b) {
     Req* q = b.reqs[k];
     arena.release(q->arena_off, q->arena_bytes);
     resident--;
-    finish(q, (b.h_latch[k] & clk::kErrNonFinite) ? CL_ERR_NONFINITE : 0);
+    finish(q, b.err ? b.err : (b.h_latch[k] & clk::kErrNonFinite) ? CL_ERR_NONFINITE : 0);
   }
   b.reqs.clear();
   b.busy = false;
+  b.err = CL_OK;
 }
 
 void cl_server::loop() {
@@ -612,6 +639,21 @@ int cl_serve_stats(cl_server* s, long long* out) {
 }
 
 double cl_serve_clock(cl_server* s) { return s ? s->now() : 0.0; }
+
+int cl_serve_release(cl_server* s, long long ticket) {
+  if (!s) return CL_ERR_INVALID_ARG;
+  Req* q = nullptr;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return CL_ERR_INVALID_ARG;
+    if (it->second->status == 1) return 1;  // still pending: kept
+    q = it->second;
+    s->all.erase(it);
+  }
+  delete q;  // finish() already destroyed its event
+  return CL_OK;
+}
 
 void cl_serve_free(cl_server* s) {
   if (!s) return;

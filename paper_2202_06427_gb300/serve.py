@@ -28,12 +28,13 @@ def _declare(lib):
     lib.cl_serve_wait.argtypes = [P, ll, dbl]
     lib.cl_serve_times.argtypes = [P, ll, P]
     lib.cl_serve_stats.argtypes = [P, P]
+    lib.cl_serve_release.argtypes = [P, ll]
     lib.cl_serve_clock.argtypes = [P]
     lib.cl_serve_clock.restype = dbl
     lib.cl_serve_free.argtypes = [P]
     lib.cl_serve_free.restype = None
     for f in ("cl_serve_create", "cl_serve_submit", "cl_serve_poll", "cl_serve_wait", "cl_serve_times",
-              "cl_serve_stats"):
+              "cl_serve_stats", "cl_serve_release"):
         getattr(lib, f).restype = i32
     lib._serve_declared = True
     return lib
@@ -91,6 +92,13 @@ class Server:
         t = (ctypes.c_double * 4)()
         L.check(self.lib.cl_serve_times(self.h, ticket, t), "cl_serve_times")
         return list(t)
+
+    def release(self, ticket):
+        """Forget a finished ticket (0); 1 when it is still pending."""
+        code = int(self.lib.cl_serve_release(self.h, ticket))
+        if code < 0:
+            L.check(code, "cl_serve_release")
+        return code
 
     def stats(self):
         s = (ctypes.c_longlong * 6)()

@@ -114,6 +114,13 @@ def test_failures_stay_with_their_request(cuda_ok):
             assert srv.wait(t, 60) == 0
         st = srv.stats()
         assert st["failed"] == 2 and st["arena_used"] == 0
+        # finished tickets are released; a released ticket is unknown afterwards
+        for t in tickets + [t_nan, t_big, t_empty]:
+            assert srv.release(t) == 0
+        assert srv.poll(t_nan) == -1
+        with pytest.raises(CellMapError) as e:
+            srv.release(t_nan)
+        assert e.value.code == -1
     finally:
         srv.close()
     for spec, r in good:
@@ -123,3 +130,49 @@ def test_failures_stay_with_their_request(cuda_ok):
             check_hist(r.hist.numpy(), ref)
         else:
             check_energy(r.energy.item(), ref["energy"])
+
+
+def _oracle_request(spec):
+    """Oracle result of one request of the stream, its positions drawn again
+    from the request's own seed (spawned worker)."""
+    import oracle as O
+    import synth as Sy
+    x = Sy.request_positions(spec)
+    nb = spec["nbins"] if spec["task"] == "hist" else 0
+    ref = O.pair_map(x, spec["h"], spec["rc"], band=BAND, nbins=nb, forces=spec["task"] == "forces")
+    keep = ("energy", "virial", "forces", "hist_core", "hist_maybe")
+    return {k: ref[k] for k in keep if k in ref}
+
+
+@pytest.mark.slow
+def test_whole_served_stream_matches_oracle(cuda_ok):
+    """All 512 requests of the served stream (2D and 3D, orthorhombic and
+    triclinic, N from 1,000 to 200,000, energy / forces / 100-bin histogram),
+    served together with continuous batching, each result checked against the
+    oracle (a spawn pool runs one request per task)."""
+    import multiprocessing as mp
+    S = _S()
+    specs = synth.serve_stream()
+    reqs = [S.Request(synth.request_positions(sp), sp["h"], sp["rc"], sp["task"], lcell=2, nbins=sp["nbins"])
+            for sp in specs]
+    srv = S.Server(arena_bytes=4 << 30, max_inflight=256)
+    try:
+        for r in reqs:
+            srv.submit(r)
+        for r in reqs:
+            assert srv.wait(r.ticket, 300.0) == 0
+        assert srv.stats()["largest_batch"] > 1
+    finally:
+        srv.close()
+    order = sorted(range(len(specs)), key=lambda k: -specs[k]["n"])  # largest first
+    with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
+        refs = dict(zip(order, pool.map(_oracle_request, [specs[k] for k in order], chunksize=1)))
+    for k, (spec, r) in enumerate(zip(specs, reqs)):
+        ref = refs[k]
+        if spec["task"] == "hist":
+            check_hist(r.hist.numpy(), ref)
+        else:
+            check_energy(r.energy.item(), ref["energy"])
+        if spec["task"] == "forces":
+            check_forces(r.forces.numpy(), ref["forces"])
+            check_matrix(r.virial.numpy(), ref["virial"], TOL_W)
