@@ -265,10 +265,12 @@ int cl_status(cl_list* cl, void* stream);
  * library). For applications that route all device memory through their own
  * pool or framework allocator and may not call cudaMalloc/cudaFree, and for
  * latency-critical loops that cannot afford them: cl_build allocates, this
- * call does not. It bins the particles and runs the energy sweep exactly as
- * cl_build + cl_map(CL_RED_SF_ENERGY) would, with every intermediate buffer in
- * one fixed device array inside the library (3.44 MB, held by every GPU
- * that loads the library until the process exits).
+ * call does not. It computes the same shifted-force energy as cl_build +
+ * cl_map(CL_RED_SF_ENERGY), equal to it within the energy tolerance (relative
+ * 1e-6; it runs a different sweep kernel, one thread per particle over the
+ * unpruned half stencil, so the summation order differs), with every
+ * intermediate buffer in one fixed device array inside the library (3.44 MB,
+ * held by every GPU that loads the library until the process exits).
  * pos_dev: (n, dim) FP64 device positions; energy_dev: 1 FP64 device value,
  * overwritten. Limits: n <= CL_NOALLOC_MAX_N and at most
  * CL_NOALLOC_MAX_CELLS cells in the grid the box and lcell give; larger

@@ -2,8 +2,10 @@
 memory (applications whose framework or pool allocator owns all device memory
 and forbids raw cudaMalloc/cudaFree, latency-critical loops that cannot pay
 for an allocation): its energy must equal the regular path, cl_build +
-cl_map(CL_RED_SF_ENERGY), within the energy tolerance of the parity tests, on
-consecutive calls that reuse its fixed device workspace.
+cl_map(CL_RED_SF_ENERGY), and the FP64 oracle within the energy tolerance of
+the parity tests, on consecutive calls that reuse its fixed device workspace,
+up to the largest input it accepts (65,536 particles on a grid of 65,536
+cells).
 
 Collected last on purpose (file name), so a failure here leaves every other
 test already run."""
@@ -13,8 +15,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
-from parity_util import TOL_E
+from parity_util import BAND, TOL_E, check_energy
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +54,26 @@ def test_noalloc_energy_matches_regular_path_on_consecutive_calls(cuda_ok):
         got = out.item()
         want = _regular(x, h, rc, lcell)
         assert abs(got - want) <= TOL_E * abs(want), (k, got, want)
+        check_energy(got, oracle.pair_map(x_np, h, rc, band=BAND, forces=False)["energy"])
+
+
+def test_noalloc_energy_at_its_largest_input(cuda_ok):
+    """n = CL_NOALLOC_MAX_N particles on a 64 x 32 x 32 grid (= CL_NOALLOC_MAX_CELLS
+    cells: box 48.01 x 24.01 x 24.01, rc 3, four cells per cutoff length), two
+    calls in a row, against the oracle and the regular path."""
+    h = np.diag([48.01, 24.01, 24.01])
+    x_np = synth.jittered_fractional(h, 41, 65_536, 0.4, 73)
+    rc, lcell = 3.0, 4
+    import paper_2202_06427_gb300 as P
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
+    assert P.cl_query(P.cl_build(x, h, rc, lcell), "ncells") == 65_536
+    ref = oracle.pair_map(x_np, h, rc, band=BAND, forces=False)["energy"]
+    want = _regular(x, h, rc, lcell)
+    for _ in range(2):
+        out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        assert _noalloc(x, h, rc, lcell, out) == 0
+        check_energy(out.item(), ref)
+        assert abs(out.item() - want) <= TOL_E * abs(want)
 
 
 def test_noalloc_rejects_inputs_beyond_its_workspace(cuda_ok):
