@@ -44,16 +44,31 @@ LCELL = 2
 # clustered set, where larger cells keep fewer particles in sparse cells and
 # fewer cells over the staging limits (measured: fused sweep 37 ms at 1, 57 ms at 2)
 LCELL_BY_WORKLOAD = {"w1_lattice_1m": 2, "w2_triclinic_1m": 2, "w4_clustered_16m": 1}
-# FP32 arithmetic per candidate pair and per ordered pair-image within the cutoff
-# (FMA = 2 FLOP, 1/r = 1) of the fused energy-and-gradient sweep:
-FLOP_PER_CANDIDATE = 8      # 3 sub + 1 mul + 2 fma for |x_j' - x_i|^2
-FLOP_PER_HIT_FUSED = 16     # 1/r (1); fsn = y (y^2 - 1/rc^2) (3); force 3 fma (6); r = d2 y (1),
-                            # t = 1 - r/rc (2), t^2 (1), e += t^2 y (2)
-# DRAM bytes per launch of the fused sweep (k_hood<3>, 1M lattice, lcell 2), from
-# ncu --set full: dram__bytes_read.sum + dram__bytes_write.sum = 40.71 MB + 1.21 MB.
-SWEEP_DRAM_BYTES = 41.93e6
-SM_COUNT_GB300 = 152
+# Algorithmic FP32 work of the sweep (FMA = 2 FLOP, 1/r = 1), counted on the
+# method's own work, not on what a kernel happens to evaluate:
+#   per candidate pair of the half-shell cell stencil (each unordered pair-image
+#   tested once): 3 sub + 1 mul + 2 fma for |x_j + S_o - x_i|^2 = 8 FLOP;
+#   per pair-image within the cutoff, shifted-force energy + forces + virial:
+#   1/r, u, u'/r, 3 force FMAs for i and 3 for j, 6 virial FMAs = 26 FLOP.
+FLOP_PER_CANDIDATE = 8
+FLOP_PER_PAIR = 26
+# What the neighbourhood sweep itself evaluates (full shell: every pair from both
+# ends), reported beside the algorithmic figure: 8 FLOP per staged candidate and
+# 16 per ordered pair-image (1/r, fsn, 3 force FMAs, energy term).
+FLOP_PER_HIT_FUSED = 16
+# Algorithmic bytes of binning per particle: FP64 position read (24 B), FP32
+# cell-centred coordinate + index written (16 B), cell-sorted position of the
+# original index (4 B); the per-cell counts and offsets add 8 B per cell.
+BIN_BYTES_PER_PARTICLE = 44
+BIN_BYTES_PER_CELL = 8
+# DRAM bytes per launch of the dominant kernel from one ncu capture of its
+# current version (dram__bytes_read.sum + dram__bytes_write.sum), or None when
+# the kernel has changed since the counters were taken.
+SWEEP_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
+# kernels of one headline step: bin, 3 scan, scatter, pair pack; cell list,
+# neighbourhood sweep, per-particle companion, dense-cell sweep, 2 reduce; 2 scale
+STEP_LAUNCHES = 14
 
 
 def parse():
@@ -65,6 +80,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--no-extra", action="store_true", help="skip the CPU baseline, precision and other workloads")
     p.add_argument("--workload", choices=["w1_lattice_1m", "w4_clustered_16m", "w2_triclinic_1m"],
                    default=WORKLOAD)
     return p.parse_args()
@@ -161,16 +177,80 @@ def gpu_id(dev):
 
 def load_workload(name):
     import synth
-    if name == "w2_triclinic_1m":
-        return synth.w2_triclinic()
-    return synth.w1_lattice() if name == "w1_lattice_1m" else synth.w4_clustered()
+    make = {"w0_small_10k": synth.w0_small, "w1_lattice_1m": synth.w1_lattice,
+            "w2_triclinic_1m": synth.w2_triclinic, "w4_clustered_16m": synth.w4_clustered}
+    return make[name]()
 
 
-def cpu_baseline(w, budget_s=15.0):
-    """The FP64 oracle as it stands, single-threaded on the host, on a bounded
-    sample: pairs whose smaller index is below k (energy, forces, virial)."""
+def _oracle_part(job):
+    """One worker of the host-core pool: the oracle, as it stands, on the pairs
+    whose smaller index lies in [lo, hi) (positions from a memory-mapped file)."""
+    import oracle
+    if job is None:  # warm-up: the import alone
+        return None
+    path, h, rc, nbins, forces, lo, hi = job
+    x = np.load(path, mmap_mode="r")
+    t0 = time.perf_counter()
+    r = oracle.pair_map(x, h, rc, nbins=nbins, forces=forces, i_range=(lo, hi))
+    r["seconds"] = time.perf_counter() - t0
+    return r
+
+
+class OraclePool:
+    """The single-threaded FP64 oracle run on all host cores: one spawned
+    process per core, each on a range of the smaller pair index; partial sums
+    are added in a fixed order. Started with spawn, so that it is safe after
+    the first CUDA call."""
+
+    def __init__(self, x, nproc=None):
+        import multiprocessing as mp
+        import tempfile
+        self.nproc = nproc or os.cpu_count() or 1
+        self.tmp = tempfile.TemporaryDirectory()
+        self.path = os.path.join(self.tmp.name, "x.npy")
+        np.save(self.path, np.ascontiguousarray(x, dtype=np.float64))
+        self.n = x.shape[0]
+        self.pool = mp.get_context("spawn").Pool(self.nproc)
+        self.pool.map(_oracle_part, [None] * self.nproc)  # workers import the oracle once
+
+    def load(self, x):
+        """Positions for the following runs (a new memory-mapped file)."""
+        self.path = os.path.join(self.tmp.name, "x%d.npy" % id(x))
+        np.save(self.path, np.ascontiguousarray(x, dtype=np.float64))
+        self.n = x.shape[0]
+
+    def run(self, h, rc, lo=0, hi=None, nbins=0, forces=True):
+        hi = self.n if hi is None else hi
+        cuts = np.unique(np.linspace(lo, hi, 4 * self.nproc + 1).astype(np.int64))
+        jobs = [(self.path, h, rc, nbins, forces, int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:])]
+        t0 = time.perf_counter()
+        parts = self.pool.map(_oracle_part, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        out = {k: sum(p[k] for p in parts) for k in ("count", "band_in", "band_out", "suminvr", "energy")}
+        out["virial"] = sum(p["virial"] for p in parts)
+        out["dedh"] = sum(p["dedh"] for p in parts)
+        if forces:
+            out["forces"] = sum(p["forces"] for p in parts)
+        if nbins:
+            out["hist_core"] = sum(p["hist_core"] for p in parts)
+            out["hist_maybe"] = sum(p["hist_maybe"] for p in parts)
+        out["wall_s"] = wall
+        return out
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.tmp.cleanup()
+
+
+def cpu_baseline(w, pool, budget_s=15.0):
+    """The FP64 oracle as it stands on the host: all cores on the whole
+    workload (energy, forces, virial), and one core on a bounded sample (pairs
+    whose smaller index is below k). Returns the record and the all-core result,
+    which the precision record compares the GPU against."""
     import oracle
     x, h, rc = w["x"], w["h"], w["rc"]
+    full = pool.run(h, rc, forces=True)
     k = 20_000
     t0 = time.perf_counter()
     r = oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
@@ -180,49 +260,128 @@ def cpu_baseline(w, budget_s=15.0):
         t0 = time.perf_counter()
         r = oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
         dt = time.perf_counter() - t0
-    return {"value": r["count"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "pairs (i<j) with i < %d of the %d-particle workload: energy, forces, virial in FP64; "
-                      "%.1f s, %d pairs" % (k, x.shape[0], dt, r["count"]), "seconds": dt, "pairs": r["count"]}
+    rec = {"value": full["count"] / full["wall_s"], "unit": UNIT, "cores": pool.nproc, "kind": "oracle",
+           "sample": "whole workload (%d particles, %d pairs): FP64 energy, forces, virial, box gradient; "
+                     "one process per core over ranges of the smaller index; %.2f s wall"
+                     % (x.shape[0], full["count"], full["wall_s"]),
+           "single_core": {"value": r["count"] / dt, "unit": UNIT, "cores": 1,
+                           "sample": "pairs (i<j) with i < %d: %.1f s, %d pairs" % (k, dt, r["count"])}}
+    return rec, full
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 oracle on the host cores, same metric and workload."""
+    """Reference arm: the FP64 oracle, as it stands, on all host cores (one
+    process per core over ranges of the smaller pair index), same metric and
+    workload. Each step maps the pairs whose smaller index is below k, with k
+    chosen so that the whole run stays within about two minutes."""
     if rank != 0:
         return None
-    import synth
     w = load_workload(getattr(args, "workload", WORKLOAD))
-    import oracle
     x, h, rc = w["x"], w["h"], w["rc"]
-    k = 2000
-    for _ in range(min(args.warmup, 2)):
-        oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
-    times, pairs = [], 0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = oracle.pair_map(x, h, rc, forces=True, i_range=(0, k))
-        times.append(time.perf_counter() - t0)
-        pairs = r["count"]
+    n = x.shape[0]
+    pool = OraclePool(x)
+    try:
+        probe = pool.run(h, rc, 0, min(n, 64 * pool.nproc), forces=True)
+        per_row = probe["wall_s"] / min(n, 64 * pool.nproc)
+        budget = 120.0 / max(1, args.steps + min(args.warmup, 3))
+        k = int(min(n, max(pool.nproc * 16, budget / max(per_row, 1e-9))))
+        for _ in range(min(args.warmup, 3)):
+            pool.run(h, rc, 0, k, forces=True)
+        times, pairs = [], 0
+        for _ in range(args.steps):
+            r = pool.run(h, rc, 0, k, forces=True)
+            times.append(r["wall_s"])
+            pairs = r["count"]
+    finally:
+        pool.close()
     ms = 1e3 * sum(times) / len(times)
     value = pairs / (ms / 1e3)
+    sample = ("each step: pairs (i<j) with i < %d of the %d-particle workload (%d pairs), FP64 energy, forces, "
+              "virial, box gradient; %d processes" % (k, n, pairs, pool.nproc))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": getattr(args, "workload", WORKLOAD), "n": x.shape[0], "cutoff": rc,
-                       "sample": "each step: pairs (i<j) with i < %d" % k},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "pairs (i<j) with i < %d of the 1M lattice per step, FP64 energy, "
-                                       "forces, virial, single thread" % k},
+            "config": {"workload": getattr(args, "workload", WORKLOAD), "n": n, "cutoff": rc, "sample": sample,
+                       "same_config": k == n},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.nproc, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_pairlist(args, rank, world, local):
-    """w2_triclinic_1m: binning, the sorted i<j pair list (count pass, one
-    synchronisation for the total, fill pass) and the 200-bin histogram."""
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0}, "fallback (6.8 TB/s copy bandwidth; no MEASURED_PEAKS.json on this machine)"
+
+
+def fp32_peak(dev, clocks):
+    """FP32 peak of the ALUs: SMs x 128 lanes x 2 FLOP (FMA) x SM clock. The
+    clock is the highest sampled during the timed region (the sweep runs at the
+    maximum clock), else the 2,070 MHz maximum of the part."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, \
+        "%d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived from unit counts and the maximum clock)" % (sms, mhz)
+
+
+def sweep_roofline(dev, clocks, cand_half, pairs, kms, cand_eval, kernel):
+    """Roofline record of the sweep: algorithmic FP32 work (half-shell stencil
+    candidates x 8 + pair-images x 26) / the sweep's CUDA-event time, against
+    the FP32 peak. The work the kernel itself evaluated is reported beside it."""
+    peak, basis = fp32_peak(dev, clocks)
+    flop = cand_half * FLOP_PER_CANDIDATE + pairs * FLOP_PER_PAIR
+    achieved = flop / (kms / 1e3) / 1e12
+    flop_eval = cand_eval * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_FUSED
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": kernel, "kernel_ms": kms, "flop_per_launch": flop,
+            "flop_basis": "half-shell stencil candidates x %d + pair-images x %d (energy, forces, virial)"
+                          % (FLOP_PER_CANDIDATE, FLOP_PER_PAIR),
+            "candidates_half_shell_stencil": cand_half,
+            "evaluated": {"candidates": cand_eval, "flop": flop_eval, "tflops": flop_eval / (kms / 1e3) / 1e12,
+                          "frac": flop_eval / (kms / 1e3) / 1e12 / peak,
+                          "basis": "what the sweep evaluates: staged candidates x 8 + ordered pair-images x 16"},
+            "peak_basis": basis}
+
+
+def binning_record(n, ncells, ms, peaks, basis):
+    nbytes = BIN_BYTES_PER_PARTICLE * n + BIN_BYTES_PER_CELL * ncells
+    gbs = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "ms": ms, "bytes": nbytes, "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": gbs / peaks["hbm_gbs"], "peak_basis": basis,
+            "bytes_basis": "%d B per particle + %d B per cell (algorithmic)" % (BIN_BYTES_PER_PARTICLE,
+                                                                                 BIN_BYTES_PER_CELL)}
+
+
+def rel_err(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    scale = float(np.abs(b).max()) if b.size else 0.0
+    return float(np.abs(a - b).max() / scale) if scale > 0 else float(np.abs(a - b).max())
+
+
+def count_record(gpu, ref):
+    return {"gpu": int(gpu), "oracle": int(ref["count"]), "diff": int(gpu) - int(ref["count"]),
+            "band_in": int(ref["band_in"]), "band_out": int(ref["band_out"]),
+            "within_band": bool(ref["count"] - ref["band_in"] <= gpu <= ref["count"] + ref["band_out"])}
+
+
+def hist_record(gpu, ref):
+    gpu = np.asarray(gpu, dtype=np.int64)
+    core, maybe = ref["hist_core"], ref["hist_maybe"]
+    outside = int(np.sum((gpu < core) | (gpu > core + maybe)))
+    return {"bins": int(gpu.size), "bins_outside_band": outside, "band_pairs": int(maybe.sum()),
+            "off_core": int(np.sum(gpu - core))}
+
+
+def pairlist_leg(dev, steps, warmup, pool=None):
+    """The triclinic 1M workload (rows (220,0,0), (30,215,0), (20,25,210), rc 10):
+    binning, the sorted i<j pair list (count pass, 64-bit scan, one
+    synchronisation for the total, fill pass) and the 200-bin histogram. With a
+    pool, the histogram and the pair count are checked against the oracle."""
     import torch
     import paper_2202_06427_gb300 as P
-
-    dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
     w = load_workload("w2_triclinic_1m")
     x = torch.from_numpy(w["x"]).to(dev)
     h, rc, nbins = w["h"], w["rc"], w["nbins"]
@@ -233,64 +392,153 @@ def run_pairlist(args, rank, world, local):
     bufs = (torch.empty(pairs, dtype=torch.int32, device=dev), torch.empty(pairs, dtype=torch.int32, device=dev),
             torch.empty(pairs, dtype=torch.float32, device=dev))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
 
-    def step(ev=None):
+    def step(e=None):
+        if e is not None:
+            e[0].record(stream)
         P.cl_update(cl, x)
-        if ev is not None:
-            ev[0].record(stream)
+        if e is not None:
+            e[1].record(stream)
         got = P.cl_map(cl, "pairlist", out=bufs)["npairs"]
-        if ev is not None:
-            ev[1].record(stream)
-        P.cl_map(cl, "hist", nbins=nbins)
-        return got
+        if e is not None:
+            e[2].record(stream)
+        hist = P.cl_map(cl, "hist", nbins=nbins)["hist"]
+        if e is not None:
+            e[3].record(stream)
+        return got, hist
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize(dev)
+    for k in range(steps):
+        flush.fill_(float(k))
+        got, hist = step(ev[k])
+        assert got == pairs
+    torch.cuda.synchronize(dev)
+    avg = lambda a, b: sum(e[a].elapsed_time(e[b]) for e in ev) / steps
+    ms, bms, lms, hms = avg(0, 3), avg(0, 1), avg(1, 2), avg(2, 3)
+    peaks, basis = load_peaks()
+    # algorithmic bytes of the list passes: 12 B written per pair, the sorted
+    # float4 particles read once per pass
+    nbytes = 12 * pairs + 2 * 16 * n
+    gbs = nbytes / (lms / 1e3) / 1e9
+    out = {"workload": "w2_triclinic_1m", "n": n, "cutoff": rc, "lcell": LCELL, "pairs_per_step": pairs,
+           "steps": steps, "ms_per_step": ms, "pairs_per_s": pairs / (ms / 1e3),
+           "step": "binning + sorted i<j pair list (count, 64-bit scan, fill) + 200-bin histogram",
+           "binning_ms": bms, "pairlist_ms": lms, "hist_ms": hms,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": gbs / peaks["hbm_gbs"], "traffic": None, "kernel": "pair-list passes",
+                        "kernel_ms": lms, "bytes_per_launch": nbytes,
+                        "bytes_basis": "12 B per pair written + 16 B per particle read per pass", "peak_basis": basis},
+           "binning": binning_record(n, P.cl_query(cl, "ncells"), bms, peaks, basis),
+           "gpu_launches_per_step": 15}
+    if pool is not None:
+        pool.load(w["x"])
+        ref = pool.run(h, rc, nbins=nbins, forces=False)
+        out["precision"] = {"pairs": count_record(pairs, ref), "histogram": hist_record(hist.cpu().numpy(), ref),
+                            "oracle_wall_s": ref["wall_s"]}
+    return out
+
+
+def run_pairlist(args, rank, world, local):
+    """--workload w2_triclinic_1m: the pair-list step as the bench line."""
+    import torch
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
     sampler = ClockSampler(gpu_id(dev))
     sampler.start()
-    time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier(world, dev)
-    torch.cuda.synchronize(dev)
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        starts[k].record(stream)
-        assert step(kev[k]) == pairs
-        ends[k].record(stream)
-    torch.cuda.synchronize(dev)
+    leg = pairlist_leg(dev, args.steps, args.warmup)
     barrier(world, dev)
     sampler.stop()
-    ms = reduce_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps, world, dev)
-    kms = sum(a.elapsed_time(b) for a, b in kev) / args.steps
-    peaks, basis = {"hbm_gbs": 6800.0}, "fallback copy bandwidth (6.8 TB/s, no measured peaks on this machine)"
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks, basis = json.load(f), "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
-    except (OSError, ValueError):
-        pass
-    # algorithmic bytes of the list passes: 12 B written per pair, the sorted float4
-    # particles and cell offsets read once per pass
-    nbytes = 12 * pairs + 2 * 16 * n
-    achieved = nbytes / (kms / 1e3) / 1e9
-    return {"metric": METRIC, "value": pairs * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+    ms = reduce_max(leg["ms_per_step"], world, dev)
+    return {"metric": METRIC, "value": leg["pairs_per_step"] * world / (ms / 1e3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "w2_triclinic_1m", "n": n, "cutoff": rc, "lcell": LCELL, "pairs_per_step": pairs,
-                       "step": "binning + sorted i<j pair list (count, scan, fill) + 200-bin histogram",
+            "config": {"workload": "w2_triclinic_1m", "n": leg["n"], "cutoff": leg["cutoff"], "lcell": LCELL,
+                       "pairs_per_step": leg["pairs_per_step"], "step": leg["step"],
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            # bin, 3 scan, scatter, pair pack; cell count, listed-cell count, 3 scan, cell fill,
-            # listed-cell fill, long-segment sort; histogram sweep
-            "gpu_launches": 15 * args.steps,
-            "clocks": sampler.summary(),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                         "kernel": "pair-list passes (k_pairs_cell count and fill, scan, per-particle paths)",
-                         "kernel_ms": kms, "bytes_per_launch": nbytes,
-                         "peak_basis": basis}}
+            "gpu_launches": leg["gpu_launches_per_step"] * args.steps, "clocks": sampler.summary(),
+            "roofline": leg["roofline"], "binning": leg["binning"]}
+
+
+def energy_grad_step(P, cl, out, g, grad_x, grad_h, stream, e=None):
+    """One step of the hot path: binning, the fused energy/forces/box-gradient
+    sweep, chain rule. e: four events (start, after binning, after sweep, end)."""
+    if e is not None:
+        e[0].record(stream)
+    P.cl_update(cl, out[4])
+    if e is not None:
+        e[1].record(stream)
+    P.cl_energy_grad(cl, out=out[:4])  # forward: energy, dE/dx, dE/dH in one sweep
+    if e is not None:
+        e[2].record(stream)
+    P.cl_scale(g, out[1], grad_x)  # backward: dL/dx = dL/dE dE/dx
+    P.cl_scale(g, out[2], grad_h)
+    if e is not None:
+        e[3].record(stream)
+
+
+def clustered_leg(dev, steps, warmup):
+    """The 16M clustered set (box 600, rc 8): the same step as the headline."""
+    import torch
+    import paper_2202_06427_gb300 as P
+    w = load_workload("w4_clustered_16m")
+    x = torch.from_numpy(w["x"]).to(dev)
+    h, rc = w["h"], w["rc"]
+    n = x.shape[0]
+    lcell = LCELL_BY_WORKLOAD["w4_clustered_16m"]
+    stream = torch.cuda.current_stream(dev)
+    cl = P.cl_build(x, h, rc, lcell)
+    pairs = int(P.cl_map(cl, "count")["count"].item())
+    cand_half = P.cl_query(cl, "candidates")
+    g = torch.ones(1, dtype=torch.float64, device=dev)
+    out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float64, device=dev),
+           torch.empty((3, 3), dtype=torch.float64, device=dev), None, x)
+    grad_x = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    grad_h = torch.empty((3, 3), dtype=torch.float64, device=dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for _ in range(warmup):
+        energy_grad_step(P, cl, out, g, grad_x, grad_h, stream)
+    cand = P.cl_query(cl, "sweep_candidates")
+    torch.cuda.synchronize(dev)
+    for k in range(steps):
+        energy_grad_step(P, cl, out, g, grad_x, grad_h, stream, ev[k])
+    torch.cuda.synchronize(dev)
+    avg = lambda a, b: sum(e[a].elapsed_time(e[b]) for e in ev) / steps
+    ms, bms, kms = avg(0, 3), avg(0, 1), avg(1, 2)
+    peaks, basis = load_peaks()
+    return {"workload": "w4_clustered_16m", "n": n, "cutoff": rc, "lcell": lcell, "pairs_per_step": pairs,
+            "steps": steps, "ms_per_step": ms, "pairs_per_s": pairs / (ms / 1e3),
+            "step": "binning + fused energy/forces/box-gradient sweep + chain rule",
+            "l2": "inputs (384 MB positions) larger than L2",
+            "roofline": sweep_roofline(dev, None, cand_half, pairs, kms, cand, "cl_energy_grad sweep kernels"),
+            "binning": binning_record(n, P.cl_query(cl, "ncells"), bms, peaks, basis)}
+
+
+def precision_small(P, dev, pool):
+    """Every output of the library on the 10k workload (3D, box 46.416, rc 12)
+    against the oracle: count (with the band), sum 1/r, energy, forces, virial,
+    dE/dH, a 100-bin histogram."""
+    import torch
+    w = load_workload("w0_small_10k")
+    x, h, rc = w["x"], w["h"], w["rc"]
+    pool.load(x)
+    ref = pool.run(h, rc, nbins=100, forces=True)
+    pos = torch.from_numpy(x).to(dev)
+    cl = P.cl_build(pos, h, rc, LCELL)
+    cnt = int(P.cl_map(cl, "count")["count"].item())
+    s1 = P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item()
+    hist = P.cl_map(cl, "hist", nbins=100)["hist"].cpu().numpy()
+    e, dedx, dedh, vir = P.cl_energy_grad(cl, want_virial=True)
+    return {"count": count_record(cnt, ref), "sum_inv_r_rel": abs(s1 - ref["suminvr"]) / abs(ref["suminvr"]),
+            "energy_rel": abs(e.item() - ref["energy"]) / abs(ref["energy"]),
+            "forces_maxnorm_rel": rel_err(-dedx.cpu().numpy(), ref["forces"]),
+            "virial_rel": rel_err(vir.cpu().numpy(), ref["virial"]),
+            "dedh_rel": rel_err(dedh.cpu().numpy(), ref["dedh"]),
+            "histogram": hist_record(hist, ref)}
 
 
 def run_ours(args, rank, world, local):
@@ -298,97 +546,95 @@ def run_ours(args, rank, world, local):
         return run_pairlist(args, rank, world, local)
     import torch
     import paper_2202_06427_gb300 as P
-    import synth
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    w = load_workload(getattr(args, "workload", WORKLOAD))
+    workload = getattr(args, "workload", WORKLOAD)
+    w = load_workload(workload)
     x = torch.from_numpy(w["x"]).to(dev)
     h, rc = w["h"], w["rc"]
     n = x.shape[0]
     stream = torch.cuda.current_stream(dev)
-    lcell = LCELL_BY_WORKLOAD.get(getattr(args, "workload", WORKLOAD), LCELL)
+    lcell = LCELL_BY_WORKLOAD.get(workload, LCELL)
     cl = P.cl_build(x, h, rc, lcell)
     pairs = int(P.cl_map(cl, "count")["count"].item())
     cand_half = P.cl_query(cl, "candidates")
+    ncells = P.cl_query(cl, "ncells")
     g = torch.ones(1, dtype=torch.float64, device=dev)
     out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty((n, 3), dtype=torch.float64, device=dev),
-           torch.empty((3, 3), dtype=torch.float64, device=dev), None)
+           torch.empty((3, 3), dtype=torch.float64, device=dev), None, x)
     grad_x = torch.empty((n, 3), dtype=torch.float64, device=dev)
     grad_h = torch.empty((3, 3), dtype=torch.float64, device=dev)
-    P.cl_energy_grad(cl, out=out)
+    P.cl_energy_grad(cl, out=out[:4])
     cand = P.cl_query(cl, "sweep_candidates")  # candidate pairs the fused sweep evaluates
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
-    def step(ev=None):
-        P.cl_update(cl, x)
-        if ev is not None:
-            ev[0].record(stream)
-        P.cl_energy_grad(cl, out=out)  # forward: energy, dE/dx, dE/dH in one sweep
-        if ev is not None:
-            ev[1].record(stream)
-        P.cl_scale(g, out[1], grad_x)  # backward: dL/dx = dL/dE dE/dx
-        P.cl_scale(g, out[2], grad_h)
-
     for _ in range(args.warmup):
-        step()
+        energy_grad_step(P, cl, out, g, grad_x, grad_h, stream)
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(gpu_id(dev))
     sampler.start()
     time.sleep(0.3)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier(world, dev)
     torch.cuda.synchronize(dev)
     for k in range(args.steps):
         flush.fill_(float(k))  # evict the inputs from L2 between steps (outside the timed events)
-        starts[k].record(stream)
-        step(kev[k])
-        ends[k].record(stream)
+        energy_grad_step(P, cl, out, g, grad_x, grad_h, stream, ev[k])
     torch.cuda.synchronize(dev)
     barrier(world, dev)
     sampler.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    kern_ms = [a.elapsed_time(b) for a, b in kev]
-    ms = reduce_max(sum(step_ms) / len(step_ms), world, dev)
-    kms = sum(kern_ms) / len(kern_ms)
+    avg = lambda a, b: sum(e[a].elapsed_time(e[b]) for e in ev) / args.steps
+    ms = reduce_max(avg(0, 3), world, dev)
+    bms, kms = avg(0, 1), avg(1, 2)
     value = pairs * world / (ms / 1e3)
-
-    # roofline of the dominant kernel (the fused energy-and-gradient sweep)
     clocks = sampler.summary()
-    props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
-    max_mhz = clocks["sm_max_mhz"] or 2070.0
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * max_mhz * 1e6 / 1e12
-    flop = cand * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_FUSED
-    achieved = flop / (kms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops,
-                "traffic": SWEEP_DRAM_BYTES if getattr(args, "workload", WORKLOAD) == WORKLOAD else None,
-                "kernel": "k_hood<3> (cl_energy_grad: neighbourhood sweep, energy + forces + box gradient)",
-                "kernel_ms": kms, "flop_per_launch": flop, "candidates_per_launch": cand,
-                "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (of max clock, not measured)" % (sms, max_mhz)}
+    peaks, basis = load_peaks()
+    roofline = sweep_roofline(dev, clocks, cand_half, pairs, kms, cand,
+                              "cl_energy_grad sweep kernels (neighbourhood sweep: energy + forces + box gradient)")
+    roofline["traffic"] = SWEEP_DRAM_BYTES if workload == WORKLOAD else None
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": getattr(args, "workload", WORKLOAD), "n": n, "box": float(h[0][0]), "cutoff": rc, "lcell": lcell,
+            "config": {"workload": workload, "n": n, "box": float(h[0][0]), "cutoff": rc, "lcell": lcell,
                        "pairs_per_step": pairs, "candidates_sweep": cand, "candidates_half_shell_stencil": cand_half,
                        "step": "binning + fused energy/forces/box-gradient sweep (forward) + chain rule (backward)",
                        "l2": "flushed between steps by a 256 MB write outside the timed events",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            # bin, 3 scan, scatter, pair pack; cell list, sweep, per-particle companion, dense-cell sweep,
-            # 2 reduce; 2 scale
-            "gpu_launches": 14 * args.steps,
-            "clocks": clocks, "roofline": roofline}
+            "gpu_launches": STEP_LAUNCHES * args.steps,
+            "clocks": clocks, "roofline": roofline,
+            "binning": binning_record(n, ncells, bms, peaks, basis),
+            "sweep_pairs_per_s": pairs / (kms / 1e3)}
 
     if not args.no_e2e:
         line["e2e"] = e2e(P, cl, w, dev, stream, pairs, args, world)
     if not args.no_serve:
         line["serve"] = serve_leg(dev)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0 and world == 1 and not args.no_extra:
+        line["workloads"] = {"w2_triclinic_1m": None, "w4_clustered_16m": None}
+        pool = OraclePool(w["x"]) if not args.no_cpu_baseline else None
+        try:
+            if pool is not None:
+                line["cpu_baseline"], full = cpu_baseline(w, pool)
+                e, dedx, dedh, vir = P.cl_energy_grad(cl, want_virial=True)
+                line["precision"] = {
+                    workload: {"count": count_record(pairs, full),
+                               "energy_rel": abs(e.item() - full["energy"]) / abs(full["energy"]),
+                               "forces_maxnorm_rel": rel_err(-dedx.cpu().numpy(), full["forces"]),
+                               "virial_rel": rel_err(vir.cpu().numpy(), full["virial"]),
+                               "dedh_rel": rel_err(dedh.cpu().numpy(), full["dedh"])},
+                    "w0_small_10k": precision_small(P, dev, pool)}
+            line["workloads"]["w2_triclinic_1m"] = pairlist_leg(dev, 20, 3, pool)
+            if pool is not None:
+                line["precision"]["w2_triclinic_1m"] = line["workloads"]["w2_triclinic_1m"].pop("precision")
+        finally:
+            if pool is not None:
+                pool.close()
+        del out, grad_x, flush
+        P.cl_free(cl)
+        torch.cuda.empty_cache()
+        line["workloads"]["w4_clustered_16m"] = clustered_leg(dev, 10, 3)
     return line
 
 

@@ -27,6 +27,10 @@ Functions and the passages they follow:
   mass_potential -- Code 5, second example: sum of m_i m_j / r.
   velocity_hist -- Code 10: pair counts and summed |v_i - v_j| per distance bin.
   knn_pairs     -- Code 8: the k cross pair-images of smallest distance.
+  open_box / open_pair_map / open_pairlist / open_cross_images
+                -- Sec. 4.1 without periodic boundaries: the pair-images of a
+                   box wider than the points' extent plus the cutoff on every
+                   axis are exactly the direct pairs of the open system.
   geom_info     -- widths between lattice faces and the cell grid for lcell.
   closed_form   -- see oracle.closed_form (perfect-lattice sums).
 """
@@ -344,3 +348,28 @@ def knn_pairs(xa, yb, h, rc, k, band=1e-6, img=None):
     order = np.lexsort((img["j"][sel], img["i"][sel], img["r"][sel]))[:k]
     r = img["r"][sel][order]
     return {"i": img["i"][sel][order], "j": img["j"][sel][order], "r": r}
+
+
+def open_box(*sets, rc):
+    """Orthorhombic box for points without periodic boundaries (Sec. 4.1): on
+    every axis the side exceeds the extent of all points plus rc + 1, so for
+    any two points every lattice image but the direct one lies more than
+    rc + 1 away, beyond rc(1 + 4 band)."""
+    allx = np.vstack([np.asarray(x, dtype=np.float64) for x in sets if len(x)])
+    dim = allx.shape[1]
+    ext = allx.max(axis=0) - allx.min(axis=0) if allx.shape[0] else np.zeros(dim)
+    return np.diag(ext + rc + 1.0)
+
+
+def open_pair_map(x, rc, band=1e-6, nbins=0, rmax=None, forces=True):
+    """pair_map over the direct pairs i < j with r < rc of an open system."""
+    return pair_map(x, open_box(x, rc=rc), rc, band=band, nbins=nbins, rmax=rmax, forces=forces)
+
+
+def open_pairlist(x, rc, band=1e-6):
+    return pairlist(x, open_box(x, rc=rc), rc, band=band)
+
+
+def open_cross_images(xa, yb, rc, band=1e-6):
+    """cross_images between two open sets: every (a, b) with |y_b - x_a| < rc(1 + 4 band)."""
+    return cross_images(xa, yb, open_box(xa, yb, rc=rc), rc, band=band)

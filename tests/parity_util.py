@@ -95,3 +95,68 @@ def oracle_pool(x, h, rc, nbins=0, forces=True, nproc=None):
         out["hist_core"] = sum(p["hist_core"] for p in parts)
         out["hist_maybe"] = sum(p["hist_maybe"] for p in parts)
     return out
+
+
+def _rows_part(args):
+    """Compare the GPU list's rows [lo, hi) with the oracle's rows (spawned worker)."""
+    import ctypes
+    import oracle
+    path, h, rc, lo, hi, gi, gj, gd = args
+    x = np.load(path, mmap_mode="r")
+    n = x.shape[0]
+    idx = np.arange(lo, hi, dtype=np.int64)
+    k = idx.shape[0]
+    cap = max(1024, 4 * gj.shape[0] + 1024)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    xc = np.ascontiguousarray(x)
+    hc = np.ascontiguousarray(h, dtype=np.float64)
+    while True:
+        offs = np.zeros(k + 1, dtype=np.int64)
+        oj = np.zeros(cap, dtype=np.int64)
+        od = np.zeros(cap)
+        ob = np.zeros(cap, dtype=np.int8)
+        ret = oracle._lib().or_neighbors(3 if hc.shape[0] == 3 else 2, n, p(xc), p(hc), rc, BAND, p(idx), k, cap,
+                                         p(offs), p(oj), p(od), p(ob))
+        if ret == -4:
+            cap = int(offs[k]) + 1
+            continue
+        assert ret == 0, ret
+        break
+    m = int(offs[k])
+    oi = np.repeat(idx, np.diff(offs))
+    okey = oi * n + oj[:m]
+    od, ob = od[:m], ob[:m].astype(bool)
+    gkey = gi.astype(np.int64) * n + gj
+    certain = (od < rc) & ~ob
+    missing = int(np.sum(~np.isin(okey[certain], gkey)))
+    pos = np.searchsorted(okey, gkey)
+    known = (pos < m) & (okey[np.minimum(pos, m - 1)] == gkey)
+    extra = int(np.sum(~known))
+    derr = np.abs(gd[known].astype(np.float64) - od[pos[known]])
+    return {"rows": k, "pairs": int(gkey.shape[0]), "oracle_certain": int(certain.sum()), "band": int(ob.sum()),
+            "missing": missing, "extra": extra, "max_d_err": float(derr.max()) if derr.size else 0.0}
+
+
+def pairlist_pool_check(x, h, rc, gi, gj, gd, nproc=None, chunks_per_proc=4):
+    """Whole-list comparison of a sorted GPU pair list (gi, gj, gd host arrays,
+    sorted by (i, j)) with the oracle's rows, chunked by index range in a
+    spawn pool: per chunk the oracle lists the rows' neighbours j > i and the
+    GPU slice of those rows is compared against them. Returns the summed
+    counts of missing pairs (certain oracle pairs absent), extra pairs (absent
+    from the oracle's band-widened rows) and the largest distance error."""
+    import tempfile
+    n = x.shape[0]
+    nproc = nproc or min(16, mp.cpu_count())
+    cuts = np.unique(np.linspace(0, n, chunks_per_proc * nproc + 1).astype(np.int64))
+    bounds = np.searchsorted(gi, cuts)
+    ctx = mp.get_context("spawn")
+    with tempfile.TemporaryDirectory() as tmp:
+        path = tmp + "/x.npy"
+        np.save(path, np.ascontiguousarray(x, dtype=np.float64))
+        jobs = [(path, h, rc, int(a), int(b), gi[s0:s1], gj[s0:s1], gd[s0:s1])
+                for a, b, s0, s1 in zip(cuts[:-1], cuts[1:], bounds[:-1], bounds[1:])]
+        with ctx.Pool(nproc) as pool:
+            parts = pool.map(_rows_part, jobs, chunksize=1)
+    out = {k: sum(p[k] for p in parts) for k in ("rows", "pairs", "oracle_certain", "band", "missing", "extra")}
+    out["max_d_err"] = max(p["max_d_err"] for p in parts)
+    return out

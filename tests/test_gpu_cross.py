@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from parity_util import BAND
+from parity_util import BAND, check_count, check_energy, check_forces, check_hist
 
 pytestmark = pytest.mark.gpu
 
@@ -105,10 +105,11 @@ def test_cross_pairlist_dense_queries(cuda_ok):
     assert want <= got and got <= want | maybe
 
 
-def test_open_boundaries_match_brute_force(cuda_ok):
+def test_open_boundaries_match_oracle(cuda_ok):
     """No periodic boundaries (Sec. 4.1): the bounding box makes every image but
     the direct one lie beyond the cutoff, so the cell list gives exactly the
-    pairs of the open system (brute force over all pairs, no images)."""
+    pairs of the open system (the oracle's open-system sums, pinned against a
+    direct double loop)."""
     import paper_2202_06427_gb300 as P
     rng = np.random.default_rng(901)
     xa = rng.normal(size=(2500, 3)) * 4.0 + np.array([100.0, -50.0, 3.0])
@@ -118,19 +119,28 @@ def test_open_boundaries_match_brute_force(cuda_ok):
     pb = torch.from_numpy(yb).cuda()
     cl = P.cl_build_open(pa, rc, 2, pos2=pb)
     # within set A
-    dd = np.linalg.norm(xa[:, None, :] - xa[None, :, :], axis=2)
-    iu = np.triu_indices(xa.shape[0], 1)
-    r_in = dd[iu]
-    assert int(P.cl_map(cl, "count")["count"].item()) == int(np.sum(r_in < rc))
-    e_ref = np.sum((1.0 / r_in - 1.0 / rc + (r_in - rc) / rc ** 2)[r_in < rc])
-    assert abs(P.cl_map(cl, "energy")["energy"].item() - e_ref) <= 1e-6 * abs(e_ref)
+    ref = oracle.open_pair_map(xa, rc, band=BAND, nbins=30)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    efv = P.cl_map(cl, "energy_forces_virial")
+    check_forces(efv["forces"].cpu().numpy(), ref["forces"])
+    check_hist(P.cl_map(cl, "hist", nbins=30)["hist"].cpu().numpy(), ref)
+    pl = P.cl_map(cl, "pairlist")
+    rl = oracle.open_pairlist(xa, rc, band=BAND)
+    got = set((pl["i"].cpu().numpy().astype(np.int64) * 2500 + pl["j"].cpu().numpy()).tolist())
+    key = rl["i"] * 2500 + rl["j"]
+    certain = (rl["d"] < rc) & ~rl["band"]
+    assert set(key[certain].tolist()) <= got <= set(key.tolist())
     # across the two sets
-    dx = np.linalg.norm(yb[:, None, :] - xa[None, :, :], axis=2)
-    assert P.cl_cross_count(cl, pb) == int(np.sum(dx < rc))
+    img = oracle.open_cross_images(xa, yb, rc, band=BAND)
+    edge = oracle.band_mask(img, rc, BAND)
+    inside = img["r"] < rc
+    n_cross = P.cl_cross_count(cl, pb)
+    assert int(np.sum(inside & ~edge)) <= n_cross <= int(np.sum(inside | edge))
     out = P.cl_cross_pairlist(cl, pb)
     got = set((out["b"].cpu().numpy().astype(np.int64) * 2500 + out["a"].cpu().numpy()).tolist())
-    bb, aa = np.nonzero(dx < rc)
-    assert got == set((bb.astype(np.int64) * 2500 + aa).tolist())
+    key = img["j"].astype(np.int64) * 2500 + img["i"]
+    assert set(key[inside & ~edge].tolist()) <= got <= set(key[inside | edge].tolist())
 
 
 def test_cross_errors(cuda_ok):

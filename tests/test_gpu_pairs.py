@@ -7,7 +7,7 @@ import torch
 
 import oracle
 import synth
-from parity_util import BAND, check_count, check_hist, oracle_pool
+from parity_util import BAND, check_count, check_hist, oracle_pool, pairlist_pool_check
 
 pytestmark = pytest.mark.gpu
 
@@ -158,6 +158,11 @@ def test_workload_triclinic_1m(cuda_ok):
     check_count(pl["npairs"], ref)  # tested from the smaller index's end: band pairs may differ from cnt
     assert 2.0e8 < cnt < 2.2e8
     i, j, d = check_list_structure(pl, n, rc)
+    # the whole list, row by row, against the oracle's rows (chunked in a pool)
+    whole = pairlist_pool_check(x, h, rc, i, j, d)
+    assert whole["rows"] == n and whole["pairs"] == len(i)
+    assert whole["missing"] == 0 and whole["extra"] == 0, whole
+    assert whole["max_d_err"] <= BAND * rc, whole
     rows = np.random.default_rng(3).choice(n, size=1500, replace=False)
     rows = np.sort(np.concatenate([rows, [0, n - 1]]))
     refs = oracle.neighbors(x, h, rc, rows, band=BAND)
