@@ -222,11 +222,6 @@ def test_all_in_one_cell_and_multi_image(cuda_ok):
     cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, 1)
     assert P.cl_query(cl, "ncells") == 1
     check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
-    # more than 2^31 pairs: the pair list's offsets and total are 64-bit, so a
-    # call with a small buffer reports CL_ERR_CAPACITY and the exact total
-    total = pairlist_total(P, cl)
-    assert total > 2 ** 31
-    check_count(total, ref)
     check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
     efv = P.cl_map(cl, "energy_forces_virial")
     check_forces(efv["forces"].cpu().numpy(), ref["forces"])
