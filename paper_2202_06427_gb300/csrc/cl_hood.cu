@@ -66,17 +66,18 @@ __host__ __device__ constexpr int hood_nv(int mode) {
 }
 
 struct Smem {
-  float4 xy[kCap / 2];   // staged pairs (x_2k, x_2k+1, y_2k, y_2k+1)
-  float2 zz[kCap / 2];   // (z_2k, z_2k+1)
+  float4 xy[kCap / 2 + 16];  // staged pairs (x_2k, x_2k+1, y_2k, y_2k+1); 32 trash entries at the end
+  float2 zz[kCap / 2 + 16];  // (z_2k, z_2k+1)
   float4 oxy[kHome / 2]; // own cell in sorted order, same layout
   float2 ozz[kHome / 2];
   int hid[kHome];        // original index of the home particle
   float acc[kHome][6];   // Gn and its T = 0 part
   float4 otab[kTab];     // stencil entry: (shift x, y, z, unwrapped offset as int bits)
+  unsigned short rowk[kTab + 1];  // rows of the stencil: entries [rowk[r], rowk[r + 1])
+  int nrows;
   float wmax[kWarps];
   int nf, nb;            // staged entries with T = 0 (from the front) and T != 0 (from the back)
   int item;
-  int pref;              // the cell after this one
   unsigned long long ncand;  // candidate pairs this CTA evaluated
   double out[kWarps][16];    // per-warp sums: share of sum fsn r (x) r (6), X (9), energy (1)
 };
@@ -198,154 +199,196 @@ __device__ __forceinline__ void hood_own(const float4* __restrict__ xy, const fl
   }
 }
 
-// Neighbour cell of stencil entry k for one home cell: its particle range, its
-// shift, and the key offset of its segment (T != 0 staged apart).
-struct OffInfo {
-  int j0, j1, seg;
-  float sx, sy, sz;
-};
-
-template <bool FORCE>
-__device__ __forceinline__ OffInfo off_info(const SweepArgs& A, const Smem& S, int k, int cx, int cy, int cz) {
-  OffInfo f;
-  const float4 t = S.otab[k];
-  int ox, oy, oz;
-  unpack_off(__float_as_int(t.w), ox, oy, oz);
-  int x2 = cx + ox, y2 = cy + oy, z2 = cz + oz;
-  const bool wrap = (x2 < 0) || (x2 >= A.nx) || (y2 < 0) || (y2 >= A.ny) || (z2 < 0) || (z2 >= A.nz);
-  x2 %= A.nx;
-  x2 += x2 < 0 ? A.nx : 0;
-  y2 %= A.ny;
-  y2 += y2 < 0 ? A.ny : 0;
-  z2 %= A.nz;
-  z2 += z2 < 0 ? A.nz : 0;
-  const int c = x2 + A.nx * (y2 + A.ny * z2);
-  f.j0 = A.cell_start[c];
-  f.j1 = A.cell_start[c + 1];
-  f.seg = (FORCE && wrap) ? 1 : 0;
-  f.sx = t.x;
-  f.sy = t.y;
-  f.sz = t.z;
-  return f;
-}
-
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
-// L1 prefetch of the cell ranges (cell_start pairs) that stencil entry k of cell
-// h reads, and of the cell's own range.
-__device__ __forceinline__ void prefetch_ranges(const SweepArgs& A, const Smem& S, int h, int k) {
-  const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
-  if (k == 1) prefetch_l1(A.cell_start + h);
-  if (k < A.noff && k < kTab) {
+// Rows of the stencil. Entries 1.. of the stencil are ordered by (oz, oy, ox)
+// with ox fastest, so a maximal run of entries with the same (oy, oz) and
+// consecutive ox is a row of neighbour cells; cells are linearised x-fastest,
+// so at one home cell the particles of a row are ONE contiguous range of the
+// sorted arrays, or a few where the row crosses the periodic boundary in x
+// (segments, each with its own lattice image along x). The own cell (entry 0)
+// is in no row.
+__device__ __forceinline__ int floordiv_i(int a, int b) {  // b > 0
+  if (a >= 0 && a < b) return 0;  // inside the box: the common case, no division
+  const int q = a / b;
+  return q - ((a % b != 0) && (a < 0) ? 1 : 0);
+}
+
+// Row table of the stencil in S.otab (entries 1 .. min(noff, kTab) - 1), built
+// by one thread.
+__device__ void build_rows(const SweepArgs& A, Smem& S) {
+  const int ne = A.noff < kTab ? A.noff : kTab;
+  int nr = 0, pox = 0, poy = 0, poz = 0;
+  for (int k = 1; k < ne; ++k) {
     int ox, oy, oz;
     unpack_off(__float_as_int(S.otab[k].w), ox, oy, oz);
-    int x2 = (cx + ox) % A.nx, y2 = (cy + oy) % A.ny, z2 = (cz + oz) % A.nz;
-    x2 += x2 < 0 ? A.nx : 0;
-    y2 += y2 < 0 ? A.ny : 0;
-    z2 += z2 < 0 ? A.nz : 0;
-    prefetch_l1(A.cell_start + x2 + A.nx * (y2 + A.ny * z2));
+    if (k == 1 || oy != poy || oz != poz || ox != pox + 1) S.rowk[nr++] = (unsigned short)k;
+    pox = ox;
+    poy = oy;
+    poz = oz;
   }
+  S.rowk[nr] = (unsigned short)(ne > 1 ? ne : 1);
+  S.nrows = nr;
 }
 
-// Staging by one warp of its stencil entries 1 + warp + kWarps m, m < nmine
-// (lane m holds entry m's OffInfo). Lanes take consecutive particles of a
-// neighbour cell (coalesced loads); the first 32 particles of kRound cells are
-// loaded before any is used. Kept particles are compacted with ballots, T = 0
-// entries from the front of the buffer and T != 0 entries from the back, with
-// one shared-memory atomic per segment and round. Writes stay in bounds;
-// overflow (nf + nb + 2 > kCap) is detected afterwards.
+// One contiguous particle range of a row at a home cell: sorted particles
+// [p0, p1); a particle in wrapped cell column xj has stencil entry ebase + xj;
+// back = 1 when its lattice image is not zero (T != 0 neighbours are staged
+// apart for the virial).
+struct RowSeg {
+  int p0, p1, ebase, back;
+  bool valid;  // the row has a segment of that number
+};
+
+// Segment number `which` of row r at home cell (cx, cy, cz).
+template <bool FORCE>
+__device__ __forceinline__ RowSeg row_segment(const SweepArgs& A, const Smem& S, int r, int which, int cx, int cy,
+                                              int cz) {
+  RowSeg g;
+  g.p0 = g.p1 = g.ebase = g.back = 0;
+  g.valid = false;
+  const int e0 = S.rowk[r], e1 = S.rowk[r + 1];
+  int ox0, oy, oz, ox1, t1, t2;
+  unpack_off(__float_as_int(S.otab[e0].w), ox0, oy, oz);
+  unpack_off(__float_as_int(S.otab[e1 - 1].w), ox1, t1, t2);
+  int y2 = cy + oy, z2 = cz + oz;
+  const int ty = floordiv_i(y2, A.ny), tz = floordiv_i(z2, A.nz);
+  y2 -= ty * A.ny;
+  z2 -= tz * A.nz;
+  int ox = ox0;
+  for (int k = 0; ox <= ox1; ++k) {
+    const int x = cx + ox;
+    const int tx = floordiv_i(x, A.nx);
+    const int xw = x - tx * A.nx;
+    const int len = min(ox1 - ox + 1, A.nx - xw);  // cells up to the row's end or the box edge
+    if (k == which) {
+      const int ca = xw + A.nx * (y2 + A.ny * z2);
+      g.p0 = A.cell_start[ca];
+      g.p1 = A.cell_start[ca + len];
+      g.ebase = e0 - ox0 + tx * A.nx - cx;
+      g.back = (FORCE && (tx | ty | tz) != 0) ? 1 : 0;
+      g.valid = true;
+      break;
+    }
+    ox += len;
+  }
+  return g;
+}
+
+// Entry e of the staged pair layout: x at 2e - (e & 1), y two floats later, z at e.
 __device__ __forceinline__ void stage_put(Smem& S, int e, float x, float y, float z) {
-  if (e >= 0 && e < kCap) {
-    // entry e of the pair layout: x at 2e - (e & 1), y two floats later, z at e
-    float* const xyf = reinterpret_cast<float*>(S.xy);
-    const int ix = 2 * e - (e & 1);
-    xyf[ix] = x;
-    xyf[ix + 2] = y;
-    reinterpret_cast<float*>(S.zz)[e] = z;
-  }
+  float* const xyf = reinterpret_cast<float*>(S.xy);
+  const int ix = 2 * e - (e & 1);
+  xyf[ix] = x;
+  xyf[ix + 2] = y;
+  reinterpret_cast<float*>(S.zz)[e] = z;
 }
 
-// One 32-particle group of a cell, compacted on its own (cells of more than 32).
-__device__ __forceinline__ void stage_group(Smem& S, float4 q, float sx, float sy, float sz, int seg, float top2,
-                                            unsigned lt) {
-  const float x = q.x + sx, y = q.y + sy, z = q.z + sz;
-  const bool keep = fmaf(x, x, fmaf(y, y, z * z)) < top2;
-  const unsigned m = __ballot_sync(0xffffffffu, keep);
-  if (!m) return;
-  int base = 0;
-  if (lt == 0u) base = atomicAdd(seg ? &S.nb : &S.nf, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (keep) {
-    const int r = base + __popc(m & lt);
-    stage_put(S, seg ? kCap - 1 - r : r, x, y, z);
-  }
+// Staged-buffer entry of a particle: rank r among the kept T = 0 entries (from
+// the front) or T != 0 entries (from the back); lanes that keep nothing, and
+// ranks beyond the buffer (an overflowing cell, handed to the dense-cell sweep
+// afterwards), write to the lane's trash entry past the end.
+__device__ __forceinline__ int stage_slot(bool keep, bool back, int r, int lane) {
+  const int e = back ? kCap - 1 - r : r;
+  return (keep && e >= 0 && e < kCap) ? e : kCap + lane;
 }
 
-__device__ __forceinline__ void stage_warp(const SweepArgs& A, Smem& S, const OffInfo& mine, int nmine, float top2) {
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
-  for (int m0 = 0; m0 < nmine; m0 += kRound) {
-    float4 q[kRound];
-#pragma unroll
-    for (int r = 0; r < kRound; ++r) {
-      const int src = (m0 + r) & 31;
-      const int j0 = __shfl_sync(0xffffffffu, mine.j0, src);
-      int j1 = __shfl_sync(0xffffffffu, mine.j1, src);
-      if (m0 + r >= nmine) j1 = j0;
-      const int j = j0 + lane;
-      q[r] = j < j1 ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f);
+constexpr int kStageBatch = 4;  // 32-particle chunks of a segment loaded before any is used
+
+// Staging by warp w of rows w, w + kWarps, ..., 32 segments at a time: lane l
+// describes segment l & 1 of row w + kWarps (m0 + l / 2) (rows with more
+// segments, which only very small grids have, are walked one by one
+// afterwards). The warp then takes the segments in turn, lanes over
+// consecutive particles (coalesced), kStageBatch chunks loaded before any is
+// used and one shared-memory atomic per segment and batch; loads, shifts,
+// tests and writes are predicated rather than branched. Each particle is
+// shifted into the home frame by its own stencil entry (found from its cell
+// column) and kept when |x'| < top; kept particles are compacted with ballots,
+// T = 0 entries from the front of the buffer and T != 0 entries from the back.
+// Overflow (nf + nb + 2 > kCap) is detected afterwards.
+template <bool FORCE>
+__device__ __forceinline__ void stage_rows(const SweepArgs& A, Smem& S, int cx, int cy, int cz, float top2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nrows = S.nrows;
+  const int nmine = nrows > warp ? (nrows - 1 - warp) / kWarps + 1 : 0;
+  for (int m0 = 0; m0 < nmine; m0 += 16) {
+    const int m = m0 + (lane >> 1);
+    RowSeg sg;
+    sg.p0 = sg.p1 = sg.ebase = sg.back = 0;
+    bool more = false;
+    if (m < nmine) {
+      const int r = warp + kWarps * m;
+      sg = row_segment<FORCE>(A, S, r, lane & 1, cx, cy, cz);
+      if (!sg.valid) sg.p0 = sg.p1 = 0;
+      if (lane & 1) more = row_segment<FORCE>(A, S, r, 2, cx, cy, cz).valid;
     }
-    // ballots of the round, then one atomic per segment
-    unsigned m[kRound];
-    int seg[kRound];
-    int nF = 0, nB = 0;
+    unsigned live = __ballot_sync(0xffffffffu, sg.p1 > sg.p0);  // non-empty segments
+    while (live) {
+      const int src = __ffs(live) - 1;
+      live &= live - 1;
+      const int p0 = __shfl_sync(0xffffffffu, sg.p0, src);
+      const int p1 = __shfl_sync(0xffffffffu, sg.p1, src);
+      const int eb = __shfl_sync(0xffffffffu, sg.ebase, src);
+      const bool back = __shfl_sync(0xffffffffu, sg.back, src) != 0;
+      for (int pb = p0; pb < p1; pb += 32 * kStageBatch) {
+        float4 v[kStageBatch];
+        unsigned c[kStageBatch];
 #pragma unroll
-    for (int r = 0; r < kRound; ++r) {
-      const int src = (m0 + r) & 31;
-      const float x = q[r].x + __shfl_sync(0xffffffffu, mine.sx, src);
-      const float y = q[r].y + __shfl_sync(0xffffffffu, mine.sy, src);
-      const float z = q[r].z + __shfl_sync(0xffffffffu, mine.sz, src);
-      seg[r] = __shfl_sync(0xffffffffu, mine.seg, src);
-      m[r] = __ballot_sync(0xffffffffu, fmaf(x, x, fmaf(y, y, z * z)) < top2);
-      q[r].x = x;
-      q[r].y = y;
-      q[r].z = z;
-      if (seg[r]) nB += __popc(m[r]);
-      else nF += __popc(m[r]);
-    }
-    int bF = 0, bB = 0;
-    if (lane == 0) {
-      if (nF) bF = atomicAdd(&S.nf, nF);
-      if (nB) bB = atomicAdd(&S.nb, nB);
-    }
-    bF = __shfl_sync(0xffffffffu, bF, 0);
-    bB = __shfl_sync(0xffffffffu, bB, 0);
+        for (int u = 0; u < kStageBatch; ++u) {
+          const int p = min(pb + 32 * u + lane, p1 - 1);  // clamped: the tail re-reads the last particle
+          v[u] = A.xs[p];
+          c[u] = A.cellc[p];
+        }
+        unsigned mk[kStageBatch];
+        int n = 0;
 #pragma unroll
-    for (int r = 0; r < kRound; ++r) {
-      if ((m[r] >> lane) & 1u) {
-        const int rk = __popc(m[r] & lt);
-        stage_put(S, seg[r] ? kCap - 1 - (bB + rk) : bF + rk, q[r].x, q[r].y, q[r].z);
+        for (int u = 0; u < kStageBatch; ++u) {
+          const float4 sh = S.otab[eb + (int)(c[u] & 1023u)];
+          v[u].x += sh.x;
+          v[u].y += sh.y;
+          v[u].z += sh.z;
+          const bool keep = pb + 32 * u + lane < p1 &&
+                            fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, v[u].z * v[u].z)) < top2;
+          mk[u] = __ballot_sync(0xffffffffu, keep);
+          n += __popc(mk[u]);
+        }
+        int base = 0;
+        if (lane == 0 && n) base = atomicAdd(back ? &S.nb : &S.nf, n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+        for (int u = 0; u < kStageBatch; ++u) {
+          const bool keep = (mk[u] >> lane) & 1u;
+          stage_put(S, stage_slot(keep, back, base + __popc(mk[u] & lt), lane), v[u].x, v[u].y, v[u].z);
+          base += __popc(mk[u]);
+        }
       }
-      if (seg[r]) bB += __popc(m[r]);
-      else bF += __popc(m[r]);
     }
-    // the rest of cells with more than 32 particles
-#pragma unroll 1
-    for (int r = 0; r < kRound; ++r) {
-      const int src = (m0 + r) & 31;
-      const int j0 = __shfl_sync(0xffffffffu, mine.j0, src);
-      int j1 = __shfl_sync(0xffffffffu, mine.j1, src);
-      if (m0 + r >= nmine) j1 = j0;
-      if (j1 - j0 <= 32) continue;
-      const float sx = __shfl_sync(0xffffffffu, mine.sx, src);
-      const float sy = __shfl_sync(0xffffffffu, mine.sy, src);
-      const float sz = __shfl_sync(0xffffffffu, mine.sz, src);
-      const int sg = __shfl_sync(0xffffffffu, mine.seg, src);
-      for (int jb = j0 + 32; jb < j1; jb += 32) {
-        const int j = jb + lane;
-        stage_group(S, j < j1 ? A.xs[j] : make_float4(kFar, kFar, kFar, 0.f), sx, sy, sz, sg, top2, lt);
+    // rows of more than two segments (grids narrower than the row): the rest, one by one
+    unsigned mm = __ballot_sync(0xffffffffu, more);
+    while (mm) {
+      const int src = __ffs(mm) - 1;
+      mm &= mm - 1;
+      const int rr = warp + kWarps * (m0 + (src >> 1));
+      for (int which = 2;; ++which) {
+        const RowSeg g = row_segment<FORCE>(A, S, rr, which, cx, cy, cz);
+        if (!g.valid) break;
+        for (int pb = g.p0; pb < g.p1; pb += 32) {
+          const int p = min(pb + lane, g.p1 - 1);
+          float4 v = A.xs[p];
+          const float4 sh = S.otab[g.ebase + (int)(A.cellc[p] & 1023u)];
+          v.x += sh.x;
+          v.y += sh.y;
+          v.z += sh.z;
+          const bool keep = pb + lane < g.p1 && fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)) < top2;
+          const unsigned mk = __ballot_sync(0xffffffffu, keep);
+          int base = 0;
+          if (lane == 0 && mk) base = atomicAdd(g.back ? &S.nb : &S.nf, __popc(mk));
+          base = __shfl_sync(0xffffffffu, base, 0);
+          stage_put(S, stage_slot(keep, g.back != 0, base + __popc(mk & lt), lane), v.x, v.y, v.z);
+        }
       }
     }
   }
@@ -899,6 +942,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     const Off& o = A.off[k];
     S.otab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[HALF ? 1 : 0][k]));
   }
+  __syncthreads();
+  if (tid == 0) build_rows(A, S);
   // Work items (cells of the list made by k_hood_list) come from an atomic
   // counter two ahead: thread 0 keeps the list positions in registers, so the
   // atomic's latency overlaps whole cells, and every thread prefetches into L1
@@ -915,7 +960,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     __syncthreads();
     if (tid == 0) {
       S.item = next1 < nlist ? H.list[next1] : -1;
-      S.pref = next2 < nlist ? H.list[next2] : -1;
       S.nf = 0;
       S.nb = 0;
     }
@@ -928,7 +972,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     }
     const int hs = A.cell_start[h];
     const int nh = A.cell_start[h + 1] - hs;
-    if (S.pref >= 0) prefetch_ranges(A, S, S.pref, 1 + warp + kWarps * lane);
     const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
     float cc[3];  // centre of the home cell (wrapped absolute frame), FP32
 #pragma unroll
@@ -954,13 +997,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
 #pragma unroll
     for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
     if (lane == 0) S.wmax[warp] = d;
-    // stencil entries of this warp: 1 + warp + kWarps m, lane m holding entry m
-    OffInfo mine;
-    mine.j0 = mine.j1 = mine.seg = 0;
-    mine.sx = mine.sy = mine.sz = 0.f;
-    const int kmine = 1 + warp + kWarps * lane;
-    if (kmine < A.noff) mine = off_info<FORCE>(A, S, kmine, cx, cy, cz);
-    const int nmine = (A.noff - 1 - warp + kWarps - 1) / kWarps;
     __syncthreads();
     float dmax = S.wmax[0];
 #pragma unroll
@@ -968,7 +1004,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     const float top = H.rc + dmax + H.eps;
 
     // ---- staging
-    stage_warp(A, S, mine, nmine, top * top);
+    stage_rows<FORCE>(A, S, cx, cy, cz, top * top);
     __syncthreads();
     const int nf = S.nf, nb = S.nb;
     if (nf + nb + 2 > kCap) {  // left to the dense-cell sweep
