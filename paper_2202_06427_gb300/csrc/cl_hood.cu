@@ -71,7 +71,7 @@ struct Smem {
   float4 oxy[kHome / 2]; // own cell in sorted order, same layout
   float2 ozz[kHome / 2];
   int hid[kHome];        // original index of the home particle
-  float acc[kHome][6];   // Gn and its T = 0 part
+  float acc[kHome][6];   // Gn of the neighbours across the boundary (T != 0) and of the others (T = 0)
   float4 otab[kTab];     // stencil entry: (shift x, y, z, unwrapped offset as int bits)
   unsigned short rowk[kTab + 1];  // rows of the stencil: entries [rowk[r], rowk[r + 1])
   int nrows;
@@ -92,6 +92,29 @@ __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Warp sums of N values at once (N a power of two, at most 32): at each
+// butterfly step a lane keeps the half of its values selected by its lane bit
+// and adds its partner's copy of that half, so N - 1 + (5 - log2 N) shuffles
+// replace 5 N. On return v[0] of lane l holds the sum of value l >> (5 - log2 N)
+// (every lane holds one of them).
+template <int N>
+__device__ __forceinline__ void warp_reduce_multi(float (&v)[N]) {
+  const int lane = threadIdx.x & 31;
+  int off = 16;
+#pragma unroll
+  for (int n = N; n > 1; n >>= 1, off >>= 1) {
+    const bool upper = lane & off;
+#pragma unroll
+    for (int i = 0; i < n / 2; ++i) {
+      const float send = upper ? v[i] : v[n / 2 + i];
+      const float keep = upper ? v[n / 2 + i] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+    }
+  }
+#pragma unroll
+  for (; off; off >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], off);
 }
 
 __device__ __forceinline__ float own_x(const Smem& S, int t) {
@@ -1051,69 +1074,72 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
       hood_scan<ENERGY, FORCE, false>(S.xy, S.zz, k0a, k1a, I, A.rc2, A.irc, A.irc2, a0, a1, e, nullptr);
       hood_own<ENERGY, FORCE, HALF>(S.oxy, S.ozz, ngroups, t0, t1, I, A.rc2, A.irc, A.irc2, a0, a1, e);
       if (FORCE) {
-        // T = 0 part first, then the neighbours across the boundary
-        float g6[6] = {a0.gx.x + a0.gx.y, a0.gy.x + a0.gy.y, a0.gz.x + a0.gz.y,
-                       a1.gx.x + a1.gx.y, a1.gy.x + a1.gy.y, a1.gz.x + a1.gz.y};
-        float A6[6];
+        // per-lane partial Gn: the T = 0 part from the first scan, then the
+        // part of the neighbours across the boundary; all warp-summed at once
+        float v[16];
+        v[0] = a0.gx.x + a0.gx.y;
+        v[1] = a0.gy.x + a0.gy.y;
+        v[2] = a0.gz.x + a0.gz.y;
+        v[3] = a1.gx.x + a1.gx.y;
+        v[4] = a1.gy.x + a1.gy.y;
+        v[5] = a1.gz.x + a1.gz.y;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) A6[q] = warp_sum(g6[q]);
+        for (int q = 6; q < 16; ++q) v[q] = 0.f;
         if (k1b > k0b) {
           a0.gx = a0.gy = a0.gz = a1.gx = a1.gy = a1.gz = f2(0.f);
           float2 w[6];
 #pragma unroll
           for (int q = 0; q < 6; ++q) w[q] = f2(0.f);
           hood_scan<ENERGY, FORCE, true>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, w);
+          float wv[8];
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const float t = warp_sum(w[q].x + w[q].y);
-            if (lane == 0) S.out[warp][q] += (double)t;
-          }
-          const float b6[6] = {a0.gx.x + a0.gx.y, a0.gy.x + a0.gy.y, a0.gz.x + a0.gz.y,
-                               a1.gx.x + a1.gx.y, a1.gy.x + a1.gy.y, a1.gz.x + a1.gz.y};
-#pragma unroll
-          for (int q = 0; q < 6; ++q) g6[q] = A6[q] + warp_sum(b6[q]);
-        } else {
-#pragma unroll
-          for (int q = 0; q < 6; ++q) g6[q] = A6[q];
+          for (int q = 0; q < 6; ++q) wv[q] = w[q].x + w[q].y;
+          wv[6] = wv[7] = 0.f;
+          warp_reduce_multi<8>(wv);  // lane l: value l >> 2
+          if ((lane & 3) == 0 && (lane >> 2) < 6) S.out[warp][lane >> 2] += (double)wv[0];
+          v[6] = a0.gx.x + a0.gx.y;
+          v[7] = a0.gy.x + a0.gy.y;
+          v[8] = a0.gz.x + a0.gz.y;
+          v[9] = a1.gx.x + a1.gx.y;
+          v[10] = a1.gy.x + a1.gy.y;
+          v[11] = a1.gz.x + a1.gz.y;
         }
-        if (lane == 0) {
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            S.acc[t0][q] = g6[q];
-            S.acc[t0][3 + q] = A6[q];
-          }
-          if (has1) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-              S.acc[t1][q] = g6[3 + q];
-              S.acc[t1][3 + q] = A6[3 + q];
-            }
+        if (ENERGY) v[12] = e.x + e.y;
+        warp_reduce_multi<16>(v);  // lane l: value l >> 1
+        // acc[t][0..2]: T != 0 part of Gn, acc[t][3..5]: its T = 0 part
+        const int k = lane >> 1;
+        if ((lane & 1) == 0) {
+          if (k < 12) {
+            const int kk = k < 6 ? k : k - 6;  // component of the pair (t0: 0..2, t1: 3..5)
+            const int t = kk < 3 ? t0 : t1;
+            if (kk < 3 || has1) S.acc[t][(k < 6 ? 3 : 0) + kk % 3] = v[0];
+          } else if (ENERGY && k == 12) {
+            S.out[warp][15] += (double)v[0];
           }
         }
-      } else if (k1b > k0b) {
-        hood_scan<ENERGY, FORCE, false>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, nullptr);
-      }
-      if (ENERGY) {
-        const float t = warp_sum(e.x + e.y);
-        if (lane == 0) S.out[warp][15] += (double)t;
+      } else {
+        if (k1b > k0b)
+          hood_scan<ENERGY, FORCE, false>(S.xy, S.zz, k0b, k1b, I, A.rc2, A.irc, A.irc2, a0, a1, e, nullptr);
+        if (ENERGY) {
+          const float t = warp_sum(e.x + e.y);
+          if (lane == 0) S.out[warp][15] += (double)t;
+        }
       }
     }
     __syncthreads();
     if (FORCE && warp * 32 < nh) {  // warp-uniform: every lane joins the reductions
-      float o[15];
+      float o[16];
 #pragma unroll
-      for (int q = 0; q < 15; ++q) o[q] = 0.f;
+      for (int q = 0; q < 16; ++q) o[q] = 0.f;
       if (tid < nh) {
         const int t = tid;
-        particle_terms<MODE>(o, S.hid[t], own_x(S, t), own_y(S, t), own_z(S, t), cc, S.acc[t][0], S.acc[t][1],
-                             S.acc[t][2], S.acc[t][3], S.acc[t][4], S.acc[t][5], forces, grad, g, pos);
+        particle_terms<MODE>(o, S.hid[t], own_x(S, t), own_y(S, t), own_z(S, t), cc, S.acc[t][0] + S.acc[t][3],
+                             S.acc[t][1] + S.acc[t][4], S.acc[t][2] + S.acc[t][5], S.acc[t][3], S.acc[t][4],
+                             S.acc[t][5], forces, grad, g, pos);
       }
       constexpr int NO = GRAD ? 15 : 6;
-#pragma unroll
-      for (int q = 0; q < NO; ++q) {
-        const float t = warp_sum(o[q]);
-        if (lane == 0) S.out[warp][q] += (double)t;
-      }
+      warp_reduce_multi<16>(o);  // lane l: value l >> 1
+      if ((lane & 1) == 0 && (lane >> 1) < NO) S.out[warp][lane >> 1] += (double)o[0];
     }
   }
 
