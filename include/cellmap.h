@@ -269,7 +269,7 @@ int cl_status(cl_list* cl, void* stream);
  * cl_map(CL_RED_SF_ENERGY), equal to it within the energy tolerance (relative
  * 1e-6; it runs a different sweep kernel, one thread per particle over the
  * unpruned half stencil, so the summation order differs), with every
- * intermediate buffer in one fixed device array inside the library (3.44 MB,
+ * intermediate buffer in one fixed device array inside the library (3.18 MB,
  * held by every GPU that loads the library until the process exits).
  * pos_dev: (n, dim) FP64 device positions; energy_dev: 1 FP64 device value,
  * overwritten. Limits: n <= CL_NOALLOC_MAX_N and at most

@@ -14,13 +14,10 @@ struct cl_list {
   const double* pos;
   long long ncells_alloc;
   // device workspace
-  unsigned* packed;
   int* slot;
   float4* xl;
   float4* xs;
   unsigned* cellc;
-  float4* xy2;  // shifted pairs for the packed 3D sweeps
-  float2* zz2;
   int* counts;
   int* cell_start;
   unsigned char* hflag;  // per cell: 1 when a staged sweep (neighbourhood or pair list) leaves it to a per-particle sweep
@@ -80,13 +77,10 @@ void free_cells(cl_list* c) {
 
 void free_all(cl_list* c) {
   free_cells(c);
-  cudaFree(c->packed);
   cudaFree(c->slot);
   cudaFree(c->xl);
   cudaFree(c->xs);
   cudaFree(c->cellc);
-  cudaFree(c->xy2);
-  cudaFree(c->zz2);
   cudaFree(c->meta);
   cudaFree(c->partials);
   cudaFree(c->sums);
@@ -125,8 +119,6 @@ void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
   A->xs = c->xs;
   A->cellc = c->cellc;
   A->cell_start = c->cell_start;
-  A->xy2 = c->geo.dim == 3 ? c->xy2 : nullptr;
-  A->zz2 = c->geo.dim == 3 ? c->zz2 : nullptr;
   A->n = c->n;
   A->nx = c->geo.n[0];
   A->ny = c->geo.n[1];
@@ -195,7 +187,6 @@ int run_build(cl_list* c, cudaStream_t s) {
   clk::BuildBufs b;
   b.pos = c->pos;
   b.n = c->n;
-  b.packed = c->packed;
   b.slot = c->slot;
   b.xl = c->xl;
   b.counts = c->counts;
@@ -204,8 +195,6 @@ int run_build(cl_list* c, cudaStream_t s) {
   b.meta = c->meta;
   b.xs = c->xs;
   b.cellc = c->cellc;
-  b.xy2 = c->geo.dim == 3 ? c->xy2 : nullptr;
-  b.zz2 = c->geo.dim == 3 ? c->zz2 : nullptr;
   return clk::launch_build(c->geo, b, s);
 }
 
@@ -353,13 +342,10 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   int e = CL_OK;
   size_t b = 0;
   const size_t nn = (size_t)n;
-  if (!e) e = dev_alloc(&c->packed, nn, &b);
   if (!e) e = dev_alloc(&c->slot, nn, &b);
   if (!e) e = dev_alloc(&c->xl, nn, &b);
   if (!e) e = dev_alloc(&c->xs, nn, &b);
   if (!e) e = dev_alloc(&c->cellc, nn, &b);
-  if (!e && box->dim == 3) e = dev_alloc(&c->xy2, nn, &b);
-  if (!e && box->dim == 3) e = dev_alloc(&c->zz2, nn, &b);
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);

@@ -6,13 +6,17 @@
 //                  the integer part, centred FP32 local coordinate from the
 //                  fractional part; counts particles per cell with an atomic
 //                  whose return value is the particle's slot in its cell.
-//   k_scan_*       exclusive prefix sum of the per-cell counts (reduce tiles,
-//                  scan tile sums, rescan tiles) -> cell_start[ncells + 1];
-//                  also the number of non-empty cells and the largest count.
+//   k_scan_*       exclusive prefix sum of the per-cell counts: per-tile sums
+//                  (and the number of non-empty cells and the largest count),
+//                  then per tile the sum of the tiles before it and the
+//                  rescan -> cell_start[ncells + 1].
 //   k_scatter      moves each particle's (local coordinate, index) into its
 //                  cell's range: the per-cell contiguous copy of Sec. 2.6
 //                  ("vector of lists ... an immutable copy of the particle
 //                  coordinates and index", Sec. 2.8).
+// Per particle the build reads its FP64 position once (24 B) and moves 20 B
+// through k_bin's output (local coordinate with the packed cell, slot) to the
+// sorted arrays (16 B coordinate and index, 4 B packed cell).
 //
 // FP64 is kept for the position in cell units. On this GPU FP64 issues at
 // about 1/74 of the FP32 rate, so per axis the kernel spends one FP64
@@ -33,9 +37,8 @@ struct BinArgs {
   int nx, ny, nz;
   double m[9];      // t = x M
   float g[9];       // cell edge vectors (rows)
-  unsigned* packed; // per original particle: packed cell coordinates
   int* slot;        // per original particle: position inside its cell
-  float4* xl;       // per original particle: centred local coordinate + index
+  float4* xl;       // per original particle: centred local coordinate, w = packed cell
   int* counts;      // per cell
   int* err;         // error latch
 };
@@ -102,11 +105,9 @@ __global__ void __launch_bounds__(256) k_bin(const __grid_constant__ BinArgs a) 
     o = sentinel_pos(i);
     atomicOr(a.err, kErrNonFinite);
   }
-  o.w = __int_as_float(i);
+  o.w = __uint_as_float((unsigned)c[0] | ((unsigned)c[1] << 10) | ((unsigned)c[2] << 20));
   const int lin = c[0] + a.nx * (c[1] + a.ny * c[2]);
-  const int s = atomicAdd(&a.counts[lin], 1);
-  a.packed[i] = (unsigned)c[0] | ((unsigned)c[1] << 10) | ((unsigned)c[2] << 20);
-  a.slot[i] = s;
+  a.slot[i] = atomicAdd(&a.counts[lin], 1);
   a.xl[i] = o;
 }
 
@@ -182,32 +183,23 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restr
   }
 }
 
-// One block: exclusive scan of the tile sums in place; cell_start[ncells] = total.
-template <class T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_tiles(T* __restrict__ tile_sum, int ntiles,
-                                                            T* __restrict__ cell_start, long long ncells) {
-  __shared__ T carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < ntiles; base += kScanThreads) {
-    const int t = base + threadIdx.x;
-    const T v = (t < ntiles) ? tile_sum[t] : T(0);
-    T excl;
-    block_excl_scan(v, &excl);
-    const T c0 = carry;
-    if (t < ntiles) tile_sum[t] = c0 + excl;
-    __syncthreads();
-    if (threadIdx.x == kScanThreads - 1) carry = c0 + excl + v;
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) cell_start[ncells] = carry;
-}
-
-// Per tile: rescan the counts with the tile's offset -> cell_start.
+// Per tile: the sum of the tiles before it (read straight from the tile sums,
+// so no separate pass scans them), then the rescan of the tile's counts ->
+// cell_start; the last tile also writes cell_start[ncells] = total.
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int* __restrict__ counts, long long ncells,
-                                                            const T* __restrict__ tile_off,
+                                                            const T* __restrict__ tile_sum,
                                                             T* __restrict__ cell_start) {
+  __shared__ T part[kScanThreads / 32];
+  T before = 0;
+  for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) before += tile_sum[t];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = before;
+  __syncthreads();
+  T off = 0;
+#pragma unroll
+  for (int w = 0; w < kScanThreads / 32; ++w) off += part[w];
   const long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanPer;
   int v[kScanPer];
   T s = 0;
@@ -218,37 +210,27 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int* __restri
   }
   T excl;
   block_excl_scan(s, &excl);
-  T run = tile_off[blockIdx.x] + excl;
+  T run = off + excl;
 #pragma unroll
   for (int k = 0; k < kScanPer; ++k) {
     if (base + k < ncells) cell_start[base + k] = run;
     run += v[k];
   }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) cell_start[ncells] = run;
 }
 
-__global__ void __launch_bounds__(256) k_scatter(int n, int nx, int ny, const unsigned* __restrict__ packed,
-                                                const int* __restrict__ slot, const float4* __restrict__ xl,
-                                                const int* __restrict__ cell_start, float4* __restrict__ xs,
-                                                unsigned* __restrict__ cellc) {
+__global__ void __launch_bounds__(256) k_scatter(int n, int nx, int ny, const int* __restrict__ slot,
+                                                const float4* __restrict__ xl, const int* __restrict__ cell_start,
+                                                float4* __restrict__ xs, unsigned* __restrict__ cellc) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const unsigned cc = packed[i];
+  float4 v = xl[i];
+  const unsigned cc = __float_as_uint(v.w);
   const int lin = (int)(cc & 1023u) + nx * ((int)((cc >> 10) & 1023u) + ny * (int)(cc >> 20));
   const int p = cell_start[lin] + slot[i];
-  xs[p] = xl[i];
+  v.w = __int_as_float(i);
+  xs[p] = v;
   cellc[p] = cc;
-}
-
-// Shifted pairs for the packed sweep: element j holds particles j and j+1 of
-// the sorted order, so a range of any start and parity is read two at a time.
-__global__ void __launch_bounds__(256) k_pack_pairs(int n, const float4* __restrict__ xs, float4* __restrict__ xy2,
-                                                   float2* __restrict__ zz2) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
-  const float4 a = xs[j];
-  const float4 b = (j + 1 < n) ? xs[j + 1] : sentinel_pos(n);
-  xy2[j] = make_float4(a.x, b.x, a.y, b.y);
-  zz2[j] = make_float2(a.z, b.z);
 }
 
 // ------------------------------------------------------------ host entry --
@@ -271,7 +253,7 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
     a.m[k] = std::ldexp(g.m[k], 32);  // exact: t 2^32 = x (M 2^32)
     a.g[k] = g.g[k];
   }
-  a.packed = b.packed; a.slot = b.slot; a.xl = b.xl; a.counts = b.counts; a.err = b.meta;
+  a.slot = b.slot; a.xl = b.xl; a.counts = b.counts; a.err = b.meta;
   const int blocks = (b.n + 255) / 256;
   if (b.n > 0) {
     if (g.dim == 3) {
@@ -283,11 +265,9 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
     }
   }
   k_scan_reduce<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.meta);
-  k_scan_tiles<int><<<1, kScanThreads, 0, s>>>(b.tile_sum, ntiles, b.cell_start, nc);
   k_scan_final<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
   if (b.n > 0)
-    k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.packed, b.slot, b.xl, b.cell_start, b.xs, b.cellc);
-  if (b.n > 0 && b.xy2 && b.zz2) k_pack_pairs<<<blocks, 256, 0, s>>>(b.n, b.xs, b.xy2, b.zz2);
+    k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.slot, b.xl, b.cell_start, b.xs, b.cellc);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
@@ -296,14 +276,14 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
 namespace clk {
 
 // Exclusive scan of n int counts into 64-bit start[n + 1] (start[n] = total),
-// with the same three kernels as the cell offsets; meta receives the number of
+// with the same two kernels as the cell offsets; meta receives the number of
 // non-zero counts and the largest one. The pair list's offsets and total are
 // 64-bit: a list may hold more than 2^31 pairs.
 int launch_scan64(const int* counts, long long n, long long* tile_sum, long long* start, int* meta, cudaStream_t s) {
   const int ntiles = scan_tiles_for(n);
   if (cudaMemsetAsync(meta + 1, 0, sizeof(int) * 2, s) != cudaSuccess) return CL_ERR_CUDA;
+  if (ntiles == 0) return cudaMemsetAsync(start, 0, sizeof(long long), s) == cudaSuccess ? CL_OK : CL_ERR_CUDA;
   k_scan_reduce<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, meta);
-  k_scan_tiles<long long><<<1, kScanThreads, 0, s>>>(tile_sum, ntiles, start, n);
   k_scan_final<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, start);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }

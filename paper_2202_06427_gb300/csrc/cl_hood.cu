@@ -577,8 +577,8 @@ __device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs&
   {
     const int c = cx + A.nx * (cy + A.ny * cz);
     const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
-    if (FORCE) scan_pairs(A.xy2, A.zz2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
-    scan_pairs(A.xy2, A.zz2, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    if (FORCE) scan_pairs(A.xs, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    scan_pairs(A.xs, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
     red.cell_done(acc);
     ncand += (unsigned long long)(FORCE ? s1 - s0 - 1 : s1 - p - 1);
   }
@@ -592,7 +592,7 @@ __device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs&
                  (cz + oz >= A.nz);
     }
     const int j0 = A.cell_start[c], j1 = A.cell_start[c + 1];
-    scan_pairs(A.xy2, A.zz2, j0, j1, o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2, red, acc);
+    scan_pairs(A.xs, j0, j1, o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2, red, acc);
     red.cell_done(acc);
     ncand += (unsigned long long)(j1 - j0);
   }

@@ -83,8 +83,6 @@ struct SweepArgs {
   const float4* xs;
   const unsigned* cellc;
   const int* cell_start;
-  const float4* xy2;    // shifted pairs (x_j, x_j+1, y_j, y_j+1), 3D; null: unpaired sweep
-  const float2* zz2;    // (z_j, z_j+1)
   int n;
   int nx, ny, nz;
   float rc2, irc, irc2;
@@ -107,17 +105,14 @@ namespace clk {
 struct BuildBufs {
   const double* pos;
   int n;
-  unsigned* packed;
-  int* slot;
-  float4* xl;
+  int* slot;    // per original particle: position inside its cell
+  float4* xl;   // per original particle: centred local coordinate, w = packed cell (cx | cy << 10 | cz << 20)
   int* counts;
   int* cell_start;
   int* tile_sum;
   int* meta;  // [0] error latch, [1] non-empty cells, [2] max occupancy
   float4* xs;
   unsigned* cellc;
-  float4* xy2;  // optional (null: not built): shifted pairs of xs for the packed 3D sweep
-  float2* zz2;
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);

@@ -11,7 +11,7 @@
 // sorted particles, per-cell counts and offsets, per-CTA partial sums) lives
 // in one file-scope __device__ array of fixed size, carved into 256-byte
 // aligned pieces. Each GPU that loads the library holds this array
-// (3,441,920 bytes) until the process exits. Host code only ever passes the
+// (3,179,776 bytes) until the process exits. Host code only ever passes the
 // array's device address, obtained once per device with cudaGetSymbolAddress;
 // the host-side name of the array is a stand-in, never a device pointer.
 //
@@ -33,8 +33,7 @@ constexpr int kMaxDevices = 64;
 constexpr size_t up256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffXl = 0;
 constexpr size_t kOffXs = kOffXl + up256(16 * kMaxN);
-constexpr size_t kOffPacked = kOffXs + up256(16 * kMaxN);
-constexpr size_t kOffSlot = kOffPacked + up256(4 * kMaxN);
+constexpr size_t kOffSlot = kOffXs + up256(16 * kMaxN);
 constexpr size_t kOffCellc = kOffSlot + up256(4 * kMaxN);
 constexpr size_t kOffCounts = kOffCellc + up256(4 * kMaxN);
 constexpr size_t kOffStart = kOffCounts + up256(4 * kMaxCells);
@@ -43,6 +42,7 @@ constexpr size_t kOffMeta = kOffTiles + up256(4 * ((kMaxCells + 2047) / 2048 + 1
 constexpr size_t kOffPartials = kOffMeta + 256;
 constexpr size_t kOffSums = kOffPartials + up256(8 * 16 * ((kMaxN + 255) / 256 + 1));
 constexpr size_t kScratchBytes = kOffSums + 256;
+static_assert(kScratchBytes == 3179776, "the workspace size stated in cellmap.h");
 
 }  // namespace
 
@@ -119,20 +119,15 @@ extern "C" int cl_energy_noalloc(const double* pos_dev, long long n, const cl_bo
   b.n = (int)n;
   b.xl = reinterpret_cast<float4*>(base + kOffXl);
   b.xs = reinterpret_cast<float4*>(base + kOffXs);
-  b.packed = reinterpret_cast<unsigned*>(base + kOffPacked);
   b.slot = reinterpret_cast<int*>(base + kOffSlot);
   b.cellc = reinterpret_cast<unsigned*>(base + kOffCellc);
   b.counts = reinterpret_cast<int*>(base + kOffCounts);
   b.cell_start = reinterpret_cast<int*>(base + kOffStart);
   b.tile_sum = reinterpret_cast<int*>(base + kOffTiles);
   b.meta = reinterpret_cast<int*>(base + kOffMeta);
-  b.xy2 = nullptr;  // unpaired sweep: no room for the shifted pairs in the fixed workspace
-  b.zz2 = nullptr;
   if (cudaMemsetAsync(b.meta, 0, 4 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if ((e = clk::launch_build(g, b, s))) return e;
   A.xs = b.xs;
-  A.xy2 = nullptr;
-  A.zz2 = nullptr;
   A.cellc = b.cellc;
   A.cell_start = b.cell_start;
   A.n = (int)n;

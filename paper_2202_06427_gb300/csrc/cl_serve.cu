@@ -288,7 +288,7 @@ size_t request_bytes(const Req& q) {
   const size_t n = (size_t)q.r.n, d = (size_t)q.geo.dim, C = (size_t)q.geo.ncells;
   const size_t tiles = (size_t)clk::scan_tiles_for((long long)C);
   const size_t items = n > 0 ? (n + clk::kServeThreads - 1) / clk::kServeThreads : 1;
-  size_t b = up(n * d * 8) + 2 * up(n * 16) + 3 * up(n * 4) + up(C * 4) + up((C + 1) * 4) + up(tiles * 4 + 4) +
+  size_t b = up(n * d * 8) + 2 * up(n * 16) + 2 * up(n * 4) + up(C * 4) + up((C + 1) * 4) + up(tiles * 4 + 4) +
              up(16) + up(q.off.size() * sizeof(clk::Off)) + up(items * 7 * 8) + up(8) + up(72);
   if (q.r.task == CL_TASK_FORCES) b += up(n * d * 4);
   if (q.r.task == CL_TASK_HIST) b += up((size_t)q.r.nbins * 8);
@@ -338,15 +338,12 @@ bool cl_server::admit_one(Req* q) {
   B.n = (int)n;
   B.xl = reinterpret_cast<float4*>(take(n * 16));
   B.xs = reinterpret_cast<float4*>(take(n * 16));
-  B.packed = reinterpret_cast<unsigned*>(take(n * 4));
   B.slot = reinterpret_cast<int*>(take(n * 4));
   B.cellc = reinterpret_cast<unsigned*>(take(n * 4));
   B.counts = reinterpret_cast<int*>(take(C * 4));
   B.cell_start = reinterpret_cast<int*>(take((C + 1) * 4));
   B.tile_sum = reinterpret_cast<int*>(take((size_t)clk::scan_tiles_for((long long)C) * 4 + 4));
   B.meta = reinterpret_cast<int*>(take(16));
-  B.xy2 = nullptr;  // the batched sweep reads the unpaired layout
-  B.zz2 = nullptr;
   q->d_off = reinterpret_cast<clk::Off*>(take(q->off.size() * sizeof(clk::Off)));
   q->nitems = n > 0 ? (int)((n + clk::kServeThreads - 1) / clk::kServeThreads) : 0;
   q->d_partials = reinterpret_cast<double*>(take((size_t)std::max(q->nitems, 1) * 7 * 8));

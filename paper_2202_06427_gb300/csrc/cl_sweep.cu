@@ -340,8 +340,7 @@ int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, doubl
   if (A.n > 0) {
     if (dim == 3) {
       if (kind == 0) k_sweep_scalar<3, 0><<<nb, 256, 0, s>>>(A, partials);
-      else if (A.xy2 && A.zz2) k_sweep2_energy<<<nb, 256, 0, s>>>(A, partials);
-      else k_sweep_scalar<3, 1><<<nb, 256, 0, s>>>(A, partials);
+      else k_sweep2_energy<<<nb, 256, 0, s>>>(A, partials);
     } else {
       if (kind == 0) k_sweep_scalar<2, 0><<<nb, 256, 0, s>>>(A, partials);
       else k_sweep_scalar<2, 1><<<nb, 256, 0, s>>>(A, partials);
@@ -370,12 +369,9 @@ int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, floa
   const int NW = dim == 3 ? kVirN3 : kVirN2;
   const int NV = mode == 0 ? 1 + NW : NW + dim * dim;
   if (A.n > 0) {
-    if (dim == 3 && A.xy2 && A.zz2) {
+    if (dim == 3) {
       if (mode == 0) k_sweep2_force<0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
       else k_sweep2_force<1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
-    } else if (dim == 3) {
-      if (mode == 0) k_sweep_force<3, 0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
-      else k_sweep_force<3, 1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
     } else {
       if (mode == 0) k_sweep_force<2, 0><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);
       else k_sweep_force<2, 1><<<nb, 256, 0, s>>>(A, forces, grad, gE, pos, partials);

@@ -292,20 +292,20 @@ __device__ __forceinline__ void cell_done_of(const Red2Force<E>& r, typename Red
   r.cell_done(a, sx, sy, sz);
 }
 
-// Candidates j in [j0, j1) against one particle, two at a time. (sx, sy, sz)
-// = S_o - x_i, so that the displacement is x_j + S_o - x_i = x_j + s.
+// Candidates j in [j0, j1) against one particle, two at a time (the second
+// read is clamped to the range and masked). (sx, sy, sz) = S_o - x_i, so that
+// the displacement is x_j + S_o - x_i = x_j + s.
 template <class R, class Acc>
-__device__ __forceinline__ void scan_pairs(const float4* __restrict__ xy2, const float2* __restrict__ zz2, int j0,
-                                           int j1, float sx, float sy, float sz, float rc2, const R& red,
-                                           Acc& acc) {
+__device__ __forceinline__ void scan_pairs(const float4* __restrict__ xs, int j0, int j1, float sx, float sy,
+                                           float sz, float rc2, const R& red, Acc& acc) {
   const float2 s2x = f2(sx), s2y = f2(sy), s2z = f2(sz);
 #pragma unroll 2
   for (int j = j0; j < j1; j += 2) {
-    const float4 q = __ldg(&xy2[j]);
-    const float2 z = __ldg(&zz2[j]);
-    const float2 dx = __fadd2_rn(make_float2(q.x, q.y), s2x);
-    const float2 dy = __fadd2_rn(make_float2(q.z, q.w), s2y);
-    const float2 dz = __fadd2_rn(z, s2z);
+    const float4 a = __ldg(&xs[j]);
+    const float4 b = __ldg(&xs[min(j + 1, j1 - 1)]);
+    const float2 dx = __fadd2_rn(make_float2(a.x, b.x), s2x);
+    const float2 dy = __fadd2_rn(make_float2(a.y, b.y), s2y);
+    const float2 dz = __fadd2_rn(make_float2(a.z, b.z), s2z);
     float2 d2 = __fmul2_rn(dz, dz);
     d2 = __ffma2_rn(dy, dy, d2);
     d2 = __ffma2_rn(dx, dx, d2);
@@ -338,14 +338,14 @@ __device__ __forceinline__ bool sweep_particle2(const SweepArgs& A, const R& red
   {
     const int c = cx + A.nx * (cy + A.ny * cz);
     const int s0 = A.cell_start[c], s1 = A.cell_start[c + 1];
-    if (R::kFull) scan_pairs(A.xy2, A.zz2, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
-    scan_pairs(A.xy2, A.zz2, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    if (R::kFull) scan_pairs(A.xs, s0, p, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
+    scan_pairs(A.xs, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
     cell_done_of(red, acc, 0.f, 0.f, 0.f);
   }
   for (int k = 1; k < A.noff; ++k) {
     const int c = stencil_cell(A, k, cx, cy, cz);
     const Off& o = A.off[k];
-    scan_pairs(A.xy2, A.zz2, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
+    scan_pairs(A.xs, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
                red, acc);
     cell_done_of(red, acc, o.sx, o.sy, o.sz);
   }
