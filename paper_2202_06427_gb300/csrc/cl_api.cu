@@ -27,7 +27,8 @@ struct cl_list {
   int* meta;
   double* partials;
   double* sums;
-  int* work;  // work counter of the persistent neighbourhood sweep
+  int* work;  // work counters of the persistent neighbourhood sweeps
+  float4* hforce;  // per sorted particle: forces accumulated by the half-shell sweep (kept zero between launches)
   unsigned long long* u64;
   // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
   int* pl_count;
@@ -85,6 +86,7 @@ void free_all(cl_list* c) {
   cudaFree(c->partials);
   cudaFree(c->sums);
   cudaFree(c->work);
+  cudaFree(c->hforce);
   cudaFree(c->u64);
   cudaFree(c->d_off_half);
   cudaFree(c->d_off_full);
@@ -173,6 +175,9 @@ int set_geometry(cl_list* c, const cl_box* box) {
   c->hood->flag = c->hflag;
   c->hood->list = c->hlist;
   c->hood->dense = c->hdense;
+  c->hood->hforce = c->hforce;
+  c->hood->xl = c->xl;
+  c->hood->slot = c->slot;
   delete hood;
   c->half->noff = nh;
   c->full->noff = nf;
@@ -349,8 +354,10 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
-  if (!e) e = dev_alloc(&c->work, 6, &b);  // [0] work counter, [1] list length, [2..3] candidate counter,
-                                           // [4] dense cells, [5] their work counter
+  if (!e) e = dev_alloc(&c->work, 8, &b);  // [0] work counter, [1] list length, [2..3] candidate counter,
+                                           // [4] dense cells, [5] their work counter, [6] mixed flag
+  if (!e && box->dim == 3) e = dev_alloc(&c->hforce, nn, &b);
+  if (!e && box->dim == 3 && nn > 0 && cudaMemset(c->hforce, 0, sizeof(float4) * nn) != cudaSuccess) e = CL_ERR_CUDA;
   if (!e) e = dev_alloc(&c->u64, 8, &b);
   if (!e) e = dev_alloc(&c->d_off_half, (size_t)clk::kMaxOff, &b);
   if (!e) e = dev_alloc(&c->d_off_full, (size_t)clk::kMaxOff, &b);
@@ -393,13 +400,13 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
     case CL_RED_SF_ENERGY:
       if (!r->energy) return CL_ERR_INVALID_ARG;
       if (dim == 3 && c->n > 0)
-        return clk::launch_hood(*c->half, *c->hood, c->work, 2, c->geo.hinv, nullptr, nullptr, nullptr, nullptr,
+        return clk::launch_hood(*c->half, nullptr, *c->hood, c->work, 2, c->geo.hinv, nullptr, nullptr, nullptr, nullptr,
                                 c->partials, hood_cap(c), c->sums, r->energy, nullptr, nullptr, s);
       return clk::launch_scalar(*c->half, dim, 1, c->partials, c->sums, r->energy, s);
     case CL_RED_SF_ENERGY_FORCES_VIRIAL:
       if (!r->forces && c->n > 0) return CL_ERR_INVALID_ARG;
       if (dim == 3 && c->n > 0)
-        return clk::launch_hood(*c->full, *c->hood, c->work, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr,
+        return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr,
                                 c->partials, hood_cap(c), c->sums, r->energy, r->virial, nullptr, s);
       return clk::launch_force(*c->full, dim, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr, c->partials,
                                c->sums, r->energy, r->virial, nullptr, s);
@@ -420,7 +427,7 @@ int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_p
   if (!cc || !grad_energy_dev || (cc->n > 0 && !grad_pos_dev)) return CL_ERR_INVALID_ARG;
   cl_list* c = const_cast<cl_list*>(cc);
   if (c->geo.dim == 3 && c->n > 0)
-    return clk::launch_hood(*c->full, *c->hood, c->work, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev,
+    return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev,
                             c->pos, c->partials, hood_cap(c), c->sums, nullptr, virial_dev, grad_box_dev,
                             (cudaStream_t)stream);
   return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev, c->pos,
@@ -433,7 +440,7 @@ int cl_energy_grad(const cl_list* cc, const double* scale_dev, double* energy_de
   cl_list* c = const_cast<cl_list*>(cc);
   cudaStream_t s = (cudaStream_t)stream;
   if (c->geo.dim == 3 && c->n > 0)
-    return clk::launch_hood(*c->full, *c->hood, c->work, 3, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
+    return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 3, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
                             c->partials, hood_cap(c), c->sums, energy_dev, virial_dev, grad_box_dev, s);
   // 2D (and the empty list): the energy sweep, then the backward sweep
   int e = clk::launch_scalar(*c->half, c->geo.dim, 1, c->partials, c->sums, energy_dev, s);

@@ -38,6 +38,7 @@
 // thread per home particle against windows of the staged neighbourhood. All
 // three compute the same per-particle virial share and write per-CTA partials
 // to one buffer.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -53,7 +54,7 @@ constexpr int kHome = 128;             // home particles of the fast path (one p
 constexpr int kMinHome = 8;            // fewer home particles: the per-particle companion is cheaper
 constexpr int kCap = 2560;             // staged neighbour entries (even)
 constexpr int kTab = 1 + kWarps * 32;  // stencil entries the fast path takes (32 per warp)
-constexpr int kRound = 8;              // neighbour cells a warp loads before using them
+constexpr int kHCap = 1536;            // staged entries of the half-shell path
 // Padding entries sit at (kFar, kFar, kFar) and a missing second home particle
 // of a group at -kFar: far from everything and from each other (the stand-ins
 // of non-finite inputs lie within [1e15, 2e15) per axis), with squared
@@ -617,19 +618,68 @@ __device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs&
 // stencil larger than the table) are flagged 1 for the per-particle companion.
 // A cell whose staged neighbourhood overflows is moved to the dense list by
 // the sweep itself.
+// Particles in the neighbour cells (cx + ox, cy + oy, cz + oz), ox0 <= ox <= ox1
+// (wrapped): one contiguous range unless the run crosses the box edge in x.
+__device__ __forceinline__ int run_count(const int* __restrict__ cell_start, int nx, int ny, int nz, int cx, int cy,
+                                         int cz, int ox0, int ox1, int oy, int oz) {
+  const int y2 = ((cy + oy) % ny + ny) % ny, z2 = ((cz + oz) % nz + nz) % nz;
+  const int row = nx * (y2 + ny * z2);
+  const int xa = cx + ox0, xb = cx + ox1;
+  if (xa >= 0 && xb < nx) return cell_start[row + xb + 1] - cell_start[row + xa];
+  int n = 0;
+  for (int x = xa; x <= xb; ++x) {
+    const int xw = (x % nx + nx) % nx;
+    n += cell_start[row + xw + 1] - cell_start[row + xw];
+  }
+  return n;
+}
+
+// Work lists: cells with kMinHome..kHome particles (and a stencil that fits
+// the table) go to the neighbourhood sweep (list, work[1] of them); cells with
+// more than kHome particles are flagged 2 and listed for the dense-cell sweep
+// (dense, *ndense of them); the other non-empty cells (fewer particles, or a
+// stencil larger than the table) are flagged 1 for the per-particle companion.
+// A cell whose staged neighbourhood overflows is moved to the dense list by
+// the sweep itself. With half != 0 (the half-shell path is tried), *mixed is
+// set when some non-empty cell is not on the list or holds more than kHCap
+// particles in its half stencil's cells (opk_half, noff_half entries), so
+// that the full-shell kernels take the launch instead.
 __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_start, int ncells, int noff,
                                                    int* __restrict__ work, int* __restrict__ list,
                                                    unsigned char* __restrict__ flag, int* __restrict__ dense,
-                                                   int* __restrict__ ndense) {
+                                                   int* __restrict__ ndense, const __grid_constant__ HoodArgs H,
+                                                   int noff_half, int nx, int ny, int nz) {
+  const int half = H.half;
+  const int* opk_half = H.opk[1];
+  int* mixed = H.mixed;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-  bool take = false, big = false;
+  bool take = false, big = false, mix = false;
   if (h < ncells) {
     const int nh = cell_start[h + 1] - cell_start[h];
     take = nh >= kMinHome && nh <= kHome && noff <= kTab;
     big = nh > kHome;
     flag[h] = (nh > 0 && !take) ? (big ? 2 : 1) : 0;
+    mix = nh > 0 && !take;
+    if (half && take) {
+      const int cx = h % nx, cy = (h / nx) % ny, cz = h / (nx * ny);
+      int cnt = 0, r0 = 0, px = 0, py = 0, pz = 0;
+      for (int k = 1; k <= noff_half; ++k) {
+        int ox = 0, oy = 0, oz = 0;
+        if (k < noff_half) unpack_off(opk_half[k], ox, oy, oz);
+        if (k > 1 && (k == noff_half || oy != py || oz != pz || ox != px + 1)) {
+          cnt += run_count(cell_start, nx, ny, nz, cx, cy, cz, r0, px, py, pz);
+          r0 = ox;
+        }
+        if (k == 1) r0 = ox;
+        px = ox;
+        py = oy;
+        pz = oz;
+      }
+      mix = mix || cnt > kHCap;
+    }
   }
+  if (__any_sync(0xffffffffu, mix) && (threadIdx.x & 31) == 0) atomicOr(mixed, 1);
   const unsigned m = __ballot_sync(0xffffffffu, take), mb = __ballot_sync(0xffffffffu, big);
   int base = 0, bbase = 0;
   if ((threadIdx.x & 31) == 0) {
@@ -952,6 +1002,10 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
                                                       double* __restrict__ partials) {
   constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1, HALF = MODE == 2;
   constexpr bool GRAD = MODE == 1 || MODE == 3;
+  if (H.half && !*H.mixed) {  // the half-shell path took this launch
+    if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
+    return;
+  }
   extern __shared__ __align__(16) unsigned char smraw[];
   Smem& S = *reinterpret_cast<Smem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1172,6 +1226,523 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   }
 }
 
+// ------------------------------------------------------------ half shell
+// Each pair-image once (Sec. 2.8: "only half of the neighboring cells are
+// evaluated"): one CTA per home cell stages the particles of the half
+// stencil's cells within rc + d_max of the centre, and sweeps them
+// entry-major: a warp holds 64 staged entries (two per lane) and runs over
+// the home particles four at a time, so the force on each entry accumulates
+// in the lane's registers and leaves the CTA as one vector atomic per entry,
+// while the forces on the four home particles are warp-summed per step into
+// shared memory and leave as one vector atomic per home particle. Forces thus
+// land in a per-sorted-particle FP32 buffer, from which k_half_finish writes
+// the outputs and the per-particle virial and box-gradient shares.
+//
+// Virial. With X the wrapped absolute positions, a pair-image (h, e) with
+// lattice image T of the entry has r = X_e + T.H - X_h, so over all pairs
+//   sum fsn r (x) r = sum_p X_p (x) F_p + sum_pairs (T.H) (x) f_e,
+// f_e = fsn r the force on the entry: the first sum is per particle
+// (k_half_finish), the second is added here for the entries across the
+// boundary (T != 0) from their accumulated forces. In the partials layout of
+// the other sweeps (minus the sum over ordered pairs) this is -2 times it.
+//
+// The path is taken only when every non-empty cell is a fast-path cell whose
+// half neighbourhood fits kHCap (k_hood_list checks, and sets *mixed
+// otherwise); then no pair is left to the full-shell kernels, which exit, and
+// vice versa.
+
+struct HalfSmem {
+  float4 ent[kHCap + 32];  // (x, y, z in the home frame, sorted position as int bits); 32 trash entries
+  int img[kHCap];          // lattice image of the T != 0 entries, (tx, ty, tz) as signed bytes
+  float4 home[kHome + 4];  // home particles (-x, -y, -z, sorted position), padded by far entries
+  float4 own[kHome];       // the same with (x, y, z): the own cell's entries
+  float hg[kHome][3];      // per home particle: sum of fsn r over its entries
+  float4 otab[kTab];       // half stencil: (shift x, y, z, unwrapped offset as int bits)
+  unsigned short rowk[kTab + 1];
+  int nrows;
+  float wmax[kWarps];
+  int nf, nb, item, next;
+  unsigned long long ncand;
+  double out[kWarps][16];
+};
+
+// Row segment of the half stencil (the same walk as row_segment) with the
+// segment's lattice image packed as bytes.
+template <int DUMMY>
+__device__ __forceinline__ RowSeg half_segment(const SweepArgs& A, const HalfSmem& S, int r, int which, int cx, int cy,
+                                               int cz, int& image) {
+  RowSeg g;
+  g.p0 = g.p1 = g.ebase = g.back = 0;
+  g.valid = false;
+  image = 0;
+  const int e0 = S.rowk[r], e1 = S.rowk[r + 1];
+  int ox0, oy, oz, ox1, t1, t2;
+  unpack_off(__float_as_int(S.otab[e0].w), ox0, oy, oz);
+  unpack_off(__float_as_int(S.otab[e1 - 1].w), ox1, t1, t2);
+  int y2 = cy + oy, z2 = cz + oz;
+  const int ty = floordiv_i(y2, A.ny), tz = floordiv_i(z2, A.nz);
+  y2 -= ty * A.ny;
+  z2 -= tz * A.nz;
+  int ox = ox0;
+  for (int k = 0; ox <= ox1; ++k) {
+    const int x = cx + ox;
+    const int tx = floordiv_i(x, A.nx);
+    const int xw = x - tx * A.nx;
+    const int len = min(ox1 - ox + 1, A.nx - xw);
+    if (k == which) {
+      const int ca = xw + A.nx * (y2 + A.ny * z2);
+      g.p0 = A.cell_start[ca];
+      g.p1 = A.cell_start[ca + len];
+      g.ebase = e0 - ox0 + tx * A.nx - cx;
+      g.back = (tx | ty | tz) != 0 ? 1 : 0;
+      g.valid = true;
+      image = (tx & 255) | ((ty & 255) << 8) | ((tz & 255) << 16);
+      break;
+    }
+    ox += len;
+  }
+  return g;
+}
+
+__device__ __forceinline__ int half_slot(bool keep, bool back, int r, int lane) {
+  const int e = back ? kHCap - 1 - r : r;
+  return (keep && e >= 0 && e < kHCap) ? e : kHCap + lane;
+}
+
+// Staging of the half neighbourhood: the row walk of stage_rows, writing
+// (x', sorted position) entries and the image of the T != 0 ones.
+__device__ __forceinline__ void half_stage(const SweepArgs& A, HalfSmem& S, int cx, int cy, int cz, float top2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nrows = S.nrows;
+  const int nmine = nrows > warp ? (nrows - 1 - warp) / kWarps + 1 : 0;
+  for (int m0 = 0; m0 < nmine; m0 += 16) {
+    const int m = m0 + (lane >> 1);
+    RowSeg sg;
+    sg.p0 = sg.p1 = sg.ebase = sg.back = 0;
+    int img = 0;
+    bool more = false;
+    if (m < nmine) {
+      const int r = warp + kWarps * m;
+      sg = half_segment<0>(A, S, r, lane & 1, cx, cy, cz, img);
+      if (!sg.valid) sg.p0 = sg.p1 = 0;
+      int dummy;
+      if (lane & 1) more = half_segment<0>(A, S, r, 2, cx, cy, cz, dummy).valid;
+    }
+    unsigned live = __ballot_sync(0xffffffffu, sg.p1 > sg.p0);
+    unsigned mm = __ballot_sync(0xffffffffu, more);
+    for (int which = 2;; ++which) {
+      while (live) {
+        const int src = __ffs(live) - 1;
+        live &= live - 1;
+        const int p0 = __shfl_sync(0xffffffffu, sg.p0, src);
+        const int p1 = __shfl_sync(0xffffffffu, sg.p1, src);
+        const int eb = __shfl_sync(0xffffffffu, sg.ebase, src);
+        const bool back = __shfl_sync(0xffffffffu, sg.back, src) != 0;
+        const int im = __shfl_sync(0xffffffffu, img, src);
+        for (int pb = p0; pb < p1; pb += 32 * kStageBatch) {
+          float4 v[kStageBatch];
+          unsigned c[kStageBatch];
+#pragma unroll
+          for (int u = 0; u < kStageBatch; ++u) {
+            const int p = min(pb + 32 * u + lane, p1 - 1);
+            v[u] = A.xs[p];
+            c[u] = A.cellc[p];
+          }
+          unsigned mk[kStageBatch];
+          int n = 0;
+#pragma unroll
+          for (int u = 0; u < kStageBatch; ++u) {
+            const float4 sh = S.otab[eb + (int)(c[u] & 1023u)];
+            v[u].x += sh.x;
+            v[u].y += sh.y;
+            v[u].z += sh.z;
+            v[u].w = __int_as_float(min(pb + 32 * u + lane, p1 - 1));
+            const bool keep = pb + 32 * u + lane < p1 &&
+                              fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, v[u].z * v[u].z)) < top2;
+            mk[u] = __ballot_sync(0xffffffffu, keep);
+            n += __popc(mk[u]);
+          }
+          int base = 0;
+          if (lane == 0 && n) base = atomicAdd(back ? &S.nb : &S.nf, n);
+          base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+          for (int u = 0; u < kStageBatch; ++u) {
+            const bool keep = (mk[u] >> lane) & 1u;
+            const int e = half_slot(keep, back, base + __popc(mk[u] & lt), lane);
+            S.ent[e] = v[u];
+            if (back && e < kHCap) S.img[e] = im;
+            base += __popc(mk[u]);
+          }
+        }
+      }
+      // rows of more than two segments (grids narrower than the row): segment `which` of each
+      if (!mm) break;
+      live = 0;
+      unsigned still = 0;
+      if (m < nmine && ((mm >> lane) & 1u)) {
+        const int r = warp + kWarps * m;
+        sg = half_segment<0>(A, S, r, which, cx, cy, cz, img);
+        if (!sg.valid) sg.p0 = sg.p1 = 0;
+        int dummy;
+        still = half_segment<0>(A, S, r, which + 1, cx, cy, cz, dummy).valid ? 1u : 0u;
+      } else {
+        sg.p0 = sg.p1 = 0;
+      }
+      live = __ballot_sync(0xffffffffu, sg.p1 > sg.p0);
+      mm = __ballot_sync(0xffffffffu, still != 0);
+      if (!live && !mm) break;
+    }
+  }
+}
+
+constexpr int kEnt = 4;             // staged entries per lane in a chunk of the half-shell sweep
+constexpr int kChunk = 32 * kEnt;   // entries per chunk
+
+// The staged entries of a cell taken as one sequence: the T = 0 entries
+// [0, nf), then the T != 0 entries (stored at the back of the buffer), then
+// the home particles themselves (own cell). Position j of the sequence: its
+// entry, and (own cell) its home index, else a large value.
+struct SeqInfo {
+  int nf, nb, nh;
+};
+__device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q, int j, int& own, bool far_up) {
+  own = 0x7fffffff;
+  if (j < q.nf) return S.ent[j];
+  if (j < q.nf + q.nb) return S.ent[kHCap - q.nb + (j - q.nf)];
+  if (j < q.nf + q.nb + q.nh) {
+    own = j - q.nf - q.nb;
+    return S.own[own];
+  }
+  return far_up ? make_float4(kFar, kFar, kFar, 0.f) : make_float4(-kFar, -kFar, -kFar, 0.f);
+}
+
+// One chunk of kChunk positions of the sequence (kEnt per lane: base + lane
+// + 32 u) against every home particle, four home particles per step. MASK
+// (the chunk holds own-cell positions): a pair with an own-cell entry counts
+// when the entry comes after the home particle. The lane's entries' forces
+// (sum of fsn r, r = entry - home) accumulate in jx, jy, jz (pair k: positions
+// u = 2k, 2k + 1); each home particle's sum of fsn r over the chunk is
+// warp-summed per step into S.hg.
+template <bool MASK>
+__device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int base, int nh, float rc2, float irc,
+                                           float irc2, float2 (&jx)[kEnt / 2], float2 (&jy)[kEnt / 2],
+                                           float2 (&jz)[kEnt / 2], float2& e) {
+  const int lane = threadIdx.x & 31;
+  float2 qx[kEnt / 2], qy[kEnt / 2], qz[kEnt / 2];
+  int own[kEnt];
+#pragma unroll
+  for (int k = 0; k < kEnt / 2; ++k) {
+    const float4 a = seq_entry(S, sq, base + lane + 64 * k, own[2 * k], true);
+    const float4 b = seq_entry(S, sq, base + lane + 64 * k + 32, own[2 * k + 1], false);
+    qx[k] = make_float2(a.x, b.x);
+    qy[k] = make_float2(a.y, b.y);
+    qz[k] = make_float2(a.z, b.z);
+    jx[k] = jy[k] = jz[k] = f2(0.f);
+  }
+  for (int h0 = 0; h0 < nh; h0 += 4) {
+    float v[16];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 hp = S.home[h0 + u];  // broadcast; negated coordinates, padded past nh by far entries
+      float2 gx = f2(0.f), gy = f2(0.f), gz = f2(0.f);
+#pragma unroll
+      for (int k = 0; k < kEnt / 2; ++k) {
+        const float2 dx = __fadd2_rn(qx[k], f2(hp.x)), dy = __fadd2_rn(qy[k], f2(hp.y)),
+                     dz = __fadd2_rn(qz[k], f2(hp.z));
+        float2 d2 = __fmul2_rn(dz, dz);
+        d2 = __ffma2_rn(dy, dy, d2);
+        d2 = __ffma2_rn(dx, dx, d2);
+        float2 y = make_float2(rsqrtf(d2.x), rsqrtf(d2.y));
+        if (MASK) {
+          y.x = (own[2 * k] > h0 + u && d2.x < rc2) ? y.x : 0.f;
+          y.y = (own[2 * k + 1] > h0 + u && d2.y < rc2) ? y.y : 0.f;
+        }
+        float2 fsn = __fmul2_rn(__ffma2_rn(y, y, f2(-irc2)), y);
+        fsn.x = fmaxf(fsn.x, 0.f);
+        fsn.y = fmaxf(fsn.y, 0.f);
+        jx[k] = __ffma2_rn(fsn, dx, jx[k]);
+        jy[k] = __ffma2_rn(fsn, dy, jy[k]);
+        jz[k] = __ffma2_rn(fsn, dz, jz[k]);
+        gx = __ffma2_rn(fsn, dx, gx);
+        gy = __ffma2_rn(fsn, dy, gy);
+        gz = __ffma2_rn(fsn, dz, gz);
+        float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-irc), f2(1.0f));
+        t.x = fmaxf(t.x, 0.f);
+        t.y = fmaxf(t.y, 0.f);
+        e = __ffma2_rn(__fmul2_rn(t, t), y, e);
+      }
+      v[3 * u + 0] = gx.x + gx.y;
+      v[3 * u + 1] = gy.x + gy.y;
+      v[3 * u + 2] = gz.x + gz.y;
+    }
+    v[12] = v[13] = v[14] = v[15] = 0.f;
+    warp_reduce_multi<16>(v);  // lane l: value l >> 1
+    const int k = lane >> 1;
+    if ((lane & 1) == 0 && k < 12 && h0 + k / 3 < nh) atomicAdd(&S.hg[h0 + k / 3][k % 3], v[0]);
+  }
+}
+
+// Adds the accumulated force of sequence position j to its particle (vector
+// atomic) and, for an entry across the boundary, the symmetric part of
+// (T.H) (x) f to the lane's virial sums.
+__device__ __forceinline__ void half_flush(const HoodArgs& H, const HalfSmem& S, const SeqInfo& q, int j, float fx,
+                                           float fy, float fz, float* wv) {
+  if (j >= q.nf + q.nb + q.nh || (fx == 0.f && fy == 0.f && fz == 0.f)) return;
+  const bool back = j >= q.nf && j < q.nf + q.nb;
+  const int idx = j < q.nf ? j : (back ? kHCap - q.nb + (j - q.nf) : -1);
+  const int p = __float_as_int(idx >= 0 ? S.ent[idx].w : S.own[j - q.nf - q.nb].w);
+  atomicAdd(&H.hforce[p], make_float4(fx, fy, fz, 0.f));
+  if (back) {
+    const int im = S.img[idx];
+    const float tx = (float)(signed char)(im & 255), ty = (float)(signed char)((im >> 8) & 255),
+                tz = (float)(signed char)((im >> 16) & 255);
+    float t[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) t[a] = tx * H.hrow[a] + ty * H.hrow[3 + a] + tz * H.hrow[6 + a];
+    const float f[3] = {fx, fy, fz};
+    wv[0] += t[0] * f[0];
+    wv[1] += 0.5f * (t[0] * f[1] + t[1] * f[0]);
+    wv[2] += 0.5f * (t[0] * f[2] + t[2] * f[0]);
+    wv[3] += t[1] * f[1];
+    wv[4] += 0.5f * (t[1] * f[2] + t[2] * f[1]);
+    wv[5] += t[2] * f[2];
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant__ SweepArgs A,
+                                                           const __grid_constant__ HoodArgs H,
+                                                           double* __restrict__ partials) {
+  constexpr bool ENERGY = MODE != 1;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  HalfSmem& S = *reinterpret_cast<HalfSmem*>(smraw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NV = hood_nv(MODE);
+  if (*H.mixed) {  // the full-shell kernels take this launch
+    if (tid < NV) partials[(size_t)blockIdx.x * NV + tid] = 0.0;
+    return;
+  }
+  for (int k = tid; k < kWarps * 16; k += kThreads) (&S.out[0][0])[k] = 0.0;
+  for (int k = tid; k < A.noff && k < kTab; k += kThreads) {
+    const Off& o = A.off[k];
+    S.otab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[1][k]));
+  }
+  for (int k = tid; k < kHome * 3; k += kThreads) (&S.hg[0][0])[k] = 0.f;
+  if (tid == 0) S.ncand = 0;
+  __syncthreads();
+  if (tid == 0) {
+    const int ne = A.noff < kTab ? A.noff : kTab;
+    int nr = 0, pox = 0, poy = 0, poz = 0;
+    for (int k = 1; k < ne; ++k) {
+      int ox, oy, oz;
+      unpack_off(__float_as_int(S.otab[k].w), ox, oy, oz);
+      if (k == 1 || oy != poy || oz != poz || ox != pox + 1) S.rowk[nr++] = (unsigned short)k;
+      pox = ox;
+      poy = oy;
+      poz = oz;
+    }
+    S.rowk[nr] = (unsigned short)(ne > 1 ? ne : 1);
+    S.nrows = nr;
+  }
+  float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // lane's sum of (T.H) (x) f over its entries across the boundary
+  float2 e = f2(0.f);
+  const int nlist = H.work[1];
+  int next1 = 0;
+  if (tid == 0) next1 = atomicAdd(H.work, 1);
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      S.item = next1 < nlist ? H.list[next1] : -1;
+      if (next1 < nlist) next1 = atomicAdd(H.work, 1);
+      S.nf = 0;
+      S.nb = 0;
+      S.next = 0;
+    }
+    __syncthreads();
+    const int h = S.item;
+    if (h < 0) break;
+    const int hs = A.cell_start[h];
+    const int nh = A.cell_start[h + 1] - hs;
+    const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
+    float d = 0.f;
+    for (int t = tid; t < kHome + 4; t += kThreads) {
+      if (t < nh) {
+        const float4 hq = A.xs[hs + t];
+        d = fmaxf(d, fminf(sqrtf(fmaf(hq.x, hq.x, fmaf(hq.y, hq.y, hq.z * hq.z))), H.hd));
+        S.home[t] = make_float4(-hq.x, -hq.y, -hq.z, __int_as_float(hs + t));  // negated: d = x_e + home
+        S.own[t] = make_float4(hq.x, hq.y, hq.z, __int_as_float(hs + t));
+      } else {
+        S.home[t] = make_float4(kFar, -kFar, kFar, __int_as_float(0));  // padding: far from every entry
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if (lane == 0) S.wmax[warp] = d;
+    __syncthreads();
+    float dmax = S.wmax[0];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) dmax = fmaxf(dmax, S.wmax[w]);
+    const float top = H.rc + dmax + H.eps;
+    half_stage(A, S, cx, cy, cz, top * top);
+    __syncthreads();
+    const int nf = min(S.nf, kHCap), nb = min(S.nb, kHCap - nf);  // k_hood_list guarantees nf + nb <= kHCap
+    SeqInfo sq;
+    sq.nf = nf;
+    sq.nb = nb;
+    sq.nh = nh;
+    const int nseq = nf + nb + nh;
+    const int nch = (nseq + kChunk - 1) / kChunk;
+    const int cmask = (nf + nb) / kChunk;  // the first chunk holding own-cell positions
+    if (tid == 0) S.ncand += (unsigned long long)nh * (unsigned long long)(nf + nb) + (unsigned long long)(nh * (nh - 1) / 2);
+    // chunks of the sequence, taken from a counter; only the chunks holding
+    // own-cell positions apply the order mask
+    for (;;) {
+      int c = 0;
+      if (lane == 0) c = atomicAdd(&S.next, 1);
+      c = __shfl_sync(0xffffffffu, c, 0);
+      if (c >= nch) break;
+      float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
+      const int base = c * kChunk;
+      if (c < cmask) half_chunk<false>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e);
+      else half_chunk<true>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e);
+#pragma unroll
+      for (int k = 0; k < kEnt / 2; ++k) {
+        const int j0 = base + lane + 64 * k;
+        half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
+        half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+      }
+    }
+    // this cell's energy and boundary terms into the warp's FP64 sums
+    {
+      float v[8] = {wv[0], wv[1], wv[2], wv[3], wv[4], wv[5], ENERGY ? e.x + e.y : 0.f, 0.f};
+      warp_reduce_multi<8>(v);  // lane l: value l >> 2
+      if ((lane & 3) == 0 && (lane >> 2) < 6) S.out[warp][lane >> 2] += -2.0 * (double)v[0];
+      if (ENERGY && lane == 24) S.out[warp][15] += (double)v[0];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) wv[q] = 0.f;
+      e = f2(0.f);
+    }
+    __syncthreads();
+    // the home particles' forces: minus their sums of fsn r
+    if (tid < nh) {
+      const float gx = S.hg[tid][0], gy = S.hg[tid][1], gz = S.hg[tid][2];
+      if (gx != 0.f || gy != 0.f || gz != 0.f) atomicAdd(&H.hforce[hs + tid], make_float4(-gx, -gy, -gz, 0.f));
+      S.hg[tid][0] = S.hg[tid][1] = S.hg[tid][2] = 0.f;
+    }
+  }
+  // per-CTA partials: -2 (T.H) (x) f sums, energy (each pair-image once)
+  __syncthreads();
+  if (tid == 0 && S.ncand) atomicAdd(H.cand, S.ncand);
+  if (tid < NV) {
+    int src;
+    if (MODE == 2) src = 15;
+    else if (tid < kVirN3) src = tid;
+    else if (MODE == 0) src = 15;
+    else if (tid < kVirN3 + 9) src = -1;  // X: from k_half_finish
+    else src = 15;
+    double acc = 0.0;
+    if (src >= 0)
+      for (int w = 0; w < kWarps; ++w) acc += S.out[w][src];
+    partials[(size_t)blockIdx.x * NV + tid] = acc;
+  }
+}
+
+// Per particle i after the half-shell sweep: its force F (from the
+// accumulated buffer, which it clears for the next launch), the outputs
+// (MODE 0: forces; 1, 3: grad = -g F) and the per-CTA sums of -2 X (x) F
+// (symmetric part) and, for the gradient modes, x_raw (x) F.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_half_finish(const __grid_constant__ SweepArgs A,
+                                                     const __grid_constant__ HoodArgs H, float* __restrict__ forces,
+                                                     double* __restrict__ grad, const double* __restrict__ gE,
+                                                     const double* __restrict__ pos, double* __restrict__ partials) {
+  constexpr bool GRAD = MODE == 1 || MODE == 3;
+  constexpr int NV = hood_nv(MODE);
+  if (*H.mixed) {
+    if (threadIdx.x < NV) partials[(size_t)blockIdx.x * NV + threadIdx.x] = 0.0;
+    return;
+  }
+  const float g = GRAD ? (float)*gE : 0.f;
+  float o[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) o[q] = 0.f;
+  // original order: FP64 positions and gradients coalesced. Four particles per
+  // thread and step, each load stage issued for all four before the next, so
+  // that the dependent loads (cell start, then the accumulated force) overlap.
+  constexpr int U = 4;
+  const int stride = gridDim.x * blockDim.x;
+  for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < A.n; i0 += U * stride) {
+    float4 q[U];
+    int p[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * stride;
+      q[u] = i < A.n ? H.xl[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      p[u] = i < A.n ? H.slot[i] : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned cc = __float_as_uint(q[u].w);
+      const int i = i0 + u * stride;
+      if (i < A.n)
+        p[u] += A.cell_start[(int)(cc & 1023u) + A.nx * ((int)((cc >> 10) & 1023u) + A.ny * (int)(cc >> 20))];
+    }
+    float4 f4[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) f4[u] = i0 + u * stride < A.n ? H.hforce[p[u]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * stride;
+      if (i >= A.n) break;
+      H.hforce[p[u]] = make_float4(0.f, 0.f, 0.f, 0.f);
+      const unsigned cc = __float_as_uint(q[u].w);
+      const float cx = (float)(cc & 1023u) + 0.5f, cy = (float)((cc >> 10) & 1023u) + 0.5f, cz = (float)(cc >> 20) + 0.5f;
+      float X[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        X[a] = fmaf(cx, H.gf[a], fmaf(cy, H.gf[3 + a], cz * H.gf[6 + a])) + (a == 0 ? q[u].x : a == 1 ? q[u].y : q[u].z);
+      const float F[3] = {f4[u].x, f4[u].y, f4[u].z};
+      o[0] -= 2.f * X[0] * F[0];
+      o[1] -= X[0] * F[1] + X[1] * F[0];
+      o[2] -= X[0] * F[2] + X[2] * F[0];
+      o[3] -= 2.f * X[1] * F[1];
+      o[4] -= X[1] * F[2] + X[2] * F[1];
+      o[5] -= 2.f * X[2] * F[2];
+      if (MODE == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) forces[(size_t)i * 3 + a] = F[a];
+      } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = (double)(-g * F[a]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const float xa = (float)pos[(size_t)i * 3 + a];
+#pragma unroll
+          for (int b = 0; b < 3; ++b) o[6 + a * 3 + b] = fmaf(xa, F[b], o[6 + a * 3 + b]);
+        }
+      }
+    }
+  }
+  // -2 X (x) F sums already carry the sign of the partials; X (x) F as is
+  warp_reduce_multi<16>(o);  // lane l: value l >> 1
+  __shared__ double sm[8][16];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if ((lane & 1) == 0) sm[warp][lane >> 1] = (double)o[0];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    int src;  // column of o for partial threadIdx.x
+    if (threadIdx.x < kVirN3) src = threadIdx.x;
+    else if (MODE == 0) src = -1;  // energy: from the sweep
+    else if (threadIdx.x < kVirN3 + 9) src = threadIdx.x;
+    else src = -1;
+    double acc = 0.0;
+    if (src >= 0)
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += sm[w][src];
+    partials[(size_t)blockIdx.x * NV + threadIdx.x] = acc;
+  }
+}
+
 }  // namespace
 
 int hood_grid(int mode) {
@@ -1192,6 +1763,31 @@ int hood_grid(int mode) {
 }
 
 size_t hood_smem_bytes() { return sizeof(Smem); }
+
+// Persistent CTAs of the half-shell sweep, per mode (0, 1, 3).
+int half_grid(int mode) {
+  static DevCache cached[4];
+  if (mode < 0 || mode > 3 || mode == 2) return 0;
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (const int c = cached[mode].get(dev)) return c;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  const int bytes = (int)sizeof(HalfSmem);
+  cudaError_t e;
+  if (mode == 0) {
+    e = cudaFuncSetAttribute(k_hood_half<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<0>, kThreads, bytes);
+  } else if (mode == 1) {
+    e = cudaFuncSetAttribute(k_hood_half<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<1>, kThreads, bytes);
+  } else {
+    e = cudaFuncSetAttribute(k_hood_half<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<3>, kThreads, bytes);
+  }
+  if (e != cudaSuccess || per < 1) return 0;
+  cached[mode].put(dev, sms * per);
+  return sms * per;
+}
 
 // Persistent CTAs of the dense-cell sweep (all resident), per mode; also
 // raises the kernels' shared-memory limit on the current device.
@@ -1241,6 +1837,7 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
     for (int a = 0; a < 3; ++a) {
       H->g[k * 3 + a] = geo.h[k * 3 + a] / geo.n[k];
       H->gf[k * 3 + a] = (float)H->g[k * 3 + a];
+      H->hrow[k * 3 + a] = (float)geo.h[k * 3 + a];
     }
   const double eps = 1e-4 * (geo.rc + hd);
   H->rc = (float)geo.rc;
@@ -1250,48 +1847,75 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
   return CL_OK;
 }
 
-int launch_hood(const SweepArgs& A, const HoodArgs& Hin, int* work, int mode, const double* hinv, float* forces,
-                double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
-                double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s) {
+int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& Hin, int* work, int mode,
+                const double* hinv, float* forces, double* grad, const double* gE, const double* pos,
+                double* partials, long long partials_cap, double* sums, double* energy, double* virial,
+                double* gradbox, cudaStream_t s) {
   const int NV = hood_nv(mode);
+  const bool half = Ahalf && mode != 2 && Hin.hforce && A.noff <= kTab && Ahalf->noff <= kTab && A.n > 0;
   const int nrest = (A.n + 255) / 256;  // CTAs of the companion sweep
   const int ndc = dense_grid(mode);     // CTAs of the dense-cell sweep
   int nb = hood_grid(mode);
-  if (nb <= 0 || ndc <= 0) return CL_ERR_CUDA;
+  int nhb = half ? half_grid(mode) : 0;
+  const int nfin = half ? std::min(nrest, 152 * 8) : 0;
+  if (nb <= 0 || ndc <= 0 || (half && nhb <= 0)) return CL_ERR_CUDA;
   if (nb > Hin.ncells) nb = Hin.ncells;
-  const long long room = partials_cap / NV - nrest - ndc;
-  if (nb > room) nb = (int)room;
-  if (nb < 1) return CL_ERR_INVALID_ARG;
+  if (nhb > Hin.ncells) nhb = Hin.ncells;
+  const long long room = partials_cap / NV - nrest - ndc - nfin;
+  if (nb + nhb > room) {
+    nb = (int)(room / 2);
+    nhb = half ? (int)(room - nb) : 0;
+  }
+  if (nb < 1 || (half && nhb < 1)) return CL_ERR_INVALID_ARG;
   HoodArgs H = Hin;
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
   H.ndense = work + 4;
-  if (cudaMemsetAsync(work, 0, 6 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  H.mixed = work + 6;
+  H.half = half ? 1 : 0;
+  if (cudaMemsetAsync(work, 0, 8 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
-                                                     H.ndense);
-  const size_t smem = sizeof(Smem);
-  double* rest = partials + (size_t)nb * NV;
+                                                     H.ndense, H, half ? Ahalf->noff : 0, A.nx, A.ny, A.nz);
+  // partials: [half-shell sweep][its per-particle finish][full-shell sweep][companion][dense cells]
+  double* pfin = partials + (size_t)nhb * NV;
+  double* pfull = pfin + (size_t)nfin * NV;
+  double* rest = pfull + (size_t)nb * NV;
   double* dpart = rest + (size_t)nrest * NV;
+  const size_t smem = sizeof(Smem);
+  const size_t hsmem = sizeof(HalfSmem);
   const size_t dsmem = dense_smem_bytes(A.noff);
   if (mode == 0) {
-    k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    if (half) {
+      k_hood_half<0><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
+      k_half_finish<0><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
+    }
+    k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
     k_hood_rest<0><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<0><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else if (mode == 1) {
-    k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    if (half) {
+      k_hood_half<1><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
+      k_half_finish<1><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
+    }
+    k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
     k_hood_rest<1><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<1><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else if (mode == 2) {
-    k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
     k_hood_rest<2><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<2><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else {
-    k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
+    if (half) {
+      k_hood_half<3><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
+      k_half_finish<3><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
+    }
+    k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
     k_hood_rest<3><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<3><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   }
   const int final_mode = mode == 2 ? 1 : (mode == 0 ? 2 : (mode == 1 ? 3 : 4));
-  return finish_reduction(final_mode, 3, hinv, nb + nrest + ndc, NV, partials, sums, energy, virial, gradbox, gE, s);
+  return finish_reduction(final_mode, 3, hinv, nhb + nfin + nb + nrest + ndc, NV, partials, sums, energy, virial,
+                          gradbox, gE, s);
 }
 
 }  // namespace clk

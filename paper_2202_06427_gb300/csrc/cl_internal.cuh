@@ -152,6 +152,12 @@ struct HoodArgs {
   unsigned char* flag;       // per cell: 1 per-particle companion sweep, 2 dense-cell sweep
   int* dense;                // cells of the dense-cell sweep (ncells capacity)
   int* ndense;               // their number (work[4])
+  float hrow[9];             // lattice rows H (FP32): lattice image T maps to the shift T.H
+  float4* hforce;            // half-shell path: per sorted particle, accumulated force (n entries)
+  const float4* xl;          // per original particle: local coordinate, w = packed cell (binning output)
+  const int* slot;           // per original particle: position inside its cell
+  int* mixed;                // work[6]: 1 when some cell is not swept by the half-shell path
+  int half;                  // 1 when the half-shell path is tried for this launch
 };
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
                    HoodArgs* H);
@@ -159,7 +165,10 @@ size_t hood_smem_bytes();
 // mode 0: energy, forces, virial; 1: backward; 2: energy (half shell, A = half
 // stencil); 3: energy and the backward outputs.
 // partials_cap: doubles available in partials (sweep_partials_needed).
-int launch_hood(const SweepArgs& A, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
+// Ahalf (modes 0, 1, 3; may be null): the half stencil, for the half-shell
+// path taken when every non-empty cell fits it (H.hforce must then hold n
+// entries); the full-shell kernels take the launch otherwise.
+int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
                 double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
                 double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s);
 
