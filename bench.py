@@ -52,10 +52,13 @@ LCELL_BY_WORKLOAD = {"w1_lattice_1m": 2, "w2_triclinic_1m": 2, "w4_clustered_16m
 #   1/r, u, u'/r, 3 force FMAs for i and 3 for j, 6 virial FMAs = 26 FLOP.
 FLOP_PER_CANDIDATE = 8
 FLOP_PER_PAIR = 26
-# What the neighbourhood sweep itself evaluates (full shell: every pair from both
-# ends), reported beside the algorithmic figure: 8 FLOP per staged candidate and
-# 16 per ordered pair-image (1/r, fsn, 3 force FMAs, energy term).
+# What the sweep itself evaluates, reported beside the algorithmic figure: 8 FLOP
+# per staged candidate, and per pair-image within the cutoff either 16 FLOP from
+# each end (full-shell kernels: 1/r, fsn, 3 force FMAs, energy term) or, on the
+# half-shell path (each pair-image once), the force on both particles as well
+# (1/r, fsn, 6 force FMAs, energy term: 22 FLOP).
 FLOP_PER_HIT_FUSED = 16
+FLOP_PER_HIT_HALF = 22
 # Algorithmic bytes of binning per particle: FP64 position read (24 B), FP32
 # cell-centred coordinate + index written (16 B), cell-sorted position of the
 # original index (4 B); the per-cell counts and offsets add 8 B per cell.
@@ -66,8 +69,9 @@ BIN_BYTES_PER_CELL = 8
 # the kernel has changed since the counters were taken.
 SWEEP_DRAM_BYTES = None
 FP32_LANES_PER_SM = 128
-# kernels of one headline step: bin, 3 scan, scatter, pair pack; cell list,
-# neighbourhood sweep, per-particle companion, dense-cell sweep, 2 reduce; 2 scale
+# kernels of one headline step: bin, 2 scan, scatter; cell list, half-shell sweep,
+# its per-particle finish, full-shell sweep (exits when the half shell took the
+# grid), per-particle companion, dense-cell sweep, 2 reduce; 2 scale
 STEP_LAUNCHES = 14
 
 
@@ -326,22 +330,28 @@ def fp32_peak(dev, clocks):
         "%d SMs x 128 FP32 lanes x 2 FLOP x %.0f MHz (derived from unit counts and the maximum clock)" % (sms, mhz)
 
 
-def sweep_roofline(dev, clocks, cand_half, pairs, kms, cand_eval, kernel):
+def sweep_roofline(dev, clocks, cand_half, pairs, kms, cand_eval, kernel, half_path):
     """Roofline record of the sweep: algorithmic FP32 work (half-shell stencil
     candidates x 8 + pair-images x 26) / the sweep's CUDA-event time, against
-    the FP32 peak. The work the kernel itself evaluated is reported beside it."""
+    the FP32 peak. The work the kernels themselves evaluated is reported beside
+    it (half_path: each pair-image once)."""
     peak, basis = fp32_peak(dev, clocks)
     flop = cand_half * FLOP_PER_CANDIDATE + pairs * FLOP_PER_PAIR
     achieved = flop / (kms / 1e3) / 1e12
-    flop_eval = cand_eval * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_FUSED
+    if half_path:
+        flop_eval = cand_eval * FLOP_PER_CANDIDATE + pairs * FLOP_PER_HIT_HALF
+        ebasis = "staged half-shell candidates x 8 + pair-images x 22 (each once, forces on both particles)"
+    else:
+        flop_eval = cand_eval * FLOP_PER_CANDIDATE + 2 * pairs * FLOP_PER_HIT_FUSED
+        ebasis = "staged full-shell candidates x 8 + ordered pair-images x 16"
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": None, "kernel": kernel, "kernel_ms": kms, "flop_per_launch": flop,
             "flop_basis": "half-shell stencil candidates x %d + pair-images x %d (energy, forces, virial)"
                           % (FLOP_PER_CANDIDATE, FLOP_PER_PAIR),
             "candidates_half_shell_stencil": cand_half,
             "evaluated": {"candidates": cand_eval, "flop": flop_eval, "tflops": flop_eval / (kms / 1e3) / 1e12,
-                          "frac": flop_eval / (kms / 1e3) / 1e12 / peak,
-                          "basis": "what the sweep evaluates: staged candidates x 8 + ordered pair-images x 16"},
+                          "frac": flop_eval / (kms / 1e3) / 1e12 / peak, "half_shell": bool(half_path),
+                          "basis": ebasis},
             "peak_basis": basis}
 
 
@@ -503,6 +513,7 @@ def clustered_leg(dev, steps, warmup):
     for _ in range(warmup):
         energy_grad_step(P, cl, out, g, grad_x, grad_h, stream)
     cand = P.cl_query(cl, "sweep_candidates")
+    half_path = P.cl_query(cl, "sweep_half")
     torch.cuda.synchronize(dev)
     for k in range(steps):
         energy_grad_step(P, cl, out, g, grad_x, grad_h, stream, ev[k])
@@ -514,7 +525,8 @@ def clustered_leg(dev, steps, warmup):
             "steps": steps, "ms_per_step": ms, "pairs_per_s": pairs / (ms / 1e3),
             "step": "binning + fused energy/forces/box-gradient sweep + chain rule",
             "l2": "inputs (384 MB positions) larger than L2",
-            "roofline": sweep_roofline(dev, None, cand_half, pairs, kms, cand, "cl_energy_grad sweep kernels"),
+            "roofline": sweep_roofline(dev, None, cand_half, pairs, kms, cand, "cl_energy_grad sweep kernels",
+                                       half_path),
             "binning": binning_record(n, P.cl_query(cl, "ncells"), bms, peaks, basis)}
 
 
@@ -567,6 +579,7 @@ def run_ours(args, rank, world, local):
     grad_h = torch.empty((3, 3), dtype=torch.float64, device=dev)
     P.cl_energy_grad(cl, out=out[:4])
     cand = P.cl_query(cl, "sweep_candidates")  # candidate pairs the fused sweep evaluates
+    half_path = P.cl_query(cl, "sweep_half")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
 
     for _ in range(args.warmup):
@@ -591,7 +604,8 @@ def run_ours(args, rank, world, local):
     clocks = sampler.summary()
     peaks, basis = load_peaks()
     roofline = sweep_roofline(dev, clocks, cand_half, pairs, kms, cand,
-                              "cl_energy_grad sweep kernels (neighbourhood sweep: energy + forces + box gradient)")
+                              "cl_energy_grad sweep kernels (neighbourhood sweep: energy + forces + box gradient)",
+                              half_path)
     roofline["traffic"] = SWEEP_DRAM_BYTES if workload == WORKLOAD else None
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

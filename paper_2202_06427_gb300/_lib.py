@@ -20,7 +20,7 @@ CL_RED_COUNT, CL_RED_SUM_INV_R, CL_RED_SF_ENERGY, CL_RED_SF_ENERGY_FORCES_VIRIAL
 
 INFO = {"n": 0, "dim": 1, "grid_x": 2, "grid_y": 3, "grid_z": 4, "ncells": 5, "nonempty": 6, "max_occupancy": 7,
         "bytes": 8, "stencil_half": 9, "stencil_full": 10, "candidates": 11, "work_tiles": 12,
-        "sweep_candidates": 13}
+        "sweep_candidates": 13, "sweep_half": 14}
 
 
 class cl_box(ctypes.Structure):

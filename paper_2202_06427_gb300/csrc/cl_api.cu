@@ -618,6 +618,14 @@ int cl_query(const cl_list* c, int what, long long* value, void* stream) {
       *value = what == CL_INFO_NONEMPTY ? m[1] : m[2];
       return CL_OK;
     }
+    case CL_INFO_SWEEP_HALF: {
+      int mixed = 1;
+      if (cudaMemcpyAsync(&mixed, c->work + 6, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CL_ERR_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+      *value = (c->geo.dim == 3 && c->n > 0 && !mixed) ? 1 : 0;
+      return CL_OK;
+    }
     case CL_INFO_SWEEP_CANDIDATES: {
       unsigned long long v = 0;
       if (cudaMemcpyAsync(&v, c->work + 2, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
