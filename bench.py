@@ -620,6 +620,8 @@ def run_ours(args, rank, world, local):
             "clocks": clocks, "roofline": roofline,
             "binning": binning_record(n, ncells, bms, peaks, basis),
             "sweep_pairs_per_s": pairs / (kms / 1e3)}
+    if not args.no_extra:
+        line["reductions"] = reduction_times(P, cl, dev, flush)
 
     if not args.no_e2e:
         line["e2e"] = e2e(P, cl, w, dev, stream, pairs, args, world)
@@ -650,6 +652,30 @@ def run_ours(args, rank, world, local):
         torch.cuda.empty_cache()
         line["workloads"]["w4_clustered_16m"] = clustered_leg(dev, 10, 3)
     return line
+
+
+def reduction_times(P, cl, dev, flush, reps=20):
+    """Device time of each built-in reduction on the built list (one cl_map
+    call, output allocation included; L2 flushed before each call)."""
+    import torch
+    calls = {"count": lambda: P.cl_map(cl, "count"),
+             "sum_inv_r": lambda: P.cl_map(cl, "sum_inv_r"),
+             "energy": lambda: P.cl_map(cl, "energy"),
+             "hist_100_bins": lambda: P.cl_map(cl, "hist", nbins=100),
+             "energy_forces_virial": lambda: P.cl_map(cl, "energy_forces_virial")}
+    out = {}
+    for name, f in calls.items():
+        for _ in range(2):
+            f()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for k in range(reps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            f()
+            ev[k][1].record()
+        torch.cuda.synchronize(dev)
+        out[name + "_ms"] = sum(a.elapsed_time(b) for a, b in ev) / reps
+    return out
 
 
 def serve_leg(dev):

@@ -61,9 +61,10 @@ constexpr int kHCap = 1536;            // staged entries of the half-shell path
 // distances that stay finite in FP32.
 constexpr float kFar = 3e15f;
 
-// Per-CTA partials: mode 0: S6, E; mode 1: S6, X9; mode 2: E; mode 3: S6, X9, E.
+// Per-CTA partials: mode 0: S6, E; mode 1: S6, X9; mode 2: E; mode 3: S6, X9, E;
+// scalar modes 4 (count), 5 (sum 1/r), 6 (histogram): one value (sum 1/r, else 0).
 __host__ __device__ constexpr int hood_nv(int mode) {
-  return mode == 0 ? 1 + kVirN3 : (mode == 1 ? kVirN3 + 9 : (mode == 2 ? 1 : kVirN3 + 10));
+  return mode == 0 ? 1 + kVirN3 : (mode == 1 ? kVirN3 + 9 : (mode == 3 ? kVirN3 + 10 : 1));
 }
 
 struct Smem {
@@ -220,6 +221,89 @@ __device__ __forceinline__ void hood_own(const float4* __restrict__ xy, const fl
     const bool m10 = HALF ? e0 > t1 : e0 != t1, m11 = HALF ? e1 > t1 : e1 != t1;
     hood_pair<ENERGY, FORCE, false, true>(qx, qy, z, I[0], I[1], I[2], m00, m01, rc2, irc, irc2, a0, e, nullptr);
     hood_pair<ENERGY, FORCE, false, true>(qx, qy, z, I[3], I[4], I[5], m10, m11, rc2, irc, irc2, a1, e, nullptr);
+  }
+}
+
+// Scalar reductions of the half-shell staged sweep, per candidate pair:
+// MODE 4 count, 5 sum 1/r, 6 distance histogram (each pair-image within the
+// cutoff once). Unlike the energy, whose terms vanish at the cutoff, these
+// test d2 < rc^2 explicitly. 1/r is the hardware reciprocal square root
+// (relative error about 1e-7, as in the energy sweep). The histogram takes
+// x = r nbins / rmax = sqrt(d2 scale^2) from the hardware square root and
+// counts the pair in bin floor(x) when x < xlim = min(nbins, rc scale), with
+// shared-memory atomics; floor(x) comes from adding 2^23 rounded toward zero
+// (for 0 <= x < 2^23 the sum's low mantissa bits are floor(x)), which keeps
+// the float-to-int conversion off the special-function unit. The histogram is
+// kept in hcopies copies (stride hstride = 1 mod 32, so one bin of different
+// copies lies in different banks), lane l adding to copy l mod hcopies; the
+// copies are summed at the end.
+struct ScalarRed {
+  float rc2, scale2, xlim;
+  unsigned* hist;  // shared memory: this lane's copy
+};
+
+__host__ __device__ constexpr int hist_stride(int nbins) { return nbins + ((33 - nbins % 32) % 32); }
+
+__device__ __forceinline__ void hist_hit(const ScalarRed& R, bool m, float s2) {
+  const float x = sqrt_approx(s2);
+  const int b = __float_as_int(__fadd_rz(x, 8388608.0f)) - 0x4B000000;
+  if (m && x < R.xlim) atomicAdd(&R.hist[b], 1u);
+}
+
+template <int MODE, bool MASK>
+__device__ __forceinline__ void scalar_pair(float2 qx, float2 qy, float2 qz, float2 ix, float2 iy, float2 iz, bool m0,
+                                            bool m1, const ScalarRed& R, unsigned& n, float2& acc) {
+  const float2 dx = __fadd2_rn(qx, ix), dy = __fadd2_rn(qy, iy), dz = __fadd2_rn(qz, iz);
+  float2 d2 = __fmul2_rn(dz, dz);
+  d2 = __ffma2_rn(dy, dy, d2);
+  d2 = __ffma2_rn(dx, dx, d2);
+  bool h0 = false, h1 = false;
+  if (MODE != 6) {
+    h0 = d2.x < R.rc2 && (!MASK || m0);
+    h1 = d2.y < R.rc2 && (!MASK || m1);
+  }
+  if (MODE == 4) n += (h0 ? 1u : 0u) + (h1 ? 1u : 0u);
+  if (MODE == 5) {
+    float2 y = rsqrt2(d2);
+    y.x = h0 ? y.x : 0.f;
+    y.y = h1 ? y.y : 0.f;
+    acc = __fadd2_rn(acc, y);
+  }
+  if (MODE == 6) {
+    const float2 s2 = __fmul2_rn(d2, f2(R.scale2));
+    hist_hit(R, !MASK || m0, s2.x);
+    hist_hit(R, !MASK || m1, s2.y);
+  }
+}
+
+template <int MODE>
+__device__ __forceinline__ void scalar_scan(const float4* __restrict__ xy, const float2* __restrict__ zz, int k0,
+                                            int k1, const float2 (&I)[6], const ScalarRed& R, unsigned& n,
+                                            float2& acc) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll 2
+  for (int k = k0 + lane; k < k1; k += 32) {
+    const float4 q = xy[k];
+    const float2 z = zz[k];
+    const float2 qx = make_float2(q.x, q.y), qy = make_float2(q.z, q.w);
+    scalar_pair<MODE, false>(qx, qy, z, I[0], I[1], I[2], true, true, R, n, acc);
+    scalar_pair<MODE, false>(qx, qy, z, I[3], I[4], I[5], true, true, R, n, acc);
+  }
+}
+
+// Own cell, half shell: entries after the home particle.
+template <int MODE>
+__device__ __forceinline__ void scalar_own(const float4* __restrict__ xy, const float2* __restrict__ zz, int npairs,
+                                           int t0, int t1, const float2 (&I)[6], const ScalarRed& R, unsigned& n,
+                                           float2& acc) {
+  const int lane = threadIdx.x & 31;
+  for (int k = lane; k < npairs; k += 32) {
+    const float4 q = xy[k];
+    const float2 z = zz[k];
+    const float2 qx = make_float2(q.x, q.y), qy = make_float2(q.z, q.w);
+    const int e0 = 2 * k, e1 = 2 * k + 1;
+    scalar_pair<MODE, true>(qx, qy, z, I[0], I[1], I[2], e0 > t0, e1 > t0, R, n, acc);
+    scalar_pair<MODE, true>(qx, qy, z, I[3], I[4], I[5], e0 > t1, e1 > t1, R, n, acc);
   }
 }
 
@@ -722,6 +806,10 @@ __global__ void __launch_bounds__(256) k_hood_rest(const __grid_constant__ Sweep
                                                    double* __restrict__ grad, const double* __restrict__ gE,
                                                    const double* __restrict__ pos, double* __restrict__ partials) {
   constexpr bool GRAD = MODE == 1 || MODE == 3;
+  if (H.half && !*H.mixed) {  // the half-shell path took this launch: no flagged cells
+    if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
+    return;
+  }
   const float g = GRAD ? (float)*gE : 0.f;
   ThreadOut T;
   T.es = T.ec = 0.f;
@@ -994,13 +1082,16 @@ __global__ void __launch_bounds__(kDenseThreads, 3) k_hood_dense(const __grid_co
 
 // MODE 0: energy, forces, virial (full shell). MODE 1: backward: grad_pos, X,
 // virial (full shell). MODE 2: energy (half shell). MODE 3: energy and the
-// backward outputs in one full-shell sweep.
+// backward outputs in one full-shell sweep. MODES 4, 5, 6: pair count, sum
+// 1/r, distance histogram (half shell; the histogram in dynamic shared memory
+// after Smem).
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ SweepArgs A, const __grid_constant__ HoodArgs H,
                                                       float* __restrict__ forces, double* __restrict__ grad,
                                                       const double* __restrict__ gE, const double* __restrict__ pos,
                                                       double* __restrict__ partials) {
-  constexpr bool FORCE = MODE != 2, ENERGY = MODE != 1, HALF = MODE == 2;
+  constexpr bool SCALAR = MODE >= 4;
+  constexpr bool FORCE = MODE != 2 && !SCALAR, ENERGY = MODE != 1 && !SCALAR, HALF = MODE == 2 || SCALAR;
   constexpr bool GRAD = MODE == 1 || MODE == 3;
   if (H.half && !*H.mixed) {  // the half-shell path took this launch
     if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
@@ -1019,6 +1110,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
     const Off& o = A.off[k];
     S.otab[k] = make_float4(o.sx, o.sy, o.sz, __int_as_float(H.opk[HALF ? 1 : 0][k]));
   }
+  ScalarRed R;
+  R.rc2 = A.rc2;
+  R.scale2 = H.hscale * H.hscale;
+  R.xlim = H.hxlim;
+  unsigned* const hist_all = reinterpret_cast<unsigned*>(smraw + sizeof(Smem));
+  R.hist = hist_all + (lane & (H.hcopies - 1)) * H.hstride;
+  if (MODE == 6)
+    for (int b = tid; b < H.hcopies * H.hstride; b += kThreads) hist_all[b] = 0u;
+  unsigned cnt = 0;  // MODE 4: this lane's pairs
   __syncthreads();
   if (tid == 0) build_rows(A, S);
   // Work items (cells of the list made by k_hood_list) come from an atomic
@@ -1122,6 +1222,17 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
       I[3] = f2(has1 ? -own_x(S, t1) : kFar);
       I[4] = f2(has1 ? -own_y(S, t1) : kFar);
       I[5] = f2(has1 ? -own_z(S, t1) : kFar);
+      if (SCALAR) {
+        float2 sacc = f2(0.f);
+        scalar_scan<MODE>(S.xy, S.zz, k0a, k1a, I, R, cnt, sacc);
+        scalar_own<MODE>(S.oxy, S.ozz, ngroups, t0, t1, I, R, cnt, sacc);
+        if (k1b > k0b) scalar_scan<MODE>(S.xy, S.zz, k0b, k1b, I, R, cnt, sacc);
+        if (MODE == 5) {
+          const float t = warp_sum(sacc.x + sacc.y);
+          if (lane == 0) S.out[warp][15] += (double)t;
+        }
+        continue;
+      }
       HAcc a0, a1;
       a0.gx = a0.gy = a0.gz = a1.gx = a1.gy = a1.gz = f2(0.f);
       float2 e = f2(0.f);
@@ -1200,12 +1311,25 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   // candidate count: one atomic per CTA
   __syncthreads();
   if (tid == 0 && S.ncand) atomicAdd(H.cand, S.ncand);
+  if (MODE == 4) {
+    unsigned long long c = cnt;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && c) atomicAdd(H.count, c);
+  }
+  if (MODE == 6)
+    for (int b = tid; b < H.nbins; b += kThreads)
+    {
+      unsigned c = 0;
+      for (int q = 0; q < H.hcopies; ++q) c += hist_all[q * H.hstride + b];
+      if (c) atomicAdd(&H.hist[b], (unsigned long long)c);
+    }
   // per-CTA partials (layout of the other sweeps) from the per-warp sums, fixed order
   constexpr int NV = hood_nv(MODE);
   if (tid < NV) {
     int src;  // S.out column of partial tid
     double sign = 1.0;
-    if (MODE == 2) {
+    if (HALF) {
       src = 15;
     } else if (tid < kVirN3) {
       src = tid;
@@ -1745,18 +1869,38 @@ __global__ void __launch_bounds__(256) k_half_finish(const __grid_constant__ Swe
 
 }  // namespace
 
+// Shared memory of k_hood<mode>: Smem, and for the histogram its copies (the
+// most of the size the grid is sized for; at least one copy).
+constexpr int kHistWords = 1408;  // histogram copies fitting five CTAs per SM
+static_assert(hist_stride(kMaxBins) >= kHistWords, "the largest histogram bounds every copy set");
+size_t hood_mode_smem(int mode) {
+  return sizeof(Smem) + (mode == 6 ? sizeof(unsigned) * (size_t)hist_stride(kMaxBins) : 0);
+}
+int hist_copies(int nbins) {
+  int c = 8;
+  while (c > 1 && c * hist_stride(nbins) > kHistWords) c >>= 1;
+  return c;
+}
+
 int hood_grid(int mode) {
-  static DevCache cached[4];
-  if (mode < 0 || mode > 3) return 0;
+  static DevCache cached[7];
+  if (mode < 0 || mode > 6) return 0;
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (const int c = cached[mode].get(dev)) return c;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   cudaError_t e;
-  if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<0>, kThreads, sizeof(Smem));
-  else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<1>, kThreads, sizeof(Smem));
-  else if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<2>, kThreads, sizeof(Smem));
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<3>, kThreads, sizeof(Smem));
+  const size_t sm = hood_mode_smem(mode);
+  if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<0>, kThreads, sm);
+  else if (mode == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<1>, kThreads, sm);
+  else if (mode == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<2>, kThreads, sm);
+  else if (mode == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<3>, kThreads, sm);
+  else if (mode == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<4>, kThreads, sm);
+  else if (mode == 5) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<5>, kThreads, sm);
+  else {
+    e = cudaFuncSetAttribute(k_hood<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<6>, kThreads, sm);
+  }
   if (e != cudaSuccess || per < 1) return 0;
   cached[mode].put(dev, sms * per);
   return sms * per;
@@ -1816,6 +1960,71 @@ int dense_grid(int mode) {
   if (e != cudaSuccess || per < 1) return 0;
   cached[mode].put(dev, sms * per);
   return sms * per;
+}
+
+int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int kind, unsigned long long* count,
+                       double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
+                       float rmax, unsigned long long* hist, cudaStream_t s) {
+  const int mode = 4 + kind;
+  if (kind < 0 || kind > 2) return CL_ERR_INVALID_ARG;
+  if (kind == 2 && (nbins < 1 || nbins > kMaxBins || !(rmax > 0.f))) return CL_ERR_INVALID_ARG;
+  const int nrest = flagged_blocks(A.n);
+  int nb = hood_grid(mode);
+  if (nb <= 0) return CL_ERR_CUDA;
+  if (nb > Hin.ncells) nb = Hin.ncells;
+  if (kind == 1 && nb + nrest > partials_cap) nb = (int)(partials_cap - nrest);
+  if (nb < 1) return CL_ERR_INVALID_ARG;
+  HoodArgs H = Hin;
+  H.work = work;
+  H.cand = reinterpret_cast<unsigned long long*>(work + 2);
+  H.ndense = work + 4;
+  H.mixed = work + 6;
+  H.half = 0;
+  H.count = count;
+  H.hist = hist;
+  H.nbins = kind == 2 ? nbins : 0;
+  H.rmax = kind == 2 ? rmax : 0.f;
+  H.hscale = kind == 2 ? (float)nbins / rmax : 0.f;
+  H.hxlim = kind == 2 ? (float)std::min((double)nbins, (double)Hin.rc * ((double)nbins / rmax)) : 0.f;
+  H.hcopies = kind == 2 ? hist_copies(nbins) : 1;
+  H.hstride = kind == 2 ? hist_stride(nbins) : 0;
+  if (cudaMemsetAsync(work, 0, 8 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  if (kind == 0 && cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
+  if (kind == 2 && cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nbins, s) != cudaSuccess) return CL_ERR_CUDA;
+  if (A.n <= 0) {
+    if (kind != 1) return CL_OK;
+    if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
+    return finish_reduction(0, 3, nullptr, 1, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
+  }
+  k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
+                                                     H.ndense, H, 0, A.nx, A.ny, A.nz);
+  size_t smem = hood_mode_smem(mode);
+  if (kind == 2) {  // the grid for this launch's histogram size
+    smem = sizeof(Smem) + sizeof(unsigned) * (size_t)H.hcopies * H.hstride;
+    int per = 0, sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<6>, kThreads, smem) != cudaSuccess || per < 1)
+      return CL_ERR_CUDA;
+    nb = std::min(sms * per, Hin.ncells);
+  }
+  // the staged sweep, then one thread per particle for the cells it left
+  // (flag != 0: few particles, more than kHome, or an overflowing ball)
+  if (kind == 0) {
+    k_hood<4><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+    if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
+    return launch_count_flagged(A, H.flag, count, s);
+  }
+  if (kind == 2) {
+    k_hood<6><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+    if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
+    return launch_hist_flagged(A, H.flag, nbins, rmax, hist, s);
+  }
+  k_hood<5><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+  if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
+  const int e = launch_suminvr_flagged(A, H.flag, partials + nb, s);
+  if (e != CL_OK) return e;
+  return finish_reduction(0, 3, nullptr, nb + nrest, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
 }
 
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,

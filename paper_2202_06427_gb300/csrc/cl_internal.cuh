@@ -124,6 +124,15 @@ int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStrea
 int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, double* sums, double* out,
                   cudaStream_t s);
 int launch_hist(const SweepArgs& A, int dim, int nbins, float rmax, unsigned long long* hist, cudaStream_t s);
+// The same three sweeps (3D) over the particles of the cells with flag != 0
+// only (the cells a neighbourhood sweep left), adding to out / hist without
+// zeroing them; the sum 1/r kind writes blocks_for(n) partials and no final
+// reduction.
+int launch_count_flagged(const SweepArgs& A, const unsigned char* flag, unsigned long long* out, cudaStream_t s);
+int launch_suminvr_flagged(const SweepArgs& A, const unsigned char* flag, double* partials, cudaStream_t s);
+int launch_hist_flagged(const SweepArgs& A, const unsigned char* flag, int nbins, float rmax,
+                        unsigned long long* hist, cudaStream_t s);
+int flagged_blocks(int n);
 int launch_force(const SweepArgs& A, int dim, int mode, const double* hinv, float* forces, double* grad,
                  const double* gE, const double* pos, double* partials, double* sums, double* energy,
                  double* virial, double* gradbox, cudaStream_t s);
@@ -158,6 +167,13 @@ struct HoodArgs {
   const int* slot;           // per original particle: position inside its cell
   int* mixed;                // work[6]: 1 when some cell is not swept by the half-shell path
   int half;                  // 1 when the half-shell path is tried for this launch
+  // scalar reductions of the staged half-shell sweep (launch_hood_scalar)
+  unsigned long long* count;  // pair count, added to
+  unsigned long long* hist;   // nbins counts of r in [0, rmax), added to
+  int nbins;
+  float rmax, hscale;         // hscale = nbins / rmax
+  float hxlim;                // min(nbins, rc hscale): bin coordinate limit of counted pairs
+  int hcopies, hstride;       // shared-memory copies of the histogram (a power of two) and their stride
 };
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,
                    HoodArgs* H);
@@ -171,6 +187,14 @@ size_t hood_smem_bytes();
 int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
                 double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
                 double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s);
+
+// Count (kind 0), sum 1/r (1) or distance histogram (2) over the half
+// stencil (A = half stencil, 3D): the staged neighbourhood sweep for the
+// cells that fit it, then the per-particle sweep for the others. The outputs
+// (count: 1 value, sum_inv_r: 1 value, hist: nbins values) are overwritten.
+int launch_hood_scalar(const SweepArgs& A, const HoodArgs& H, int* work, int kind, unsigned long long* count,
+                       double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
+                       float rmax, unsigned long long* hist, cudaStream_t s);
 
 // Two sets (cl_cross.cu): what 0 counts per query (count may be null) and their
 // total, 1 fills the pairs of each query's segment (start), 2 the per-query k

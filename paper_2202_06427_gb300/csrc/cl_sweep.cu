@@ -20,17 +20,30 @@
 // Precision: pair math in FP32 on cell-centred coordinates; per-thread FP32
 // partial sums (a few hundred terms); FP64 from the warp level up; partials
 // per CTA reduced in a fixed order.
+#include <algorithm>
+#include <cmath>
+
 #include "cl_sweep.cuh"
 
 namespace clk {
 
+// Particle p of the sweep, or A.n (none) when flag is given and p's cell is
+// not flagged: a neighbourhood sweep took that cell (3D).
+__device__ __forceinline__ int flagged_particle(const SweepArgs& A, const unsigned char* __restrict__ flag, int p) {
+  if (!flag || p >= A.n) return p;
+  const unsigned cc = A.cellc[p];
+  const int c = (int)(cc & 1023u) + A.nx * ((int)((cc >> 10) & 1023u) + A.ny * (int)(cc >> 20));
+  return flag[c] ? p : A.n;
+}
+
 template <int DIM>
-__global__ void __launch_bounds__(256) k_sweep_count(const __grid_constant__ SweepArgs A, unsigned long long* out) {
+__global__ void __launch_bounds__(256) k_sweep_count(const __grid_constant__ SweepArgs A, unsigned long long* out,
+                                                     const unsigned char* __restrict__ flag) {
   RedCount red;
   RedCount::Acc acc;
   red.init(acc);
   float4 pi;
-  sweep_particle<DIM>(A, red, acc, blockIdx.x * blockDim.x + threadIdx.x, pi);
+  sweep_particle<DIM>(A, red, acc, flagged_particle(A, flag, blockIdx.x * blockDim.x + threadIdx.x), pi);
   unsigned v = acc.n;
 #pragma unroll
   for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -39,10 +52,11 @@ __global__ void __launch_bounds__(256) k_sweep_count(const __grid_constant__ Swe
 
 // Scalar FP64 partial per CTA: sum 1/r (kind 0) or shifted-force energy (kind 1).
 template <int DIM, int KIND>
-__global__ void __launch_bounds__(256) k_sweep_scalar(const __grid_constant__ SweepArgs A, double* partials) {
+__global__ void __launch_bounds__(256) k_sweep_scalar(const __grid_constant__ SweepArgs A, double* partials,
+                                                      const unsigned char* __restrict__ flag) {
   float4 pi;
   double v[1];
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = flagged_particle(A, flag, blockIdx.x * blockDim.x + threadIdx.x);
   if (KIND == 0) {
     RedSumInvR red;
     RedSumInvR::Acc acc;
@@ -62,7 +76,8 @@ __global__ void __launch_bounds__(256) k_sweep_scalar(const __grid_constant__ Sw
 
 template <int DIM>
 __global__ void __launch_bounds__(256) k_sweep_hist(const __grid_constant__ SweepArgs A, int nbins, float rmax,
-                                                    unsigned long long* __restrict__ hist) {
+                                                    unsigned long long* __restrict__ hist,
+                                                    const unsigned char* __restrict__ flag) {
   extern __shared__ unsigned sh[];
   for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0u;
   __syncthreads();
@@ -73,7 +88,7 @@ __global__ void __launch_bounds__(256) k_sweep_hist(const __grid_constant__ Swee
   red.sh = sh;
   RedHist::Acc acc;
   float4 pi;
-  sweep_particle<DIM>(A, red, acc, blockIdx.x * blockDim.x + threadIdx.x, pi);
+  sweep_particle<DIM>(A, red, acc, flagged_particle(A, flag, blockIdx.x * blockDim.x + threadIdx.x), pi);
   __syncthreads();
   for (int b = threadIdx.x; b < nbins; b += blockDim.x)
     if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
@@ -139,6 +154,57 @@ __global__ void __launch_bounds__(256) k_sweep2_energy(const __grid_constant__ S
   sweep_particle2(A, red, acc, blockIdx.x * blockDim.x + threadIdx.x, pi);
   double v[1] = {(double)acc.e.x + (double)acc.e.y};
   block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+// Packed 3D counterparts of the count, sum 1/r and histogram sweeps.
+__global__ void __launch_bounds__(256) k_sweep2_count(const __grid_constant__ SweepArgs A, unsigned long long* out,
+                                                      const unsigned char* __restrict__ flag) {
+  Red2Count red;
+  Red2Count::Acc acc;
+  red.init(acc);
+  float4 pi;
+  sweep_particle2(A, red, acc, flagged_particle(A, flag, blockIdx.x * blockDim.x + threadIdx.x), pi);
+  unsigned v = acc.n;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(out, (unsigned long long)v);
+}
+
+__global__ void __launch_bounds__(256) k_sweep2_suminvr(const __grid_constant__ SweepArgs A, double* partials,
+                                                        const unsigned char* __restrict__ flag) {
+  Red2SumInvR red;
+  Red2SumInvR::Acc acc;
+  red.init(acc);
+  float4 pi;
+  sweep_particle2(A, red, acc, flagged_particle(A, flag, blockIdx.x * blockDim.x + threadIdx.x), pi);
+  double v[1] = {(double)acc.s.x + (double)acc.s.y};
+  block_sum_store<1>(v, partials + blockIdx.x);
+}
+
+__global__ void __launch_bounds__(256) k_sweep2_hist(const __grid_constant__ SweepArgs A, int nbins, float scale2,
+                                                     float xlim, unsigned long long* __restrict__ hist,
+                                                     const unsigned char* __restrict__ flag) {
+  extern __shared__ unsigned sh[];
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x) sh[b] = 0u;
+  __syncthreads();
+  Red2Hist red;
+  red.scale2 = scale2;
+  red.xlim = xlim;
+  red.sh = sh;
+  Red2Hist::Acc acc;
+  float4 pi;
+  sweep_particle2(A, red, acc, flagged_particle(A, flag, blockIdx.x * blockDim.x + threadIdx.x), pi);
+  __syncthreads();
+  for (int b = threadIdx.x; b < nbins; b += blockDim.x)
+    if (sh[b]) atomicAdd(&hist[b], (unsigned long long)sh[b]);
+}
+
+// Histogram parameters of the packed sweeps: scale^2 = (nbins / rmax)^2 and
+// the bin-coordinate limit min(nbins, rc nbins / rmax).
+static void hist_params(const SweepArgs& A, int nbins, float rmax, float* scale2, float* xlim) {
+  const double sc = (double)nbins / (double)rmax;
+  *scale2 = (float)(sc * sc);
+  *xlim = (float)std::min((double)nbins, std::sqrt((double)A.rc2) * sc);
 }
 
 template <int MODE>
@@ -328,8 +394,8 @@ int sweep_partials_needed(int n) { return (blocks_for(n) + kMaxPersistent) * 16;
 int launch_count(const SweepArgs& A, int dim, unsigned long long* out, cudaStream_t s) {
   if (cudaMemsetAsync(out, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
   if (A.n > 0) {
-    if (dim == 3) k_sweep_count<3><<<blocks_for(A.n), 256, 0, s>>>(A, out);
-    else k_sweep_count<2><<<blocks_for(A.n), 256, 0, s>>>(A, out);
+    if (dim == 3) k_sweep2_count<<<blocks_for(A.n), 256, 0, s>>>(A, out, nullptr);
+    else k_sweep_count<2><<<blocks_for(A.n), 256, 0, s>>>(A, out, nullptr);
   }
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
@@ -339,11 +405,11 @@ int launch_scalar(const SweepArgs& A, int dim, int kind, double* partials, doubl
   const int nb = blocks_for(A.n);
   if (A.n > 0) {
     if (dim == 3) {
-      if (kind == 0) k_sweep_scalar<3, 0><<<nb, 256, 0, s>>>(A, partials);
+      if (kind == 0) k_sweep2_suminvr<<<nb, 256, 0, s>>>(A, partials, nullptr);
       else k_sweep2_energy<<<nb, 256, 0, s>>>(A, partials);
     } else {
-      if (kind == 0) k_sweep_scalar<2, 0><<<nb, 256, 0, s>>>(A, partials);
-      else k_sweep_scalar<2, 1><<<nb, 256, 0, s>>>(A, partials);
+      if (kind == 0) k_sweep_scalar<2, 0><<<nb, 256, 0, s>>>(A, partials, nullptr);
+      else k_sweep_scalar<2, 1><<<nb, 256, 0, s>>>(A, partials, nullptr);
     }
   } else {
     if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
@@ -355,8 +421,36 @@ int launch_hist(const SweepArgs& A, int dim, int nbins, float rmax, unsigned lon
   if (cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nbins, s) != cudaSuccess) return CL_ERR_CUDA;
   const size_t smem = sizeof(unsigned) * nbins;
   if (A.n > 0) {
-    if (dim == 3) k_sweep_hist<3><<<blocks_for(A.n), 256, smem, s>>>(A, nbins, rmax, hist);
-    else k_sweep_hist<2><<<blocks_for(A.n), 256, smem, s>>>(A, nbins, rmax, hist);
+    if (dim == 3) {
+      float scale2, xlim;
+      hist_params(A, nbins, rmax, &scale2, &xlim);
+      k_sweep2_hist<<<blocks_for(A.n), 256, smem, s>>>(A, nbins, scale2, xlim, hist, nullptr);
+    }
+    else {
+      k_sweep_hist<2><<<blocks_for(A.n), 256, smem, s>>>(A, nbins, rmax, hist, nullptr);
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int flagged_blocks(int n) { return blocks_for(n); }
+
+int launch_count_flagged(const SweepArgs& A, const unsigned char* flag, unsigned long long* out, cudaStream_t s) {
+  if (A.n > 0) k_sweep2_count<<<blocks_for(A.n), 256, 0, s>>>(A, out, flag);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int launch_suminvr_flagged(const SweepArgs& A, const unsigned char* flag, double* partials, cudaStream_t s) {
+  if (A.n > 0) k_sweep2_suminvr<<<blocks_for(A.n), 256, 0, s>>>(A, partials, flag);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
+int launch_hist_flagged(const SweepArgs& A, const unsigned char* flag, int nbins, float rmax,
+                        unsigned long long* hist, cudaStream_t s) {
+  if (A.n > 0) {
+    float scale2, xlim;
+    hist_params(A, nbins, rmax, &scale2, &xlim);
+    k_sweep2_hist<<<blocks_for(A.n), 256, sizeof(unsigned) * nbins, s>>>(A, nbins, scale2, xlim, hist, flag);
   }
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }

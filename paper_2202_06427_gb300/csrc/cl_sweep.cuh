@@ -210,6 +210,54 @@ struct Red2Energy {
   }
 };
 
+// Pair count, sum 1/r and distance histogram (half shell), packed. The
+// histogram takes x = r nbins / rmax = sqrt(d2 scale^2) from the hardware
+// square root (relative error about 1e-7) and counts the pair in bin floor(x)
+// when x < xlim = min(nbins, rc scale); floor(x) is read from the low mantissa
+// bits of x + 2^23 added with rounding toward zero (exact for 0 <= x < 2^23),
+// which keeps the conversion off the special-function unit.
+__device__ __forceinline__ float sqrt_approx(float v) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+  return r;
+}
+
+struct Red2Count {
+  static constexpr bool kFull = false;
+  struct Acc { unsigned n; };
+  __device__ void init(Acc& a) const { a.n = 0; }
+  __device__ void hit2(Acc& a, float2, float2, float2, float2, bool h0, bool h1) const {
+    a.n += (h0 ? 1u : 0u) + (h1 ? 1u : 0u);
+  }
+};
+
+struct Red2SumInvR {
+  static constexpr bool kFull = false;
+  struct Acc { float2 s; };
+  __device__ void init(Acc& a) const { a.s = f2(0.f); }
+  __device__ void hit2(Acc& a, float2, float2, float2, float2 d2, bool h0, bool h1) const {
+    float2 y = rsqrt2(d2);
+    y.x = h0 ? y.x : 0.f;
+    y.y = h1 ? y.y : 0.f;
+    a.s = __fadd2_rn(a.s, y);
+  }
+};
+
+struct Red2Hist {
+  static constexpr bool kFull = false;
+  float scale2, xlim;
+  unsigned* sh;  // shared-memory histogram
+  struct Acc {};
+  __device__ void init(Acc&) const {}
+  __device__ void hit2(Acc&, float2, float2, float2, float2 d2, bool h0, bool h1) const {
+    const float2 s2 = __fmul2_rn(d2, f2(scale2));
+    const float2 x = make_float2(sqrt_approx(s2.x), sqrt_approx(s2.y));
+    const float2 t = __fadd2_rz(x, f2(8388608.0f));
+    if (h0 && x.x < xlim) atomicAdd(&sh[__float_as_int(t.x) - 0x4B000000], 1u);
+    if (h1 && x.y < xlim) atomicAdd(&sh[__float_as_int(t.y) - 0x4B000000], 1u);
+  }
+};
+
 // Forces and virial (optionally energy), full shell, with the opposite sign:
 // fsn = -u'(r)/r = y^3 - y/rc^2 and Gn = sum fsn r = -F_i. The virial needs no
 // per-pair work: writing r = x_j + S_o - x_i (cell-local coordinates, S_o the

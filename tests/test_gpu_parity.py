@@ -331,3 +331,61 @@ def test_workload_clustered_16m(cuda_ok):
     check_forces(dedx[torch.from_numpy(sample).cuda()].cpu().numpy(), -f_ref)
     check_matrix(vir1.cpu().numpy(), ref["virial"], TOL_W)
     check_matrix(dedh.cpu().numpy(), ref["dedh"], TOL_GB)
+
+
+def _mixed_occupancy(seed):
+    """Jittered lattice (spacing 1) in a box of side 40 with a spherical void
+    (radius 7: empty cells and cells with a few particles at its rim) and two
+    dense spheres (radius 3, spacing 0.5: hundreds of particles per cell of
+    side 4). At cell side 4 (rc 4, lcell 1) the mean occupancy is about 60."""
+    rng = np.random.default_rng(seed)
+    L = 40.0
+    h = np.eye(3) * L
+    h[1, 0], h[2, 0], h[2, 1] = 3.0, -2.0, 2.5
+    s = (np.stack(np.meshgrid(*[np.arange(40)] * 3, indexing="ij"), -1).reshape(-1, 3) + 0.5) / 40.0
+    bg = (s + rng.uniform(-0.15, 0.15, size=s.shape) / 40.0) @ h
+    void = np.array([20.0, 20.0, 20.0])
+    centres = np.array([[8.0, 9.0, 8.5], [31.0, 30.0, 31.5]])
+    g = np.stack(np.meshgrid(*[np.arange(-6, 7) * 0.5] * 3, indexing="ij"), -1).reshape(-1, 3)
+    g = g[np.linalg.norm(g, axis=1) <= 3.0]
+    keep = (np.linalg.norm(bg - void, axis=1) > 7.0) & \
+           (np.min(np.linalg.norm(bg[:, None, :] - centres[None], axis=2), axis=1) > 3.5)
+    parts = [bg[keep]] + [c + g + rng.uniform(-0.1, 0.1, size=g.shape) for c in centres]
+    x = np.vstack(parts)
+    return np.ascontiguousarray(x[rng.permutation(x.shape[0])]), h
+
+
+@pytest.mark.parametrize("lcell", [1, 2])
+def test_scalar_reductions_both_paths(cuda_ok, lcell):
+    """Count, sum 1/r and the histogram on a set mixing ordinary, empty,
+    sparse and very dense cells: at lcell 1 (about 60 particles per cell) the
+    staged neighbourhood sweep with its per-particle companion for the cells
+    it leaves, at lcell 2 (about 8) the per-particle sweep alone."""
+    P = _P()
+    x, h = _mixed_occupancy(517)
+    rc, nbins = 4.0, 37
+    ref = oracle.pair_map(x, h, rc, band=BAND, nbins=nbins, forces=False)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, lcell)
+    occ = x.shape[0] / P.cl_query(cl, "ncells")
+    assert (occ > 16) == (lcell == 1), occ
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    check_suminvr(P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item(), ref, rc)
+    check_hist(P.cl_map(cl, "hist", nbins=nbins)["hist"].cpu().numpy(), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+
+
+@pytest.mark.parametrize("lcell", [1, 2])
+@pytest.mark.parametrize("nbins,rmax_frac", [(1, 1.0), (4096, 0.6), (257, 1.3)])
+def test_hist_bins_and_rmax(cuda_ok, lcell, nbins, rmax_frac):
+    """Histogram at the bin-count limits and with rmax below and above the
+    cutoff (bins past the cutoff stay empty), on both sweep paths."""
+    P = _P()
+    x, h = _mixed_occupancy(518)
+    rc = 4.0
+    rmax = rmax_frac * rc
+    ref = oracle.pair_map(x, h, rc, band=BAND, nbins=nbins, rmax=rmax, forces=False)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, lcell)
+    hist = P.cl_map(cl, "hist", nbins=nbins, rmax=rmax)["hist"].cpu().numpy()
+    check_hist(hist, ref)
+    if rmax > rc:
+        assert hist[int(np.ceil(nbins * rc / rmax)):].sum() == 0
