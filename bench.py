@@ -64,10 +64,11 @@ FLOP_PER_HIT_HALF = 22
 # original index (4 B); the per-cell counts and offsets add 8 B per cell.
 BIN_BYTES_PER_PARTICLE = 44
 BIN_BYTES_PER_CELL = 8
-# DRAM bytes per launch of the dominant kernel from one ncu capture of its
-# current version (dram__bytes_read.sum + dram__bytes_write.sum), or None when
-# the kernel has changed since the counters were taken.
-SWEEP_DRAM_BYTES = None
+# DRAM bytes per launch of the dominant kernel (k_hood_half<3> on the 1M
+# lattice) from one ncu capture of its current version (dram__bytes_read.sum +
+# dram__bytes_write.sum = 36.39 + 0.03 MB), or None when the kernel has changed
+# since the counters were taken.
+SWEEP_DRAM_BYTES = 36_416_000
 FP32_LANES_PER_SM = 128
 # kernels of one headline step: bin, 2 scan, scatter; cell list, half-shell sweep,
 # its per-particle finish, full-shell sweep (exits when the half shell took the
@@ -606,7 +607,9 @@ def run_ours(args, rank, world, local):
     roofline = sweep_roofline(dev, clocks, cand_half, pairs, kms, cand,
                               "cl_energy_grad sweep kernels (neighbourhood sweep: energy + forces + box gradient)",
                               half_path)
-    roofline["traffic"] = SWEEP_DRAM_BYTES if workload == WORKLOAD else None
+    roofline["traffic"] = SWEEP_DRAM_BYTES if workload == WORKLOAD and half_path else None
+    if roofline["traffic"] is not None:
+        roofline["traffic_basis"] = "k_hood_half<3> (the dominant kernel of the sweep), one ncu capture"
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -179,8 +179,8 @@ int cl_scale(const double* scale_dev, const double* in_dev, double* out_dev, lon
 #define CL_INFO_SWEEP_CANDIDATES 13 /* candidate pairs the last 3D energy/force sweep evaluated (staged
                                        neighbours x home particles, own cell included); reads a counter */
 #define CL_INFO_SWEEP_HALF 14       /* 1 when the last 3D energy/force sweep with forces evaluated each
-                                       pair-image once (half shell: every non-empty cell on the fast
-                                       path), 0 when it took the full-shell kernels */
+                                       pair-image once (half shell; taken when both stencils have at
+                                       most 129 offsets), 0 when it took the full-shell kernels */
 int cl_query(const cl_list* cl, int what, long long* value, void* stream);
 
 /* Two sets of particles (Sec. 3.2, Code 8; Sec. 4.1): set A is the cell list

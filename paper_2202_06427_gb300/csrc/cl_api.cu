@@ -29,6 +29,7 @@ struct cl_list {
   double* sums;
   int* work;  // work counters of the persistent neighbourhood sweeps
   float4* hforce;  // per sorted particle: forces accumulated by the half-shell sweep (kept zero between launches)
+  int last_half;   // the last 3D energy/force sweep took the half-shell path
   unsigned long long* u64;
   // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
   int* pl_count;
@@ -365,7 +366,7 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
   if (!e) e = dev_alloc(&c->work, 8, &b);  // [0] work counter, [1] list length, [2..3] candidate counter,
-                                           // [4] dense cells, [5] their work counter, [6] mixed flag
+                                           // [4] dense cells, [5] their work counter
   if (!e && box->dim == 3) e = dev_alloc(&c->hforce, nn, &b);
   if (!e && box->dim == 3 && nn > 0 && cudaMemset(c->hforce, 0, sizeof(float4) * nn) != cudaSuccess) e = CL_ERR_CUDA;
   if (!e) e = dev_alloc(&c->u64, 8, &b);
@@ -421,9 +422,11 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       return clk::launch_scalar(*c->half, dim, 1, c->partials, c->sums, r->energy, s);
     case CL_RED_SF_ENERGY_FORCES_VIRIAL:
       if (!r->forces && c->n > 0) return CL_ERR_INVALID_ARG;
-      if (dim == 3 && c->n > 0)
+      if (dim == 3 && c->n > 0) {
+        c->last_half = clk::half_path_applies(*c->full, c->half, *c->hood, 0) ? 1 : 0;
         return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr,
                                 c->partials, hood_cap(c), c->sums, r->energy, r->virial, nullptr, s);
+      }
       return clk::launch_force(*c->full, dim, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr, c->partials,
                                c->sums, r->energy, r->virial, nullptr, s);
     case CL_RED_HIST: {
@@ -445,10 +448,12 @@ int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_p
                 double* virial_dev, void* stream) {
   if (!cc || !grad_energy_dev || (cc->n > 0 && !grad_pos_dev)) return CL_ERR_INVALID_ARG;
   cl_list* c = const_cast<cl_list*>(cc);
-  if (c->geo.dim == 3 && c->n > 0)
+  if (c->geo.dim == 3 && c->n > 0) {
+    c->last_half = clk::half_path_applies(*c->full, c->half, *c->hood, 1) ? 1 : 0;
     return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev,
                             c->pos, c->partials, hood_cap(c), c->sums, nullptr, virial_dev, grad_box_dev,
                             (cudaStream_t)stream);
+  }
   return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev, c->pos,
                            c->partials, c->sums, nullptr, virial_dev, grad_box_dev, (cudaStream_t)stream);
 }
@@ -458,9 +463,11 @@ int cl_energy_grad(const cl_list* cc, const double* scale_dev, double* energy_de
   if (!cc || !scale_dev || !energy_dev || (cc->n > 0 && !grad_pos_dev)) return CL_ERR_INVALID_ARG;
   cl_list* c = const_cast<cl_list*>(cc);
   cudaStream_t s = (cudaStream_t)stream;
-  if (c->geo.dim == 3 && c->n > 0)
+  if (c->geo.dim == 3 && c->n > 0) {
+    c->last_half = clk::half_path_applies(*c->full, c->half, *c->hood, 3) ? 1 : 0;
     return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 3, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
                             c->partials, hood_cap(c), c->sums, energy_dev, virial_dev, grad_box_dev, s);
+  }
   // 2D (and the empty list): the energy sweep, then the backward sweep
   int e = clk::launch_scalar(*c->half, c->geo.dim, 1, c->partials, c->sums, energy_dev, s);
   if (e) return e;
@@ -637,14 +644,9 @@ int cl_query(const cl_list* c, int what, long long* value, void* stream) {
       *value = what == CL_INFO_NONEMPTY ? m[1] : m[2];
       return CL_OK;
     }
-    case CL_INFO_SWEEP_HALF: {
-      int mixed = 1;
-      if (cudaMemcpyAsync(&mixed, c->work + 6, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return CL_ERR_CUDA;
-      if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
-      *value = (c->geo.dim == 3 && c->n > 0 && !mixed) ? 1 : 0;
+    case CL_INFO_SWEEP_HALF:
+      *value = c->last_half;
       return CL_OK;
-    }
     case CL_INFO_SWEEP_CANDIDATES: {
       unsigned long long v = 0;
       if (cudaMemcpyAsync(&v, c->work + 2, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;

@@ -724,10 +724,10 @@ __device__ __forceinline__ int run_count(const int* __restrict__ cell_start, int
 // (dense, *ndense of them); the other non-empty cells (fewer particles, or a
 // stencil larger than the table) are flagged 1 for the per-particle companion.
 // A cell whose staged neighbourhood overflows is moved to the dense list by
-// the sweep itself. With half != 0 (the half-shell path is tried), *mixed is
-// set when some non-empty cell is not on the list or holds more than kHCap
-// particles in its half stencil's cells (opk_half, noff_half entries), so
-// that the full-shell kernels take the launch instead.
+// the sweep itself. With half != 0 (the half-shell sweep takes the launch)
+// every non-empty cell is listed: on list when it holds at most kHome
+// particles and its half stencil's cells (opk_half, noff_half entries) at most
+// kHCap, on dense (the windowed cells) otherwise.
 __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_start, int ncells, int noff,
                                                    int* __restrict__ work, int* __restrict__ list,
                                                    unsigned char* __restrict__ flag, int* __restrict__ dense,
@@ -735,16 +735,14 @@ __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_
                                                    int noff_half, int nx, int ny, int nz) {
   const int half = H.half;
   const int* opk_half = H.opk[1];
-  int* mixed = H.mixed;
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned lt = (1u << (threadIdx.x & 31)) - 1u;
-  bool take = false, big = false, mix = false;
+  bool take = false, big = false;
   if (h < ncells) {
     const int nh = cell_start[h + 1] - cell_start[h];
-    take = nh >= kMinHome && nh <= kHome && noff <= kTab;
-    big = nh > kHome;
+    take = (half ? nh >= 1 : nh >= kMinHome) && nh <= kHome && noff <= kTab;
+    big = half ? (nh > 0 && !take) : nh > kHome;
     flag[h] = (nh > 0 && !take) ? (big ? 2 : 1) : 0;
-    mix = nh > 0 && !take;
     if (half && take) {
       const int cx = h % nx, cy = (h / nx) % ny, cz = h / (nx * ny);
       int cnt = 0, r0 = 0, px = 0, py = 0, pz = 0;
@@ -760,10 +758,12 @@ __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_
         py = oy;
         pz = oz;
       }
-      mix = mix || cnt > kHCap;
+      if (cnt > kHCap) {
+        take = false;
+        big = true;
+      }
     }
   }
-  if (__any_sync(0xffffffffu, mix) && (threadIdx.x & 31) == 0) atomicOr(mixed, 1);
   const unsigned m = __ballot_sync(0xffffffffu, take), mb = __ballot_sync(0xffffffffu, big);
   int base = 0, bbase = 0;
   if ((threadIdx.x & 31) == 0) {
@@ -806,10 +806,6 @@ __global__ void __launch_bounds__(256) k_hood_rest(const __grid_constant__ Sweep
                                                    double* __restrict__ grad, const double* __restrict__ gE,
                                                    const double* __restrict__ pos, double* __restrict__ partials) {
   constexpr bool GRAD = MODE == 1 || MODE == 3;
-  if (H.half && !*H.mixed) {  // the half-shell path took this launch: no flagged cells
-    if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
-    return;
-  }
   const float g = GRAD ? (float)*gE : 0.f;
   ThreadOut T;
   T.es = T.ec = 0.f;
@@ -1093,10 +1089,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   constexpr bool SCALAR = MODE >= 4;
   constexpr bool FORCE = MODE != 2 && !SCALAR, ENERGY = MODE != 1 && !SCALAR, HALF = MODE == 2 || SCALAR;
   constexpr bool GRAD = MODE == 1 || MODE == 3;
-  if (H.half && !*H.mixed) {  // the half-shell path took this launch
-    if (threadIdx.x < hood_nv(MODE)) partials[(size_t)blockIdx.x * hood_nv(MODE) + threadIdx.x] = 0.0;
-    return;
-  }
   extern __shared__ __align__(16) unsigned char smraw[];
   Smem& S = *reinterpret_cast<Smem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1370,10 +1362,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
 // boundary (T != 0) from their accumulated forces. In the partials layout of
 // the other sweeps (minus the sum over ordered pairs) this is -2 times it.
 //
-// The path is taken only when every non-empty cell is a fast-path cell whose
-// half neighbourhood fits kHCap (k_hood_list checks, and sets *mixed
-// otherwise); then no pair is left to the full-shell kernels, which exit, and
-// vice versa.
+// Cells whose particles or half neighbourhood exceed the buffers (more than
+// kHome particles, more than kHCap particles in the half stencil's cells)
+// take the windowed form of the same sweep: the half neighbourhood's row
+// segments are laid end to end and staged in windows of kHCap particles, each
+// window swept against the home particles in batches of kHome, and the pairs
+// within the cell are swept as a last window per batch (the cell's particles
+// from the batch's first on, ordered by index). Every non-empty cell is
+// swept, so the path covers the whole grid whenever both stencils fit the
+// table.
 
 struct HalfSmem {
   float4 ent[kHCap + 32];  // (x, y, z in the home frame, sorted position as int bits); 32 trash entries
@@ -1382,8 +1379,9 @@ struct HalfSmem {
   float4 own[kHome];       // the same with (x, y, z): the own cell's entries
   float hg[kHome][3];      // per home particle: sum of fsn r over its entries
   float4 otab[kTab];       // half stencil: (shift x, y, z, unwrapped offset as int bits)
+  int4 seg[kTab];          // windowed cells: row segments (first particle, flattened start, ebase, back | image << 1)
   unsigned short rowk[kTab + 1];
-  int nrows;
+  int nrows, nseg, ctot;
   float wmax[kWarps];
   int nf, nb, item, next;
   unsigned long long ncand;
@@ -1529,10 +1527,15 @@ constexpr int kChunk = 32 * kEnt;   // entries per chunk
 // entry, and (own cell) its home index, else a large value.
 struct SeqInfo {
   int nf, nb, nh;
+  int obase;  // own pass of a windowed cell: position j is own particle j + obase of the batch
 };
+template <bool OWNALL>
 __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q, int j, int& own, bool far_up) {
   own = 0x7fffffff;
-  if (j < q.nf) return S.ent[j];
+  if (j < q.nf) {
+    if (OWNALL) own = j + q.obase;
+    return S.ent[j];
+  }
   if (j < q.nf + q.nb) return S.ent[kHCap - q.nb + (j - q.nf)];
   if (j < q.nf + q.nb + q.nh) {
     own = j - q.nf - q.nb;
@@ -1547,8 +1550,9 @@ __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q,
 // when the entry comes after the home particle. The lane's entries' forces
 // (sum of fsn r, r = entry - home) accumulate in jx, jy, jz (pair k: positions
 // u = 2k, 2k + 1); each home particle's sum of fsn r over the chunk is
-// warp-summed per step into S.hg.
-template <bool MASK>
+// warp-summed per step into S.hg. OWNALL: the own pass of a windowed cell,
+// every entry an own-cell particle (index j + obase within the batch).
+template <bool MASK, bool OWNALL = false>
 __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int base, int nh, float rc2, float irc,
                                            float irc2, float2 (&jx)[kEnt / 2], float2 (&jy)[kEnt / 2],
                                            float2 (&jz)[kEnt / 2], float2& e) {
@@ -1557,8 +1561,8 @@ __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int b
   int own[kEnt];
 #pragma unroll
   for (int k = 0; k < kEnt / 2; ++k) {
-    const float4 a = seq_entry(S, sq, base + lane + 64 * k, own[2 * k], true);
-    const float4 b = seq_entry(S, sq, base + lane + 64 * k + 32, own[2 * k + 1], false);
+    const float4 a = seq_entry<OWNALL>(S, sq, base + lane + 64 * k, own[2 * k], true);
+    const float4 b = seq_entry<OWNALL>(S, sq, base + lane + 64 * k + 32, own[2 * k + 1], false);
     qx[k] = make_float2(a.x, b.x);
     qy[k] = make_float2(a.y, b.y);
     qz[k] = make_float2(a.z, b.z);
@@ -1634,7 +1638,226 @@ __device__ __forceinline__ void half_flush(const HoodArgs& H, const HalfSmem& S,
   }
 }
 
-template <int MODE>
+// ------------------------------------------------ windowed half-shell cells
+
+// Row segments of the half stencil at cell (cx, cy, cz) laid end to end, by
+// warp 0: S.seg[k] = (first particle, flattened start, ebase, back | image
+// << 1), S.nseg of them, S.ctot particles in all. A segment covers at least
+// one stencil entry, so there are at most kTab - 1.
+__device__ void half_segments(const SweepArgs& A, HalfSmem& S, int cx, int cy, int cz) {
+  const int lane = threadIdx.x & 31;
+  int nseg = 0;
+  for (int r0 = 0; r0 < S.nrows; r0 += 32) {
+    const int r = r0 + lane;
+    int ns = 0, img = 0;
+    if (r < S.nrows)
+      while (half_segment<0>(A, S, r, ns, cx, cy, cz, img).valid) ++ns;
+    int inc = ns;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      inc += lane >= o ? t : 0;
+    }
+    const int first = nseg + inc - ns;
+    for (int k = 0; k < ns; ++k) {
+      const RowSeg g = half_segment<0>(A, S, r, k, cx, cy, cz, img);
+      S.seg[first + k] = make_int4(g.p0, g.p1 - g.p0, g.ebase, g.back | (img << 1));  // .y: length for now
+    }
+    nseg += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  int total = 0;
+  for (int k0 = 0; k0 < nseg; k0 += 32) {
+    const int k = k0 + lane;
+    const int len = k < nseg ? S.seg[k].y : 0;
+    int inc = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      inc += lane >= o ? t : 0;
+    }
+    if (k < nseg) S.seg[k].y = total + inc - len;
+    total += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  if (lane == 0) {
+    S.nseg = nseg;
+    S.ctot = total;
+  }
+}
+
+// Staging of the flattened half-neighbourhood positions [w0, w1) (at most
+// kHCap): each position's segment by binary search over the starts, then the
+// shift, ball test and compaction of half_stage (T = 0 entries from the front,
+// T != 0 from the back).
+__device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w1, float top2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const int nseg = S.nseg;
+  for (int tb = w0 + warp * 32 * kStageBatch; tb < w1; tb += kWarps * 32 * kStageBatch) {
+    float4 v[kStageBatch];
+    unsigned c[kStageBatch];
+    int meta[kStageBatch], eb[kStageBatch];
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const int t = min(tb + 32 * u + lane, w1 - 1);
+      int lo = 0, hi = nseg;  // the last segment starting at or before t
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (S.seg[mid].y <= t) lo = mid;
+        else hi = mid;
+      }
+      const int4 sg = S.seg[lo];
+      const int p = sg.x + (t - sg.y);
+      v[u] = A.xs[p];
+      v[u].w = __int_as_float(p);
+      c[u] = A.cellc[p];
+      eb[u] = sg.z;
+      meta[u] = sg.w;
+    }
+    unsigned mf[kStageBatch], mb[kStageBatch];
+    int nfn = 0, nbn = 0;
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const float4 sh = S.otab[eb[u] + (int)(c[u] & 1023u)];
+      v[u].x += sh.x;
+      v[u].y += sh.y;
+      v[u].z += sh.z;
+      const bool keep = tb + 32 * u + lane < w1 &&
+                        fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, v[u].z * v[u].z)) < top2;
+      const bool back = (meta[u] & 1) != 0;
+      mf[u] = __ballot_sync(0xffffffffu, keep && !back);
+      mb[u] = __ballot_sync(0xffffffffu, keep && back);
+      nfn += __popc(mf[u]);
+      nbn += __popc(mb[u]);
+    }
+    int bf = 0, bb = 0;
+    if (lane == 0) {
+      if (nfn) bf = atomicAdd(&S.nf, nfn);
+      if (nbn) bb = atomicAdd(&S.nb, nbn);
+    }
+    bf = __shfl_sync(0xffffffffu, bf, 0);
+    bb = __shfl_sync(0xffffffffu, bb, 0);
+#pragma unroll
+    for (int u = 0; u < kStageBatch; ++u) {
+      const bool back = (meta[u] & 1) != 0;
+      const bool keep = ((back ? mb[u] : mf[u]) >> lane) & 1u;
+      const int e = half_slot(keep, back, back ? bb + __popc(mb[u] & lt) : bf + __popc(mf[u] & lt), lane);
+      S.ent[e] = v[u];
+      if (back && e < kHCap) S.img[e] = meta[u] >> 1;
+      bf += __popc(mf[u]);
+      bb += __popc(mb[u]);
+    }
+  }
+}
+
+// One batch of at most kHome home particles (sorted positions hp ..) against
+// the staged sequence sq: the chunks of the sequence from a counter, the
+// entries' forces flushed per chunk, the home particles' forces at the end.
+// OWNALL: the own pass (every entry an own-cell particle, masked by index).
+template <bool OWNALL>
+__device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, const SeqInfo& sq, int hp, int nbh,
+                           float2& e, float* wv) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int t = tid; t < kHome + 4; t += kThreads) {
+    if (t < nbh) {
+      const float4 hq = A.xs[hp + t];
+      S.home[t] = make_float4(-hq.x, -hq.y, -hq.z, __int_as_float(hp + t));
+    } else {
+      S.home[t] = make_float4(kFar, -kFar, kFar, __int_as_float(0));
+    }
+  }
+  if (tid == 0) S.next = 0;
+  __syncthreads();
+  const int nch = (sq.nf + sq.nb + kChunk - 1) / kChunk;
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(&S.next, 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= nch) break;
+    float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
+    const int base = c * kChunk;
+    half_chunk<OWNALL, OWNALL>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e);
+#pragma unroll
+    for (int k = 0; k < kEnt / 2; ++k) {
+      const int j0 = base + lane + 64 * k;
+      half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
+      half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+    }
+  }
+  __syncthreads();
+  if (tid < nbh) {
+    const float gx = S.hg[tid][0], gy = S.hg[tid][1], gz = S.hg[tid][2];
+    if (gx != 0.f || gy != 0.f || gz != 0.f) atomicAdd(&H.hforce[hp + tid], make_float4(-gx, -gy, -gz, 0.f));
+    S.hg[tid][0] = S.hg[tid][1] = S.hg[tid][2] = 0.f;
+  }
+  __syncthreads();
+}
+
+// A cell that does not fit the buffers: windows of its half neighbourhood,
+// each against the home particles in batches, then the pairs within the cell
+// (batch b against the particles from its first on). Returns the candidates.
+__device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, int hs, int nh,
+                                            int cx, int cy, int cz, float2& e, float* wv) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float d = 0.f;
+  for (int t = tid; t < nh; t += kThreads) {
+    const float4 hq = A.xs[hs + t];
+    d = fmaxf(d, fminf(sqrtf(fmaf(hq.x, hq.x, fmaf(hq.y, hq.y, hq.z * hq.z))), H.hd));
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+  if (lane == 0) S.wmax[warp] = d;
+  if (warp == 0) half_segments(A, S, cx, cy, cz);
+  __syncthreads();
+  float dmax = S.wmax[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) dmax = fmaxf(dmax, S.wmax[w]);
+  const float top = H.rc + dmax + H.eps;
+  const int C = S.ctot;
+  unsigned long long cand = 0;
+  for (int w0 = 0; w0 < C; w0 += kHCap) {
+    if (tid == 0) {
+      S.nf = 0;
+      S.nb = 0;
+    }
+    __syncthreads();
+    half_stage_window(A, S, w0, min(C, w0 + kHCap), top * top);
+    __syncthreads();
+    SeqInfo sq;
+    sq.nf = min(S.nf, kHCap);
+    sq.nb = min(S.nb, kHCap - sq.nf);
+    sq.nh = 0;
+    sq.obase = 0;
+    for (int b0 = 0; b0 < nh; b0 += kHome) {
+      const int nbh = min(kHome, nh - b0);
+      half_batch<false>(A, H, S, sq, hs + b0, nbh, e, wv);
+      cand += (unsigned long long)nbh * (unsigned long long)(sq.nf + sq.nb);
+    }
+  }
+  for (int b0 = 0; b0 < nh; b0 += kHome) {
+    const int nbh = min(kHome, nh - b0);
+    for (int o0 = b0; o0 < nh; o0 += kHCap) {
+      const int cnt = min(kHCap, nh - o0);
+      for (int j = tid; j < cnt; j += kThreads) {
+        const float4 q = A.xs[hs + o0 + j];
+        S.ent[j] = make_float4(q.x, q.y, q.z, __int_as_float(hs + o0 + j));
+      }
+      SeqInfo sq;
+      sq.nf = cnt;
+      sq.nb = 0;
+      sq.nh = 0;
+      sq.obase = o0 - b0;
+      half_batch<true>(A, H, S, sq, hs + b0, nbh, e, wv);  // its first barrier also covers the entries
+      cand += (unsigned long long)nbh * (unsigned long long)cnt -
+              (o0 == b0 ? (unsigned long long)nbh * (unsigned long long)(nbh + 1) / 2 : 0ull);
+    }
+  }
+  return cand;
+}
+
+// WIN = false: the fast-path cells (list); true: the windowed cells (dense),
+// from a counter of their own.
+template <int MODE, bool WIN>
 __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant__ SweepArgs A,
                                                            const __grid_constant__ HoodArgs H,
                                                            double* __restrict__ partials) {
@@ -1643,10 +1866,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
   HalfSmem& S = *reinterpret_cast<HalfSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NV = hood_nv(MODE);
-  if (*H.mixed) {  // the full-shell kernels take this launch
-    if (tid < NV) partials[(size_t)blockIdx.x * NV + tid] = 0.0;
-    return;
-  }
   for (int k = tid; k < kWarps * 16; k += kThreads) (&S.out[0][0])[k] = 0.0;
   for (int k = tid; k < A.noff && k < kTab; k += kThreads) {
     const Off& o = A.off[k];
@@ -1671,14 +1890,16 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
   }
   float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // lane's sum of (T.H) (x) f over its entries across the boundary
   float2 e = f2(0.f);
-  const int nlist = H.work[1];
+  const int ntot = WIN ? *H.ndense : H.work[1];
+  const int* items = WIN ? H.dense : H.list;
+  int* counter = WIN ? H.work + 5 : H.work;
   int next1 = 0;
-  if (tid == 0) next1 = atomicAdd(H.work, 1);
+  if (tid == 0) next1 = atomicAdd(counter, 1);
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      S.item = next1 < nlist ? H.list[next1] : -1;
-      if (next1 < nlist) next1 = atomicAdd(H.work, 1);
+      S.item = next1 < ntot ? items[next1] : -1;
+      if (next1 < ntot) next1 = atomicAdd(counter, 1);
       S.nf = 0;
       S.nb = 0;
       S.next = 0;
@@ -1689,6 +1910,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     const int hs = A.cell_start[h];
     const int nh = A.cell_start[h + 1] - hs;
     const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
+    constexpr bool win = WIN;
+    if (WIN) {
+      const unsigned long long cand = half_windowed(A, H, S, hs, nh, cx, cy, cz, e, wv);
+      if (tid == 0) S.ncand += cand;
+    } else {
     float d = 0.f;
     for (int t = tid; t < kHome + 4; t += kThreads) {
       if (t < nh) {
@@ -1715,6 +1941,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     sq.nf = nf;
     sq.nb = nb;
     sq.nh = nh;
+    sq.obase = 0;
     const int nseq = nf + nb + nh;
     const int nch = (nseq + kChunk - 1) / kChunk;
     const int cmask = (nf + nb) / kChunk;  // the first chunk holding own-cell positions
@@ -1737,6 +1964,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
         half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
       }
     }
+    }  // fast path
     // this cell's energy and boundary terms into the warp's FP64 sums
     {
       float v[8] = {wv[0], wv[1], wv[2], wv[3], wv[4], wv[5], ENERGY ? e.x + e.y : 0.f, 0.f};
@@ -1748,8 +1976,9 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
       e = f2(0.f);
     }
     __syncthreads();
-    // the home particles' forces: minus their sums of fsn r
-    if (tid < nh) {
+    // the home particles' forces: minus their sums of fsn r (the windowed
+    // path has added them per batch)
+    if (!win && tid < nh) {
       const float gx = S.hg[tid][0], gy = S.hg[tid][1], gz = S.hg[tid][2];
       if (gx != 0.f || gy != 0.f || gz != 0.f) atomicAdd(&H.hforce[hs + tid], make_float4(-gx, -gy, -gz, 0.f));
       S.hg[tid][0] = S.hg[tid][1] = S.hg[tid][2] = 0.f;
@@ -1783,10 +2012,6 @@ __global__ void __launch_bounds__(256) k_half_finish(const __grid_constant__ Swe
                                                      const double* __restrict__ pos, double* __restrict__ partials) {
   constexpr bool GRAD = MODE == 1 || MODE == 3;
   constexpr int NV = hood_nv(MODE);
-  if (*H.mixed) {
-    if (threadIdx.x < NV) partials[(size_t)blockIdx.x * NV + threadIdx.x] = 0.0;
-    return;
-  }
   const float g = GRAD ? (float)*gE : 0.f;
   float o[16];
 #pragma unroll
@@ -1919,14 +2144,23 @@ int half_grid(int mode) {
   const int bytes = (int)sizeof(HalfSmem);
   cudaError_t e;
   if (mode == 0) {
-    e = cudaFuncSetAttribute(k_hood_half<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<0>, kThreads, bytes);
+    e = cudaFuncSetAttribute(k_hood_half<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_hood_half<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<0, false>, kThreads, bytes);
   } else if (mode == 1) {
-    e = cudaFuncSetAttribute(k_hood_half<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<1>, kThreads, bytes);
+    e = cudaFuncSetAttribute(k_hood_half<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_hood_half<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<1, false>, kThreads, bytes);
   } else {
-    e = cudaFuncSetAttribute(k_hood_half<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<3>, kThreads, bytes);
+    e = cudaFuncSetAttribute(k_hood_half<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_hood_half<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<3, false>, kThreads, bytes);
   }
   if (e != cudaSuccess || per < 1) return 0;
   cached[mode].put(dev, sms * per);
@@ -1978,7 +2212,6 @@ int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int k
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
   H.ndense = work + 4;
-  H.mixed = work + 6;
   H.half = 0;
   H.count = count;
   H.hist = hist;
@@ -2056,75 +2289,85 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
   return CL_OK;
 }
 
+bool half_path_applies(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int mode) {
+  return Ahalf && mode != 2 && H.hforce && A.noff <= kTab && Ahalf->noff <= kTab && A.n > 0;
+}
+
 int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& Hin, int* work, int mode,
                 const double* hinv, float* forces, double* grad, const double* gE, const double* pos,
                 double* partials, long long partials_cap, double* sums, double* energy, double* virial,
                 double* gradbox, cudaStream_t s) {
   const int NV = hood_nv(mode);
-  const bool half = Ahalf && mode != 2 && Hin.hforce && A.noff <= kTab && Ahalf->noff <= kTab && A.n > 0;
-  const int nrest = (A.n + 255) / 256;  // CTAs of the companion sweep
-  const int ndc = dense_grid(mode);     // CTAs of the dense-cell sweep
-  int nb = hood_grid(mode);
-  int nhb = half ? half_grid(mode) : 0;
-  const int nfin = half ? std::min(nrest, 152 * 8) : 0;
-  if (nb <= 0 || ndc <= 0 || (half && nhb <= 0)) return CL_ERR_CUDA;
-  if (nb > Hin.ncells) nb = Hin.ncells;
-  if (nhb > Hin.ncells) nhb = Hin.ncells;
-  const long long room = partials_cap / NV - nrest - ndc - nfin;
-  if (nb + nhb > room) {
-    nb = (int)(room / 2);
-    nhb = half ? (int)(room - nb) : 0;
-  }
-  if (nb < 1 || (half && nhb < 1)) return CL_ERR_INVALID_ARG;
+  const bool half = half_path_applies(A, Ahalf, Hin, mode);
+  const int nrest = (A.n + 255) / 256;  // CTAs of the companion sweep (and bound of the finish grid)
+  const int final_mode = mode == 2 ? 1 : (mode == 0 ? 2 : (mode == 1 ? 3 : 4));
   HoodArgs H = Hin;
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
   H.ndense = work + 4;
-  H.mixed = work + 6;
   H.half = half ? 1 : 0;
   if (cudaMemsetAsync(work, 0, 8 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
                                                      H.ndense, H, half ? Ahalf->noff : 0, A.nx, A.ny, A.nz);
-  // partials: [half-shell sweep][its per-particle finish][full-shell sweep][companion][dense cells]
-  double* pfin = partials + (size_t)nhb * NV;
-  double* pfull = pfin + (size_t)nfin * NV;
-  double* rest = pfull + (size_t)nb * NV;
+  if (half) {
+    // every non-empty cell: fast-path or windowed half-shell sweep, then the
+    // per-particle finish; partials [sweep][finish]
+    // (the windowed kernel's CTAs exit at once when no cell needs it)
+    int nhb = half_grid(mode);
+    const int nfin = std::min(nrest, 152 * 8);
+    if (nhb <= 0) return CL_ERR_CUDA;
+    if (nhb > Hin.ncells) nhb = Hin.ncells;
+    if (2 * nhb > partials_cap / NV - nfin) nhb = (int)((partials_cap / NV - nfin) / 2);
+    if (nhb < 1) return CL_ERR_INVALID_ARG;
+    double* pwin = partials + (size_t)nhb * NV;
+    double* pfin = pwin + (size_t)nhb * NV;
+    const size_t hsmem = sizeof(HalfSmem);
+    if (mode == 0) {
+      k_hood_half<0, false><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
+      k_hood_half<0, true><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, pwin);
+      k_half_finish<0><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
+    } else if (mode == 1) {
+      k_hood_half<1, false><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
+      k_hood_half<1, true><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, pwin);
+      k_half_finish<1><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
+    } else {
+      k_hood_half<3, false><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
+      k_hood_half<3, true><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, pwin);
+      k_half_finish<3><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
+    }
+    return finish_reduction(final_mode, 3, hinv, 2 * nhb + nfin, NV, partials, sums, energy, virial, gradbox, gE, s);
+  }
+  // full-shell kernels (and the half-stencil energy, mode 2): partials
+  // [neighbourhood sweep][companion][dense cells]
+  const int ndc = dense_grid(mode);  // CTAs of the dense-cell sweep
+  int nb = hood_grid(mode);
+  if (nb <= 0 || ndc <= 0) return CL_ERR_CUDA;
+  if (nb > Hin.ncells) nb = Hin.ncells;
+  if (nb > partials_cap / NV - nrest - ndc) nb = (int)(partials_cap / NV - nrest - ndc);
+  if (nb < 1) return CL_ERR_INVALID_ARG;
+  double* rest = partials + (size_t)nb * NV;
   double* dpart = rest + (size_t)nrest * NV;
   const size_t smem = sizeof(Smem);
-  const size_t hsmem = sizeof(HalfSmem);
   const size_t dsmem = dense_smem_bytes(A.noff);
   if (mode == 0) {
-    if (half) {
-      k_hood_half<0><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
-      k_half_finish<0><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
-    }
-    k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
+    k_hood<0><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<0><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<0><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else if (mode == 1) {
-    if (half) {
-      k_hood_half<1><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
-      k_half_finish<1><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
-    }
-    k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
+    k_hood<1><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<1><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<1><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else if (mode == 2) {
-    k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
+    k_hood<2><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<2><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<2><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   } else {
-    if (half) {
-      k_hood_half<3><<<nhb, kThreads, hsmem, s>>>(*Ahalf, H, partials);
-      k_half_finish<3><<<nfin, 256, 0, s>>>(*Ahalf, H, forces, grad, gE, pos, pfin);
-    }
-    k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, pfull);
+    k_hood<3><<<nb, kThreads, smem, s>>>(A, H, forces, grad, gE, pos, partials);
     k_hood_rest<3><<<nrest, 256, 0, s>>>(A, H, forces, grad, gE, pos, rest);
     k_hood_dense<3><<<ndc, kDenseThreads, dsmem, s>>>(A, H, forces, grad, gE, pos, dpart);
   }
-  const int final_mode = mode == 2 ? 1 : (mode == 0 ? 2 : (mode == 1 ? 3 : 4));
-  return finish_reduction(final_mode, 3, hinv, nhb + nfin + nb + nrest + ndc, NV, partials, sums, energy, virial,
-                          gradbox, gE, s);
+  return finish_reduction(final_mode, 3, hinv, nb + nrest + ndc, NV, partials, sums, energy, virial, gradbox, gE,
+                          s);
 }
 
 }  // namespace clk

@@ -165,7 +165,6 @@ struct HoodArgs {
   float4* hforce;            // half-shell path: per sorted particle, accumulated force (n entries)
   const float4* xl;          // per original particle: local coordinate, w = packed cell (binning output)
   const int* slot;           // per original particle: position inside its cell
-  int* mixed;                // work[6]: 1 when some cell is not swept by the half-shell path
   int half;                  // 1 when the half-shell path is tried for this launch
   // scalar reductions of the staged half-shell sweep (launch_hood_scalar)
   unsigned long long* count;  // pair count, added to
@@ -182,8 +181,9 @@ size_t hood_smem_bytes();
 // stencil); 3: energy and the backward outputs.
 // partials_cap: doubles available in partials (sweep_partials_needed).
 // Ahalf (modes 0, 1, 3; may be null): the half stencil, for the half-shell
-// path taken when every non-empty cell fits it (H.hforce must then hold n
-// entries); the full-shell kernels take the launch otherwise.
+// path, taken when both stencils fit the kernels' table (H.hforce must then
+// hold n entries); the full-shell kernels take the launch otherwise.
+bool half_path_applies(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int mode);
 int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
                 double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
                 double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s);

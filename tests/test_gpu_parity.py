@@ -235,6 +235,36 @@ def test_all_in_one_cell_and_multi_image(cuda_ok):
     assert P.cl_query(cl2, "max_occupancy") >= 1
 
 
+def test_dense_single_cell_forces(cuda_ok):
+    """A cell holding more particles than the staging window (2,197 on a 0.1
+    lattice inside one cell of side 2, next to the periodic boundary) and a
+    sparse background: the windowed half-shell sweep with home batches and
+    several own-cell windows, forces and box gradient against the oracle.
+    (The box gradient's X = sum x (x) F carries the FP32 force error times the
+    raw position, so the pile sits near the origin.)"""
+    P = _P()
+    rng = np.random.default_rng(23)
+    h = np.array([[30.0, 0, 0], [0.0, 30.0, 0], [0.0, 0, 30.0]])
+    g = np.stack(np.meshgrid(*[np.arange(13) * 0.1] * 3, indexing="ij"), -1).reshape(-1, 3) + 0.3
+    bg = rng.uniform(0.0, 30.0, size=(6000, 3))
+    bg = bg[np.min(np.abs(bg[:, None, :] - (g.mean(0))[None, None, :]).max(axis=2), axis=1) > 1.2]
+    x = np.ascontiguousarray(np.vstack([g + rng.uniform(-0.01, 0.01, size=g.shape), bg])[rng.permutation(len(g) + len(bg))])
+    rc = 2.0
+    ref = oracle.pair_map(x, h, rc, band=BAND)
+    cl = P.cl_build(torch.from_numpy(x).cuda(), h, rc, 1)
+    assert P.cl_query(cl, "max_occupancy") > 1536
+    efv = P.cl_map(cl, "energy_forces_virial")
+    assert P.cl_query(cl, "sweep_half") == 1
+    check_energy(efv["energy"].item(), ref["energy"])
+    check_forces(efv["forces"].cpu().numpy(), ref["forces"])
+    check_matrix(efv["virial"].cpu().numpy(), ref["virial"], TOL_W)
+    e1, dedx, dedh, vir1 = P.cl_energy_grad(cl, want_virial=True)
+    check_energy(e1.item(), ref["energy"])
+    check_forces(dedx.cpu().numpy(), -ref["forces"])
+    check_matrix(dedh.cpu().numpy(), ref["dedh"], TOL_GB)
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+
+
 def test_errors_are_reported(cuda_ok):
     P = _P()
     pos = torch.zeros((4, 3), dtype=torch.float64, device="cuda")
