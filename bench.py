@@ -70,10 +70,11 @@ BIN_BYTES_PER_CELL = 8
 # since the counters were taken.
 SWEEP_DRAM_BYTES = 36_416_000
 FP32_LANES_PER_SM = 128
-# kernels of one headline step: bin, 2 scan, scatter; cell list, half-shell sweep,
-# its per-particle finish, full-shell sweep (exits when the half shell took the
-# grid), per-particle companion, dense-cell sweep, 2 reduce; 2 scale
-STEP_LAUNCHES = 14
+# kernels of one headline step: bin, 2 scan, scatter, packed cells (binning);
+# cell list, half-shell sweep of the fast-path cells, of the windowed cells
+# (exits at once when there are none), per-particle finish, 2 reduce
+# (cl_energy_grad); 2 scale (chain rule for positions and box)
+STEP_LAUNCHES = 13
 
 
 def parse():

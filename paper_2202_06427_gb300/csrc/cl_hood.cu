@@ -1866,6 +1866,11 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
   HalfSmem& S = *reinterpret_cast<HalfSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NV = hood_nv(MODE);
+  const int ntot = WIN ? *H.ndense : H.work[1];
+  if (ntot == 0) {  // no cell of this kind
+    if (tid < NV) partials[(size_t)blockIdx.x * NV + tid] = 0.0;
+    return;
+  }
   for (int k = tid; k < kWarps * 16; k += kThreads) (&S.out[0][0])[k] = 0.0;
   for (int k = tid; k < A.noff && k < kTab; k += kThreads) {
     const Off& o = A.off[k];
@@ -1890,7 +1895,6 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
   }
   float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // lane's sum of (T.H) (x) f over its entries across the boundary
   float2 e = f2(0.f);
-  const int ntot = WIN ? *H.ndense : H.work[1];
   const int* items = WIN ? H.dense : H.list;
   int* counter = WIN ? H.work + 5 : H.work;
   int next1 = 0;
