@@ -204,6 +204,7 @@ int run_build(cl_list* c, cudaStream_t s) {
   b.pos = c->pos;
   b.n = c->n;
   b.slot = c->slot;
+  b.big = c->hdense;  // free between sweeps: k_hood_list rewrites it on every launch
   b.xl = c->xl;
   b.counts = c->counts;
   b.cell_start = c->cell_start;

@@ -1382,6 +1382,8 @@ struct HalfSmem {
   int4 seg[kTab];          // windowed cells: row segments (first particle, flattened start, ebase, back | image << 1)
   unsigned short rowk[kTab + 1];
   int nrows, nseg, ctot;
+  int oct[9];              // windowed cells: octant ranges of the cell's particles
+  float bmin[kWarps][6];   // batch_ball: per-warp minima
   float wmax[kWarps];
   int nf, nb, item, next;
   unsigned long long ncand;
@@ -1687,9 +1689,11 @@ __device__ void half_segments(const SweepArgs& A, HalfSmem& S, int cx, int cy, i
 
 // Staging of the flattened half-neighbourhood positions [w0, w1) (at most
 // kHCap): each position's segment by binary search over the starts, then the
-// shift, ball test and compaction of half_stage (T = 0 entries from the front,
-// T != 0 from the back).
-__device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w1, float top2) {
+// shift, the test against the ball of centre b (home frame) and squared
+// radius top2, and the compaction of half_stage (T = 0 entries from the
+// front, T != 0 from the back).
+__device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w1, float bx, float by, float bz,
+                                  float top2) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   const int nseg = S.nseg;
@@ -1722,8 +1726,8 @@ __device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w
       v[u].x += sh.x;
       v[u].y += sh.y;
       v[u].z += sh.z;
-      const bool keep = tb + 32 * u + lane < w1 &&
-                        fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, v[u].z * v[u].z)) < top2;
+      const float ex = v[u].x - bx, ey = v[u].y - by, ez = v[u].z - bz;
+      const bool keep = tb + 32 * u + lane < w1 && fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < top2;
       const bool back = (meta[u] & 1) != 0;
       mf[u] = __ballot_sync(0xffffffffu, keep && !back);
       mb[u] = __ballot_sync(0xffffffffu, keep && back);
@@ -1793,45 +1797,110 @@ __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, c
   __syncthreads();
 }
 
-// A cell that does not fit the buffers: windows of its half neighbourhood,
-// each against the home particles in batches, then the pairs within the cell
-// (batch b against the particles from its first on). Returns the candidates.
-__device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, int hs, int nh,
-                                            int cx, int cy, int cz, float2& e, float* wv) {
+// Ball of a batch of home particles (sorted positions hp .. hp + nbh): the
+// middle of their bounding box (home frame) and the squared staging radius
+// (rc + their largest distance from it + the rounding margin)^2.
+__device__ void batch_ball(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, int hp, int nbh, float& bx,
+                           float& by, float& bz, float& top2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+  float v[6] = {kFar, kFar, kFar, kFar, kFar, kFar};  // min x, y, z and minus max x, y, z
+  if (tid < nbh) {
+    q = A.xs[hp + tid];
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = -q.x;
+    v[4] = -q.y;
+    v[5] = -q.z;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = fminf(v[k], __shfl_xor_sync(0xffffffffu, v[k], o));
+  if (lane < 6) S.bmin[warp][lane] = v[lane];
+  __syncthreads();
+  float m[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    m[k] = S.bmin[0][k];
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w) m[k] = fminf(m[k], S.bmin[w][k]);
+  }
+  bx = 0.5f * (m[0] - m[3]);
+  by = 0.5f * (m[1] - m[4]);
+  bz = 0.5f * (m[2] - m[5]);
   float d = 0.f;
-  for (int t = tid; t < nh; t += kThreads) {
-    const float4 hq = A.xs[hs + t];
-    d = fmaxf(d, fminf(sqrtf(fmaf(hq.x, hq.x, fmaf(hq.y, hq.y, hq.z * hq.z))), H.hd));
+  if (tid < nbh) {
+    const float ex = q.x - bx, ey = q.y - by, ez = q.z - bz;
+    d = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+  __syncthreads();  // every warp has read S.bmin
   if (lane == 0) S.wmax[warp] = d;
-  if (warp == 0) half_segments(A, S, cx, cy, cz);
   __syncthreads();
-  float dmax = S.wmax[0];
+  float dm = S.wmax[0];
 #pragma unroll
-  for (int w = 1; w < kWarps; ++w) dmax = fmaxf(dmax, S.wmax[w]);
-  const float top = H.rc + dmax + H.eps;
+  for (int w = 1; w < kWarps; ++w) dm = fmaxf(dm, S.wmax[w]);
+  const float top = H.rc + dm + H.eps;
+  top2 = top * top;
+}
+
+// A cell that does not fit the buffers: its half neighbourhood in windows,
+// each against the home particles in batches, then the pairs within the cell
+// (batch b against the particles from its first on). The batches of the
+// neighbourhood pass are the cell's particles in ranges of at most kHome,
+// split at the octant boundaries of their order (cells of kOctMin..kOctCap
+// particles are ordered by octant by the build), each with its own ball
+// (batch_ball), so the particles of a dense cell see about half the
+// candidates of the cell's ball. Returns the candidates.
+__device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, const HoodArgs& H, HalfSmem& S,
+                                                            int hs, int nh, int cx, int cy, int cz, float2& e,
+                                                            float* wv) {
+  const int tid = threadIdx.x;
+  if (threadIdx.x < 32) half_segments(A, S, cx, cy, cz);
+  // octant ranges of the cell's order: S.oct[g] .. S.oct[g + 1]
+  const bool octs = nh >= kOctMin && nh <= kOctCap;
+  if (tid < 9) S.oct[tid] = 0;
+  __syncthreads();
+  if (octs)
+    for (int t = tid; t < nh; t += kThreads) {
+      const float4 q = A.xs[hs + t];
+      atomicAdd(&S.oct[1 + ((q.x > 0.f ? 1 : 0) | (q.y > 0.f ? 2 : 0) | (q.z > 0.f ? 4 : 0))], 1);
+    }
+  __syncthreads();
+  if (tid == 0) {
+    if (octs)
+      for (int g = 0; g < 8; ++g) S.oct[g + 1] += S.oct[g];
+    else
+      for (int g = 1; g < 9; ++g) S.oct[g] = nh;  // one group
+  }
+  __syncthreads();
   const int C = S.ctot;
   unsigned long long cand = 0;
-  for (int w0 = 0; w0 < C; w0 += kHCap) {
-    if (tid == 0) {
-      S.nf = 0;
-      S.nb = 0;
-    }
-    __syncthreads();
-    half_stage_window(A, S, w0, min(C, w0 + kHCap), top * top);
-    __syncthreads();
-    SeqInfo sq;
-    sq.nf = min(S.nf, kHCap);
-    sq.nb = min(S.nb, kHCap - sq.nf);
-    sq.nh = 0;
-    sq.obase = 0;
-    for (int b0 = 0; b0 < nh; b0 += kHome) {
-      const int nbh = min(kHome, nh - b0);
-      half_batch<false>(A, H, S, sq, hs + b0, nbh, e, wv);
-      cand += (unsigned long long)nbh * (unsigned long long)(sq.nf + sq.nb);
+  for (int g = 0; g < 8; ++g) {
+    const int g0 = S.oct[g], g1 = S.oct[g + 1];
+    for (int b0 = g0; b0 < g1; b0 += kHome) {
+      const int nbh = min(kHome, g1 - b0);
+      float bx, by, bz, top2;
+      batch_ball(A, H, S, hs + b0, nbh, bx, by, bz, top2);
+      for (int w0 = 0; w0 < C; w0 += kHCap) {
+        if (tid == 0) {
+          S.nf = 0;
+          S.nb = 0;
+        }
+        __syncthreads();
+        half_stage_window(A, S, w0, min(C, w0 + kHCap), bx, by, bz, top2);
+        __syncthreads();
+        SeqInfo sq;
+        sq.nf = min(S.nf, kHCap);
+        sq.nb = min(S.nb, kHCap - sq.nf);
+        sq.nh = 0;
+        sq.obase = 0;
+        half_batch<false>(A, H, S, sq, hs + b0, nbh, e, wv);
+        cand += (unsigned long long)nbh * (unsigned long long)(sq.nf + sq.nb);
+      }
     }
   }
   for (int b0 = 0; b0 < nh; b0 += kHome) {

@@ -43,6 +43,11 @@ struct DevCache {
 constexpr int kMaxOff = 768;      // stencil entries (9^3 = 729 plus margin)
 constexpr int kMaxAxis = 1023;    // cells per axis (10-bit packing)
 constexpr int kMaxBins = 4096;    // histogram bins (shared-memory histogram)
+// Cells of kOctMin to kOctCap particles are ordered by the octant of their
+// particles' local coordinates (sign of x, y, z) when the list is built, so
+// that the 3D sweep can split their particles into compact groups.
+constexpr int kOctMin = 129;
+constexpr int kOctCap = 2048;
 
 // One neighbour-cell offset of the stencil.
 struct Off {
@@ -113,6 +118,7 @@ struct BuildBufs {
   int* meta;  // [0] error latch, [1] non-empty cells, [2] max occupancy
   float4* xs;
   unsigned* cellc;
+  int* big;  // ncells ints: the cells to order by octant (listed by the scan; meta[3] of them), or null
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
