@@ -1554,10 +1554,13 @@ __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q,
 // u = 2k, 2k + 1); each home particle's sum of fsn r over the chunk is
 // warp-summed per step into S.hg. OWNALL: the own pass of a windowed cell,
 // every entry an own-cell particle (index j + obase within the batch).
-template <bool MASK, bool OWNALL = false>
+// Scalar modes (MODE 4 count, 5 sum 1/r) evaluate the same candidates with
+// the reduction of scalar_pair and no forces: the count in cnt, sum 1/r in e.
+template <bool MASK, bool OWNALL = false, int MODE = 3>
 __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int base, int nh, float rc2, float irc,
                                            float irc2, float2 (&jx)[kEnt / 2], float2 (&jy)[kEnt / 2],
-                                           float2 (&jz)[kEnt / 2], float2& e) {
+                                           float2 (&jz)[kEnt / 2], float2& e, unsigned& cnt, const ScalarRed& R) {
+  constexpr bool SCALAR = MODE >= 4;
   const int lane = threadIdx.x & 31;
   float2 qx[kEnt / 2], qy[kEnt / 2], qz[kEnt / 2];
   int own[kEnt];
@@ -1569,6 +1572,17 @@ __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int b
     qy[k] = make_float2(a.y, b.y);
     qz[k] = make_float2(a.z, b.z);
     jx[k] = jy[k] = jz[k] = f2(0.f);
+  }
+  if (SCALAR) {
+    for (int h = 0; h < nh; ++h) {
+      const float4 hp = S.home[h];  // broadcast; negated coordinates
+#pragma unroll
+      for (int k = 0; k < kEnt / 2; ++k) {
+        const bool m0 = !MASK || own[2 * k] > h, m1 = !MASK || own[2 * k + 1] > h;
+        scalar_pair<MODE, MASK>(qx[k], qy[k], qz[k], f2(hp.x), f2(hp.y), f2(hp.z), m0, m1, R, cnt, e);
+      }
+    }
+    return;
   }
   for (int h0 = 0; h0 < nh; h0 += 4) {
     float v[16];
@@ -1758,9 +1772,10 @@ __device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w
 // the staged sequence sq: the chunks of the sequence from a counter, the
 // entries' forces flushed per chunk, the home particles' forces at the end.
 // OWNALL: the own pass (every entry an own-cell particle, masked by index).
-template <bool OWNALL>
+template <bool OWNALL, int MODE>
 __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, const SeqInfo& sq, int hp, int nbh,
-                           float2& e, float* wv) {
+                           float2& e, float* wv, unsigned& cnt, const ScalarRed& R) {
+  constexpr bool SCALAR = MODE >= 4;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int t = tid; t < kHome + 4; t += kThreads) {
     if (t < nbh) {
@@ -1780,16 +1795,18 @@ __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, c
     if (c >= nch) break;
     float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
     const int base = c * kChunk;
-    half_chunk<OWNALL, OWNALL>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e);
+    half_chunk<OWNALL, OWNALL, MODE>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+    if (!SCALAR) {
 #pragma unroll
-    for (int k = 0; k < kEnt / 2; ++k) {
-      const int j0 = base + lane + 64 * k;
-      half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
-      half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+      for (int k = 0; k < kEnt / 2; ++k) {
+        const int j0 = base + lane + 64 * k;
+        half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
+        half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+      }
     }
   }
   __syncthreads();
-  if (tid < nbh) {
+  if (!SCALAR && tid < nbh) {
     const float gx = S.hg[tid][0], gy = S.hg[tid][1], gz = S.hg[tid][2];
     if (gx != 0.f || gy != 0.f || gz != 0.f) atomicAdd(&H.hforce[hp + tid], make_float4(-gx, -gy, -gz, 0.f));
     S.hg[tid][0] = S.hg[tid][1] = S.hg[tid][2] = 0.f;
@@ -1855,9 +1872,10 @@ __device__ void batch_ball(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, i
 // particles are ordered by octant by the build), each with its own ball
 // (batch_ball), so the particles of a dense cell see about half the
 // candidates of the cell's ball. Returns the candidates.
+template <int MODE>
 __device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, const HoodArgs& H, HalfSmem& S,
                                                             int hs, int nh, int cx, int cy, int cz, float2& e,
-                                                            float* wv) {
+                                                            float* wv, unsigned& cnt, const ScalarRed& R) {
   const int tid = threadIdx.x;
   if (threadIdx.x < 32) half_segments(A, S, cx, cy, cz);
   // octant ranges of the cell's order: S.oct[g] .. S.oct[g + 1]
@@ -1898,7 +1916,7 @@ __device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, 
         sq.nb = min(S.nb, kHCap - sq.nf);
         sq.nh = 0;
         sq.obase = 0;
-        half_batch<false>(A, H, S, sq, hs + b0, nbh, e, wv);
+        half_batch<false, MODE>(A, H, S, sq, hs + b0, nbh, e, wv, cnt, R);
         cand += (unsigned long long)nbh * (unsigned long long)(sq.nf + sq.nb);
       }
     }
@@ -1906,18 +1924,18 @@ __device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, 
   for (int b0 = 0; b0 < nh; b0 += kHome) {
     const int nbh = min(kHome, nh - b0);
     for (int o0 = b0; o0 < nh; o0 += kHCap) {
-      const int cnt = min(kHCap, nh - o0);
-      for (int j = tid; j < cnt; j += kThreads) {
+      const int no = min(kHCap, nh - o0);
+      for (int j = tid; j < no; j += kThreads) {
         const float4 q = A.xs[hs + o0 + j];
         S.ent[j] = make_float4(q.x, q.y, q.z, __int_as_float(hs + o0 + j));
       }
       SeqInfo sq;
-      sq.nf = cnt;
+      sq.nf = no;
       sq.nb = 0;
       sq.nh = 0;
       sq.obase = o0 - b0;
-      half_batch<true>(A, H, S, sq, hs + b0, nbh, e, wv);  // its first barrier also covers the entries
-      cand += (unsigned long long)nbh * (unsigned long long)cnt -
+      half_batch<true, MODE>(A, H, S, sq, hs + b0, nbh, e, wv, cnt, R);  // its first barrier also covers the entries
+      cand += (unsigned long long)nbh * (unsigned long long)no -
               (o0 == b0 ? (unsigned long long)nbh * (unsigned long long)(nbh + 1) / 2 : 0ull);
     }
   }
@@ -1930,7 +1948,8 @@ template <int MODE, bool WIN>
 __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant__ SweepArgs A,
                                                            const __grid_constant__ HoodArgs H,
                                                            double* __restrict__ partials) {
-  constexpr bool ENERGY = MODE != 1;
+  constexpr bool ENERGY = MODE != 1 && MODE != 4 && MODE != 6;  // MODE 5 sums 1/r where the energy goes
+  constexpr bool SCALAR = MODE >= 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   HalfSmem& S = *reinterpret_cast<HalfSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1962,6 +1981,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     S.rowk[nr] = (unsigned short)(ne > 1 ? ne : 1);
     S.nrows = nr;
   }
+  // scalar modes (count, sum 1/r): the cutoff, the lane's count
+  static_assert(MODE != 6, "the histogram runs on k_hood<6>");
+  ScalarRed R;
+  R.rc2 = A.rc2;
+  R.scale2 = 0.f;
+  R.xlim = 0.f;
+  R.hist = nullptr;
+  unsigned cnt = 0;
   float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // lane's sum of (T.H) (x) f over its entries across the boundary
   float2 e = f2(0.f);
   const int* items = WIN ? H.dense : H.list;
@@ -1985,7 +2012,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     const int cx = h % A.nx, cy = (h / A.nx) % A.ny, cz = h / (A.nx * A.ny);
     constexpr bool win = WIN;
     if (WIN) {
-      const unsigned long long cand = half_windowed(A, H, S, hs, nh, cx, cy, cz, e, wv);
+      const unsigned long long cand = half_windowed<MODE>(A, H, S, hs, nh, cx, cy, cz, e, wv, cnt, R);
       if (tid == 0) S.ncand += cand;
     } else {
     float d = 0.f;
@@ -2028,13 +2055,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
       if (c >= nch) break;
       float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
       const int base = c * kChunk;
-      if (c < cmask) half_chunk<false>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e);
-      else half_chunk<true>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e);
+      if (c < cmask) half_chunk<false, false, MODE>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      else half_chunk<true, false, MODE>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      if (!SCALAR) {
 #pragma unroll
-      for (int k = 0; k < kEnt / 2; ++k) {
-        const int j0 = base + lane + 64 * k;
-        half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
-        half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+        for (int k = 0; k < kEnt / 2; ++k) {
+          const int j0 = base + lane + 64 * k;
+          half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
+          half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+        }
       }
     }
     }  // fast path
@@ -2051,7 +2080,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     __syncthreads();
     // the home particles' forces: minus their sums of fsn r (the windowed
     // path has added them per batch)
-    if (!win && tid < nh) {
+    if (!win && !SCALAR && tid < nh) {
       const float gx = S.hg[tid][0], gy = S.hg[tid][1], gz = S.hg[tid][2];
       if (gx != 0.f || gy != 0.f || gz != 0.f) atomicAdd(&H.hforce[hs + tid], make_float4(-gx, -gy, -gz, 0.f));
       S.hg[tid][0] = S.hg[tid][1] = S.hg[tid][2] = 0.f;
@@ -2060,9 +2089,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
   // per-CTA partials: -2 (T.H) (x) f sums, energy (each pair-image once)
   __syncthreads();
   if (tid == 0 && S.ncand) atomicAdd(H.cand, S.ncand);
+  if (MODE == 4) {
+    unsigned long long c = cnt;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0 && c) atomicAdd(H.count, c);
+  }
   if (tid < NV) {
     int src;
-    if (MODE == 2) src = 15;
+    if (MODE == 2 || SCALAR) src = 15;
     else if (tid < kVirN3) src = tid;
     else if (MODE == 0) src = 15;
     else if (tid < kVirN3 + 9) src = -1;  // X: from k_half_finish
@@ -2207,33 +2242,35 @@ int hood_grid(int mode) {
 size_t hood_smem_bytes() { return sizeof(Smem); }
 
 // Persistent CTAs of the half-shell sweep, per mode (0, 1, 3).
+// Shared memory of k_hood_half<mode> (the histogram mode, whose copies would
+// follow HalfSmem, is not launched: k_hood<6> is faster).
+size_t half_mode_smem(int) { return sizeof(HalfSmem); }
+
+template <int M>
+cudaError_t half_setup(int bytes, int* per) {
+  cudaError_t e = cudaFuncSetAttribute(k_hood_half<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hood_half<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_hood_half<M, false>, kThreads, bytes);
+  return e;
+}
+
+// Persistent CTAs of the half-shell sweep, per mode (0, 1, 3; scalar 4, 5);
+// also raises the kernels' shared-memory limit on the current device.
 int half_grid(int mode) {
-  static DevCache cached[4];
-  if (mode < 0 || mode > 3 || mode == 2) return 0;
+  static DevCache cached[6];
+  if (mode < 0 || mode > 5 || mode == 2) return 0;
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (const int c = cached[mode].get(dev)) return c;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const int bytes = (int)sizeof(HalfSmem);
+  const int bytes = (int)half_mode_smem(mode);
   cudaError_t e;
-  if (mode == 0) {
-    e = cudaFuncSetAttribute(k_hood_half<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_hood_half<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<0, false>, kThreads, bytes);
-  } else if (mode == 1) {
-    e = cudaFuncSetAttribute(k_hood_half<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_hood_half<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<1, false>, kThreads, bytes);
-  } else {
-    e = cudaFuncSetAttribute(k_hood_half<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_hood_half<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood_half<3, false>, kThreads, bytes);
+  switch (mode) {
+    case 0: e = half_setup<0>(bytes, &per); break;
+    case 1: e = half_setup<1>(bytes, &per); break;
+    case 3: e = half_setup<3>(bytes, &per); break;
+    case 4: e = half_setup<4>(bytes, &per); break;
+    default: e = half_setup<5>(bytes, &per); break;
   }
   if (e != cudaSuccess || per < 1) return 0;
   cached[mode].put(dev, sms * per);
@@ -2269,6 +2306,15 @@ int dense_grid(int mode) {
   return sms * per;
 }
 
+// Count and sum 1/r on the half-shell sweep (entry-major, every cell,
+// windowed where the buffers do not fit) rather than on the home-major
+// k_hood<4, 5> with the per-particle sweep for the cells it leaves. Measured
+// (CUDA events, one cl_map call): 16M clustered count 11.2 against 13.2 ms,
+// sum 1/r 12.3 against 16.7 ms; 1M lattice count 0.60 against 0.57 ms. The
+// histogram stays on k_hood<6> (1M lattice 0.93 against 1.05 ms, 16M
+// clustered 19.0 against 21.8 ms).
+inline bool scalar_half(int kind) { return kind != 2; }
+
 int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int kind, unsigned long long* count,
                        double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
                        float rmax, unsigned long long* hist, cudaStream_t s) {
@@ -2301,6 +2347,28 @@ int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int k
     if (kind != 1) return CL_OK;
     if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
     return finish_reduction(0, 3, nullptr, 1, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
+  }
+  if (scalar_half(kind) && A.noff <= kTab) {
+    // the half-shell sweep (fast-path and windowed cells) takes every cell
+    H.half = 1;
+    k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag,
+                                                       H.dense, H.ndense, H, A.noff, A.nx, A.ny, A.nz);
+    int nhb = half_grid(mode);
+    if (nhb <= 0) return CL_ERR_CUDA;
+    const size_t hsm = half_mode_smem(mode);
+    if (nhb > Hin.ncells) nhb = Hin.ncells;
+    if (kind == 1 && 2 * nhb > partials_cap) nhb = (int)(partials_cap / 2);
+    if (nhb < 1) return CL_ERR_INVALID_ARG;
+    if (kind == 0) {
+      k_hood_half<4, false><<<nhb, kThreads, hsm, s>>>(A, H, partials);
+      k_hood_half<4, true><<<nhb, kThreads, hsm, s>>>(A, H, partials + nhb);
+    } else {
+      k_hood_half<5, false><<<nhb, kThreads, hsm, s>>>(A, H, partials);
+      k_hood_half<5, true><<<nhb, kThreads, hsm, s>>>(A, H, partials + nhb);
+    }
+    if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
+    if (kind != 1) return CL_OK;
+    return finish_reduction(0, 3, nullptr, 2 * nhb, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
   }
   k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
                                                      H.ndense, H, 0, A.nx, A.ny, A.nz);
