@@ -309,7 +309,10 @@ typedef struct {
  * are the cell offsets (cells x-fastest). off_half[0] / off_full[0] is the
  * own cell; the half stencil holds the lexicographically positive offsets,
  * the full stencil all of them. All pointers are device memory owned by the
- * handle, valid until the next cl_update or cl_free. */
+ * handle, valid until the next cl_update or cl_free. The order of the
+ * particles within a cell is not fixed: the 3D sweeps may reorder the
+ * particles of cells of more than 128 particles by octant (xs and cellc stay
+ * consistent; cell_start does not change). */
 typedef struct {
   int dim;
   int n;

@@ -30,6 +30,7 @@ struct cl_list {
   int* work;  // work counters of the persistent neighbourhood sweeps
   float4* hforce;  // per sorted particle: forces accumulated by the half-shell sweep (kept zero between launches)
   int last_half;   // the last 3D energy/force sweep took the half-shell path
+  int lists_half;  // hlist / hdense / work[6..7] hold the half-shell work lists of the current cell list
   unsigned long long* u64;
   // neighbour-list workspace, allocated on the first CL_RED_PAIRLIST call
   int* pl_count;
@@ -204,7 +205,7 @@ int run_build(cl_list* c, cudaStream_t s) {
   b.pos = c->pos;
   b.n = c->n;
   b.slot = c->slot;
-  b.big = c->hdense;  // free between sweeps: k_hood_list rewrites it on every launch
+  c->lists_half = 0;  // new cell contents: the sweeps' work lists are rebuilt
   b.xl = c->xl;
   b.counts = c->counts;
   b.cell_start = c->cell_start;
@@ -277,6 +278,7 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
   // hflag / hlist: per-cell flags and the flagged cells (shared with the
   // neighbourhood sweep, which rewrites them on every launch); pl_meta[4]: their number
   const int cap = pairs_stage_cap(c->geo, c->n, ball2);
+  c->lists_half = 0;  // the pair list's passes use the list buffers
   if ((e = clk::launch_pairs_count(*c->full, dim, ball2, cap, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, s)))
     return e;
   if ((e = clk::launch_scan64(c->pl_count, c->n, c->pl_tiles, c->pl_start, c->pl_meta, s))) return e;
@@ -366,8 +368,8 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = dev_alloc(&c->meta, 4, &b);
   if (!e) e = dev_alloc(&c->partials, (size_t)clk::sweep_partials_needed(c->n), &b);
   if (!e) e = dev_alloc(&c->sums, 32, &b);
-  if (!e) e = dev_alloc(&c->work, 8, &b);  // [0] work counter, [1] list length, [2..3] candidate counter,
-                                           // [4] dense cells, [5] their work counter
+  if (!e) e = dev_alloc(&c->work, 8, &b);  // [0] work counter, [2..3] candidate counter, [5] the dense
+                                           // cells' work counter, [6] list length, [7] dense cells
   if (!e && box->dim == 3) e = dev_alloc(&c->hforce, nn, &b);
   if (!e && box->dim == 3 && nn > 0 && cudaMemset(c->hforce, 0, sizeof(float4) * nn) != cudaSuccess) e = CL_ERR_CUDA;
   if (!e) e = dev_alloc(&c->u64, 8, &b);
@@ -407,26 +409,26 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       if (!r->count) return CL_ERR_INVALID_ARG;
       if (scalar_staged(c))
         return clk::launch_hood_scalar(*c->half, *c->hood, c->work, 0, r->count, c->partials, hood_cap(c), c->sums,
-                                       nullptr, 0, 0.f, nullptr, s);
+                                       nullptr, 0, 0.f, nullptr, s, &c->lists_half);
       return clk::launch_count(*c->half, dim, r->count, s);
     case CL_RED_SUM_INV_R:
       if (!r->sum_inv_r) return CL_ERR_INVALID_ARG;
       if (scalar_staged(c))
         return clk::launch_hood_scalar(*c->half, *c->hood, c->work, 1, nullptr, c->partials, hood_cap(c), c->sums,
-                                       r->sum_inv_r, 0, 0.f, nullptr, s);
+                                       r->sum_inv_r, 0, 0.f, nullptr, s, &c->lists_half);
       return clk::launch_scalar(*c->half, dim, 0, c->partials, c->sums, r->sum_inv_r, s);
     case CL_RED_SF_ENERGY:
       if (!r->energy) return CL_ERR_INVALID_ARG;
       if (dim == 3 && c->n > 0)
         return clk::launch_hood(*c->half, nullptr, *c->hood, c->work, 2, c->geo.hinv, nullptr, nullptr, nullptr, nullptr,
-                                c->partials, hood_cap(c), c->sums, r->energy, nullptr, nullptr, s);
+                                c->partials, hood_cap(c), c->sums, r->energy, nullptr, nullptr, s, &c->lists_half);
       return clk::launch_scalar(*c->half, dim, 1, c->partials, c->sums, r->energy, s);
     case CL_RED_SF_ENERGY_FORCES_VIRIAL:
       if (!r->forces && c->n > 0) return CL_ERR_INVALID_ARG;
       if (dim == 3 && c->n > 0) {
         c->last_half = clk::half_path_applies(*c->full, c->half, *c->hood, 0) ? 1 : 0;
         return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr,
-                                c->partials, hood_cap(c), c->sums, r->energy, r->virial, nullptr, s);
+                                c->partials, hood_cap(c), c->sums, r->energy, r->virial, nullptr, s, &c->lists_half);
       }
       return clk::launch_force(*c->full, dim, 0, c->geo.hinv, r->forces, nullptr, nullptr, nullptr, c->partials,
                                c->sums, r->energy, r->virial, nullptr, s);
@@ -435,7 +437,7 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       double rmax = params->rmax > 0 ? params->rmax : c->geo.rc;
       if (scalar_staged(c))
         return clk::launch_hood_scalar(*c->half, *c->hood, c->work, 2, nullptr, c->partials, hood_cap(c), c->sums,
-                                       nullptr, params->nbins, (float)rmax, r->hist, s);
+                                       nullptr, params->nbins, (float)rmax, r->hist, s, &c->lists_half);
       return clk::launch_hist(*c->half, dim, params->nbins, (float)rmax, r->hist, s);
     }
     case CL_RED_PAIRLIST:
@@ -453,7 +455,7 @@ int cl_backward(const cl_list* cc, const double* grad_energy_dev, double* grad_p
     c->last_half = clk::half_path_applies(*c->full, c->half, *c->hood, 1) ? 1 : 0;
     return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev,
                             c->pos, c->partials, hood_cap(c), c->sums, nullptr, virial_dev, grad_box_dev,
-                            (cudaStream_t)stream);
+                            (cudaStream_t)stream, &c->lists_half);
   }
   return clk::launch_force(*c->full, c->geo.dim, 1, c->geo.hinv, nullptr, grad_pos_dev, grad_energy_dev, c->pos,
                            c->partials, c->sums, nullptr, virial_dev, grad_box_dev, (cudaStream_t)stream);
@@ -467,7 +469,8 @@ int cl_energy_grad(const cl_list* cc, const double* scale_dev, double* energy_de
   if (c->geo.dim == 3 && c->n > 0) {
     c->last_half = clk::half_path_applies(*c->full, c->half, *c->hood, 3) ? 1 : 0;
     return clk::launch_hood(*c->full, c->half, *c->hood, c->work, 3, c->geo.hinv, nullptr, grad_pos_dev, scale_dev, c->pos,
-                            c->partials, hood_cap(c), c->sums, energy_dev, virial_dev, grad_box_dev, s);
+                            c->partials, hood_cap(c), c->sums, energy_dev, virial_dev, grad_box_dev, s,
+                            &c->lists_half);
   }
   // 2D (and the empty list): the energy sweep, then the backward sweep
   int e = clk::launch_scalar(*c->half, c->geo.dim, 1, c->partials, c->sums, energy_dev, s);

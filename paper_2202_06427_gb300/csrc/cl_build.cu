@@ -15,7 +15,8 @@
 //                  ("vector of lists ... an immutable copy of the particle
 //                  coordinates and index", Sec. 2.8).
 //   k_cellc        the packed cell of every sorted particle, cell by cell.
-//   k_octsort      cells of kOctMin..kOctCap particles ordered by the octant
+//   k_octsort      (launched by the 3D half-shell sweep on its windowed cells)
+//                  cells of kOctMin..kOctCap particles ordered by the octant
 //                  of their local coordinates (slots updated to match).
 // Per particle the build reads its FP64 position once (24 B) and moves 20 B
 // through k_bin's output (local coordinate with the packed cell, slot) to the
@@ -262,13 +263,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int* __restr
 // Per tile: the sum of the tiles before it (read straight from the tile sums,
 // so no separate pass scans them), then the rescan of the tile's counts ->
 // cell_start; the last tile also writes cell_start[ncells] = total.
-// With big != null, the cells of kOctMin..kOctCap particles are appended to
-// big (nbig of them).
 template <class T>
 __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int* __restrict__ counts, long long ncells,
                                                             const T* __restrict__ tile_sum,
-                                                            T* __restrict__ cell_start, int* __restrict__ big,
-                                                            int* __restrict__ nbig) {
+                                                            T* __restrict__ cell_start) {
   __shared__ T part[kScanThreads / 32];
   T before = 0;
   for (int t = threadIdx.x; t < (int)blockIdx.x; t += kScanThreads) before += tile_sum[t];
@@ -296,24 +294,15 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const int* __restri
     run += v[k];
   }
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) cell_start[ncells] = run;
-  if (big) {
-#pragma unroll
-    for (int k = 0; k < kScanPer; ++k) {
-      const bool b = v[k] >= kOctMin && v[k] <= kOctCap;
-      const unsigned m = __ballot_sync(0xffffffffu, b);
-      if (!m) continue;
-      int at = 0;
-      if ((threadIdx.x & 31) == __ffs(m) - 1) at = atomicAdd(nbig, __popc(m));
-      at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
-      if (b) big[at + __popc(m & ((1u << (threadIdx.x & 31)) - 1u))] = (int)(base + k);
-    }
-  }
 }
 
-// Orders the particles of each listed cell by the octant of their local
-// coordinate (key = (x > 0) | (y > 0) << 1 | (z > 0) << 2): a counting sort
-// through shared memory, writing the cell's range of xs back in key order and
-// each moved particle's slot. One CTA per cell, persistent over the list.
+// Orders the particles of each listed cell of kOctMin..kOctCap particles by
+// the octant of their local coordinate (key = (x > 0) | (y > 0) << 1 |
+// (z > 0) << 2): a counting sort through shared memory, writing the cell's
+// range of xs back in key order and each moved particle's slot. The order of
+// particles within a cell is free (every sweep indexes them through xs.w and
+// slot), so the cell list stays valid. One CTA per cell, persistent over the
+// list; other listed cells are skipped.
 __global__ void __launch_bounds__(256) k_octsort(const int* __restrict__ big, const int* __restrict__ nbig,
                                                 const int* __restrict__ cell_start, float4* __restrict__ xs,
                                                 int* __restrict__ slot) {
@@ -322,7 +311,8 @@ __global__ void __launch_bounds__(256) k_octsort(const int* __restrict__ big, co
   const int nb = *nbig;
   for (int q = blockIdx.x; q < nb; q += gridDim.x) {
     const int c = big[q];
-    const int hs = cell_start[c], nh = cell_start[c + 1] - hs;  // kOctMin <= nh <= kOctCap
+    const int hs = cell_start[c], nh = cell_start[c + 1] - hs;
+    if (nh < kOctMin || nh > kOctCap) continue;  // uniform over the CTA
     if (threadIdx.x < 8) cnt[threadIdx.x] = 0;
     __syncthreads();
     for (int t = threadIdx.x; t < nh; t += blockDim.x) {
@@ -409,6 +399,12 @@ __global__ void __launch_bounds__(256) k_cellc(long long ncells, int nx, int ny,
 
 
 
+int launch_octsort(const int* cells, const int* ncells_listed, const int* cell_start, float4* xs, int* slot,
+                   cudaStream_t s) {
+  k_octsort<<<152 * 4, 256, 0, s>>>(cells, ncells_listed, cell_start, xs, slot);
+  return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
+}
+
 int scan_tiles_for(long long ncells) { return (int)((ncells + kScanTile - 1) / kScanTile); }
 
 // Enqueue the whole binning pipeline on `s`. Returns CL_OK or CL_ERR_CUDA.
@@ -447,14 +443,11 @@ int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s) {
     }
   }
   k_scan_reduce<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.meta);
-  if (b.big && g.dim == 3 && cudaMemsetAsync(b.meta + 3, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
-  k_scan_final<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start,
-                                                    g.dim == 3 ? b.big : nullptr, b.meta + 3);
+  k_scan_final<int><<<ntiles, kScanThreads, 0, s>>>(b.counts, nc, b.tile_sum, b.cell_start);
   if (b.n > 0) {
     k_scatter<<<blocks, 256, 0, s>>>(b.n, g.n[0], g.n[1], b.slot, b.xl, b.cell_start, b.xs);
     const long long cb = std::min<long long>((nc + 255) / 256, 152 * 8);
     k_cellc<<<(int)cb, 256, 0, s>>>(nc, g.n[0], g.n[1], b.cell_start, b.cellc);
-    if (b.big && g.dim == 3) k_octsort<<<152 * 4, 256, 0, s>>>(b.big, b.meta + 3, b.cell_start, b.xs, b.slot);
   }
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
@@ -472,7 +465,7 @@ int launch_scan64(const int* counts, long long n, long long* tile_sum, long long
   if (cudaMemsetAsync(meta + 1, 0, sizeof(int) * 2, s) != cudaSuccess) return CL_ERR_CUDA;
   if (ntiles == 0) return cudaMemsetAsync(start, 0, sizeof(long long), s) == cudaSuccess ? CL_OK : CL_ERR_CUDA;
   k_scan_reduce<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, meta);
-  k_scan_final<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, start, nullptr, nullptr);
+  k_scan_final<long long><<<ntiles, kScanThreads, 0, s>>>(counts, n, tile_sum, start);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 

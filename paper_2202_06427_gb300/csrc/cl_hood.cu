@@ -696,7 +696,7 @@ __device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs&
 }
 
 // Work lists: cells with kMinHome..kHome particles (and a stencil that fits
-// the table) go to the neighbourhood sweep (list, work[1] of them); cells with
+// the table) go to the neighbourhood sweep (list, work[6] of them); cells with
 // more than kHome particles are flagged 2 and listed for the dense-cell sweep
 // (dense, *ndense of them); the other non-empty cells (fewer particles, or a
 // stencil larger than the table) are flagged 1 for the per-particle companion.
@@ -719,7 +719,7 @@ __device__ __forceinline__ int run_count(const int* __restrict__ cell_start, int
 }
 
 // Work lists: cells with kMinHome..kHome particles (and a stencil that fits
-// the table) go to the neighbourhood sweep (list, work[1] of them); cells with
+// the table) go to the neighbourhood sweep (list, work[6] of them); cells with
 // more than kHome particles are flagged 2 and listed for the dense-cell sweep
 // (dense, *ndense of them); the other non-empty cells (fewer particles, or a
 // stencil larger than the table) are flagged 1 for the per-particle companion.
@@ -767,7 +767,7 @@ __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_
   const unsigned m = __ballot_sync(0xffffffffu, take), mb = __ballot_sync(0xffffffffu, big);
   int base = 0, bbase = 0;
   if ((threadIdx.x & 31) == 0) {
-    if (m) base = atomicAdd(work + 1, __popc(m));
+    if (m) base = atomicAdd(work + 6, __popc(m));
     if (mb) bbase = atomicAdd(ndense, __popc(mb));
   }
   base = __shfl_sync(0xffffffffu, base, 0);
@@ -1118,7 +1118,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
   // atomic's latency overlaps whole cells, and every thread prefetches into L1
   // the cell ranges it will read for the next cell while this one is swept.
   if (tid == 0) S.ncand = 0;
-  const int nlist = H.work[1];
+  const int nlist = H.work[6];
   int next1 = 0, next2 = 0;
   if (tid == 0) {
     next1 = atomicAdd(H.work, 1);
@@ -1954,7 +1954,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
   HalfSmem& S = *reinterpret_cast<HalfSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NV = hood_nv(MODE);
-  const int ntot = WIN ? *H.ndense : H.work[1];
+  const int ntot = WIN ? *H.ndense : H.work[6];
   if (ntot == 0) {  // no cell of this kind
     if (tid < NV) partials[(size_t)blockIdx.x * NV + tid] = 0.0;
     return;
@@ -2317,7 +2317,7 @@ inline bool scalar_half(int kind) { return kind != 2; }
 
 int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int kind, unsigned long long* count,
                        double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
-                       float rmax, unsigned long long* hist, cudaStream_t s) {
+                       float rmax, unsigned long long* hist, cudaStream_t s, int* lists_half) {
   const int mode = 4 + kind;
   if (kind < 0 || kind > 2) return CL_ERR_INVALID_ARG;
   if (kind == 2 && (nbins < 1 || nbins > kMaxBins || !(rmax > 0.f))) return CL_ERR_INVALID_ARG;
@@ -2330,7 +2330,7 @@ int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int k
   HoodArgs H = Hin;
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
-  H.ndense = work + 4;
+  H.ndense = work + 7;
   H.half = 0;
   H.count = count;
   H.hist = hist;
@@ -2340,7 +2340,9 @@ int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int k
   H.hxlim = kind == 2 ? (float)std::min((double)nbins, (double)Hin.rc * ((double)nbins / rmax)) : 0.f;
   H.hcopies = kind == 2 ? hist_copies(nbins) : 1;
   H.hstride = kind == 2 ? hist_stride(nbins) : 0;
-  if (cudaMemsetAsync(work, 0, 8 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  const bool half = scalar_half(kind) && A.noff <= kTab;
+  const bool reuse = half && lists_half && *lists_half;  // the half-shell work lists of this cell list are built
+  if (cudaMemsetAsync(work, 0, (reuse ? 6 : 8) * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if (kind == 0 && cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
   if (kind == 2 && cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nbins, s) != cudaSuccess) return CL_ERR_CUDA;
   if (A.n <= 0) {
@@ -2348,11 +2350,17 @@ int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int k
     if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
     return finish_reduction(0, 3, nullptr, 1, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
   }
-  if (scalar_half(kind) && A.noff <= kTab) {
+  if (lists_half) *lists_half = half ? 1 : 0;
+  if (half) {
     // the half-shell sweep (fast-path and windowed cells) takes every cell
     H.half = 1;
-    k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag,
-                                                       H.dense, H.ndense, H, A.noff, A.nx, A.ny, A.nz);
+    if (!reuse) {
+      k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag,
+                                                         H.dense, H.ndense, H, A.noff, A.nx, A.ny, A.nz);
+      if (launch_octsort(H.dense, H.ndense, A.cell_start, const_cast<float4*>(A.xs), const_cast<int*>(H.slot), s) !=
+          CL_OK)
+        return CL_ERR_CUDA;
+    }
     int nhb = half_grid(mode);
     if (nhb <= 0) return CL_ERR_CUDA;
     const size_t hsm = half_mode_smem(mode);
@@ -2437,7 +2445,7 @@ bool half_path_applies(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArg
 int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& Hin, int* work, int mode,
                 const double* hinv, float* forces, double* grad, const double* gE, const double* pos,
                 double* partials, long long partials_cap, double* sums, double* energy, double* virial,
-                double* gradbox, cudaStream_t s) {
+                double* gradbox, cudaStream_t s, int* lists_half) {
   const int NV = hood_nv(mode);
   const bool half = half_path_applies(A, Ahalf, Hin, mode);
   const int nrest = (A.n + 255) / 256;  // CTAs of the companion sweep (and bound of the finish grid)
@@ -2445,11 +2453,21 @@ int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& Hin,
   HoodArgs H = Hin;
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
-  H.ndense = work + 4;
+  H.ndense = work + 7;
   H.half = half ? 1 : 0;
-  if (cudaMemsetAsync(work, 0, 8 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
-  k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
-                                                     H.ndense, H, half ? Ahalf->noff : 0, A.nx, A.ny, A.nz);
+  // the half-shell work lists depend on the cell list only: built once per
+  // list (lists_half says whether the buffers hold them) and reused
+  const bool reuse = half && lists_half && *lists_half;
+  if (cudaMemsetAsync(work, 0, (reuse ? 6 : 8) * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
+  if (!reuse) {
+    k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag,
+                                                       H.dense, H.ndense, H, half ? Ahalf->noff : 0, A.nx, A.ny, A.nz);
+    // the windowed cells' particles in octant order (half_windowed's batches)
+    if (half && launch_octsort(H.dense, H.ndense, A.cell_start, const_cast<float4*>(A.xs), const_cast<int*>(H.slot),
+                               s) != CL_OK)
+      return CL_ERR_CUDA;
+  }
+  if (lists_half) *lists_half = half ? 1 : 0;
   if (half) {
     // every non-empty cell: fast-path or windowed half-shell sweep, then the
     // per-particle finish; partials [sweep][finish]

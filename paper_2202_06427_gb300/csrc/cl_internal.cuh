@@ -44,8 +44,9 @@ constexpr int kMaxOff = 768;      // stencil entries (9^3 = 729 plus margin)
 constexpr int kMaxAxis = 1023;    // cells per axis (10-bit packing)
 constexpr int kMaxBins = 4096;    // histogram bins (shared-memory histogram)
 // Cells of kOctMin to kOctCap particles are ordered by the octant of their
-// particles' local coordinates (sign of x, y, z) when the list is built, so
-// that the 3D sweep can split their particles into compact groups.
+// particles' local coordinates (sign of x, y, z) by the 3D half-shell sweep
+// when it builds its work lists, so that it can split their particles into
+// compact groups.
 constexpr int kOctMin = 129;
 constexpr int kOctCap = 2048;
 
@@ -118,10 +119,13 @@ struct BuildBufs {
   int* meta;  // [0] error latch, [1] non-empty cells, [2] max occupancy
   float4* xs;
   unsigned* cellc;
-  int* big;  // ncells ints: the cells to order by octant (listed by the scan; meta[3] of them), or null
 };
 int scan_tiles_for(long long ncells);
 int launch_build(const Geo& g, const BuildBufs& b, cudaStream_t s);
+// Orders the particles of the listed cells (ncells_listed of them, read on the
+// device) with kOctMin..kOctCap particles by octant; slots follow.
+int launch_octsort(const int* cells, const int* ncells_listed, const int* cell_start, float4* xs, int* slot,
+                   cudaStream_t s);
 int launch_scan64(const int* counts, long long n, long long* tile_sum, long long* start, int* meta, cudaStream_t s);
 
 // Sweeps and reductions (cl_sweep.cu).
@@ -160,13 +164,13 @@ struct HoodArgs {
   float hd;           // largest distance of a cell point from the cell centre
   float eps;          // rounding margin of the staging radius
   int ncells;
-  int* work;          // [0] work counter, [1] list length, [4] dense cells, [5] their work counter;
-                      // zeroed by the launcher
+  int* work;          // [0] work counter, [2..3] candidates, [5] the dense cells' work counter (zeroed
+                      // by the launcher); [6] list length, [7] dense cells (written by k_hood_list)
   int* list;          // cells the neighbourhood sweep takes (ncells capacity)
   unsigned long long* cand;  // candidate pairs evaluated (work[2..3] of the same buffer), zeroed by the launcher
   unsigned char* flag;       // per cell: 1 per-particle companion sweep, 2 dense-cell sweep
   int* dense;                // cells of the dense-cell sweep (ncells capacity)
-  int* ndense;               // their number (work[4])
+  int* ndense;               // their number (work[7])
   float hrow[9];             // lattice rows H (FP32): lattice image T maps to the shift T.H
   float4* hforce;            // half-shell path: per sorted particle, accumulated force (n entries)
   const float4* xl;          // per original particle: local coordinate, w = packed cell (binning output)
@@ -186,13 +190,18 @@ size_t hood_smem_bytes();
 // mode 0: energy, forces, virial; 1: backward; 2: energy (half shell, A = half
 // stencil); 3: energy and the backward outputs.
 // partials_cap: doubles available in partials (sweep_partials_needed).
+// lists_half (host, may be null): 1 when the list buffers (list, dense, flag,
+// work[6..7]) hold the half-shell work lists of the current cell list; they
+// are then reused, and the flag is set after a half-shell launch and cleared
+// by any other.
 // Ahalf (modes 0, 1, 3; may be null): the half stencil, for the half-shell
 // path, taken when both stencils fit the kernels' table (H.hforce must then
 // hold n entries); the full-shell kernels take the launch otherwise.
 bool half_path_applies(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int mode);
 int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, int* work, int mode, const double* hinv, float* forces,
                 double* grad, const double* gE, const double* pos, double* partials, long long partials_cap,
-                double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s);
+                double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s,
+                int* lists_half = nullptr);
 
 // Count (kind 0), sum 1/r (1) or distance histogram (2) over the half
 // stencil (A = half stencil, 3D): the staged neighbourhood sweep for the
@@ -200,7 +209,7 @@ int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, i
 // (count: 1 value, sum_inv_r: 1 value, hist: nbins values) are overwritten.
 int launch_hood_scalar(const SweepArgs& A, const HoodArgs& H, int* work, int kind, unsigned long long* count,
                        double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
-                       float rmax, unsigned long long* hist, cudaStream_t s);
+                       float rmax, unsigned long long* hist, cudaStream_t s, int* lists_half = nullptr);
 
 // Two sets (cl_cross.cu): what 0 counts per query (count may be null) and their
 // total, 1 fills the pairs of each query's segment (start), 2 the per-query k

@@ -125,7 +125,6 @@ extern "C" int cl_energy_noalloc(const double* pos_dev, long long n, const cl_bo
   b.cell_start = reinterpret_cast<int*>(base + kOffStart);
   b.tile_sum = reinterpret_cast<int*>(base + kOffTiles);
   b.meta = reinterpret_cast<int*>(base + kOffMeta);
-  b.big = nullptr;  // the per-particle energy sweep does not use the octant order
   if (cudaMemsetAsync(b.meta, 0, 4 * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if ((e = clk::launch_build(g, b, s))) return e;
   A.xs = b.xs;

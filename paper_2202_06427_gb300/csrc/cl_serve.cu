@@ -340,7 +340,6 @@ bool cl_server::admit_one(Req* q) {
   B.xs = reinterpret_cast<float4*>(take(n * 16));
   B.slot = reinterpret_cast<int*>(take(n * 4));
   B.cellc = reinterpret_cast<unsigned*>(take(n * 4));
-  B.big = nullptr;  // the per-particle sweeps do not use the octant order
   B.counts = reinterpret_cast<int*>(take(C * 4));
   B.cell_start = reinterpret_cast<int*>(take((C + 1) * 4));
   B.tile_sum = reinterpret_cast<int*>(take((size_t)clk::scan_tiles_for((long long)C) * 4 + 4));

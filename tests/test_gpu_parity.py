@@ -419,3 +419,39 @@ def test_hist_bins_and_rmax(cuda_ok, lcell, nbins, rmax_frac):
     check_hist(hist, ref)
     if rmax > rc:
         assert hist[int(np.ceil(nbins * rc / rmax)):].sum() == 0
+
+
+def test_interleaved_calls_reuse_work_lists(cuda_ok):
+    """The half-shell sweep keeps its per-cell work lists between calls on one
+    list; calls that use the same buffers (the pair list, the histogram, the
+    energy alone) and a rebuild must not leave stale lists behind."""
+    P = _P()
+    x, h = _mixed_occupancy(519)
+    rc = 4.0
+    ref = oracle.pair_map(x, h, rc, band=BAND, nbins=19)
+    pos = torch.from_numpy(x).cuda()
+    cl = P.cl_build(pos, h, rc, 1)
+
+    def grad_ok():
+        e, dedx, dedh, _ = P.cl_energy_grad(cl)
+        check_energy(e.item(), ref["energy"])
+        check_forces(dedx.cpu().numpy(), -ref["forces"])
+        check_matrix(dedh.cpu().numpy(), ref["dedh"], TOL_GB)
+
+    grad_ok()
+    grad_ok()  # reused lists
+    check_count(int(P.cl_map(cl, "count")["count"].item()), ref)
+    grad_ok()
+    lst = P.cl_map(cl, "pairlist")
+    assert ref["count"] - ref["band_in"] <= lst["npairs"] <= ref["count"] + ref["band_out"]
+    grad_ok()
+    check_hist(P.cl_map(cl, "hist", nbins=19)["hist"].cpu().numpy(), ref)
+    check_energy(P.cl_map(cl, "energy")["energy"].item(), ref["energy"])
+    grad_ok()
+    # a rebuild with the particles permuted: new cell contents, same physics
+    perm = np.random.default_rng(3).permutation(x.shape[0])
+    P.cl_update(cl, torch.from_numpy(np.ascontiguousarray(x[perm])).cuda())
+    e, dedx, _, _ = P.cl_energy_grad(cl)
+    check_energy(e.item(), ref["energy"])
+    check_forces(dedx.cpu().numpy(), -ref["forces"][perm])
+    check_suminvr(P.cl_map(cl, "sum_inv_r")["sum_inv_r"].item(), ref, rc)
