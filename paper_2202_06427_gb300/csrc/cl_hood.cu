@@ -1556,7 +1556,9 @@ __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q,
 // every entry an own-cell particle (index j + obase within the batch).
 // Scalar modes (MODE 4 count, 5 sum 1/r) evaluate the same candidates with
 // the reduction of scalar_pair and no forces: the count in cnt, sum 1/r in e.
-template <bool MASK, bool OWNALL = false, int MODE = 3>
+// KB: the chunk's blocks of 64 positions that hold sequence positions (a last
+// chunk of at most 64 skips the second block's arithmetic).
+template <bool MASK, bool OWNALL = false, int MODE = 3, int KB = kEnt / 2>
 __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int base, int nh, float rc2, float irc,
                                            float irc2, float2 (&jx)[kEnt / 2], float2 (&jy)[kEnt / 2],
                                            float2 (&jz)[kEnt / 2], float2& e, unsigned& cnt, const ScalarRed& R) {
@@ -1566,18 +1568,19 @@ __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int b
   int own[kEnt];
 #pragma unroll
   for (int k = 0; k < kEnt / 2; ++k) {
+    jx[k] = jy[k] = jz[k] = f2(0.f);
+    if (k >= KB) continue;
     const float4 a = seq_entry<OWNALL>(S, sq, base + lane + 64 * k, own[2 * k], true);
     const float4 b = seq_entry<OWNALL>(S, sq, base + lane + 64 * k + 32, own[2 * k + 1], false);
     qx[k] = make_float2(a.x, b.x);
     qy[k] = make_float2(a.y, b.y);
     qz[k] = make_float2(a.z, b.z);
-    jx[k] = jy[k] = jz[k] = f2(0.f);
   }
   if (SCALAR) {
     for (int h = 0; h < nh; ++h) {
       const float4 hp = S.home[h];  // broadcast; negated coordinates
 #pragma unroll
-      for (int k = 0; k < kEnt / 2; ++k) {
+      for (int k = 0; k < KB; ++k) {
         const bool m0 = !MASK || own[2 * k] > h, m1 = !MASK || own[2 * k + 1] > h;
         scalar_pair<MODE, MASK>(qx[k], qy[k], qz[k], f2(hp.x), f2(hp.y), f2(hp.z), m0, m1, R, cnt, e);
       }
@@ -1591,7 +1594,7 @@ __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int b
       const float4 hp = S.home[h0 + u];  // broadcast; negated coordinates, padded past nh by far entries
       float2 gx = f2(0.f), gy = f2(0.f), gz = f2(0.f);
 #pragma unroll
-      for (int k = 0; k < kEnt / 2; ++k) {
+      for (int k = 0; k < KB; ++k) {
         const float2 dx = __fadd2_rn(qx[k], f2(hp.x)), dy = __fadd2_rn(qy[k], f2(hp.y)),
                      dz = __fadd2_rn(qz[k], f2(hp.z));
         float2 d2 = __fmul2_rn(dz, dz);
@@ -1795,7 +1798,10 @@ __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, c
     if (c >= nch) break;
     float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
     const int base = c * kChunk;
-    half_chunk<OWNALL, OWNALL, MODE>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+    if (sq.nf + sq.nb - base > 64)
+      half_chunk<OWNALL, OWNALL, MODE, 2>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+    else
+      half_chunk<OWNALL, OWNALL, MODE, 1>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
     if (!SCALAR) {
 #pragma unroll
       for (int k = 0; k < kEnt / 2; ++k) {
@@ -2055,8 +2061,14 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
       if (c >= nch) break;
       float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
       const int base = c * kChunk;
-      if (c < cmask) half_chunk<false, false, MODE>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
-      else half_chunk<true, false, MODE>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      const bool full = nseq - base > 64;  // else the chunk's second half is padding
+      if (c < cmask) {
+        if (full) half_chunk<false, false, MODE, 2>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+        else half_chunk<false, false, MODE, 1>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      } else {
+        if (full) half_chunk<true, false, MODE, 2>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+        else half_chunk<true, false, MODE, 1>(S, sq, base, nh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      }
       if (!SCALAR) {
 #pragma unroll
         for (int k = 0; k < kEnt / 2; ++k) {
