@@ -1374,7 +1374,8 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood(const __grid_constant__ Sw
 
 struct HalfSmem {
   float4 ent[kHCap + 32];  // (x, y, z in the home frame, sorted position as int bits); 32 trash entries
-  int img[kHCap];          // lattice image of the T != 0 entries, (tx, ty, tz) as signed bytes
+  unsigned short img[kHCap];  // lattice image of the T != 0 entries, (tx, ty, tz) as 5-bit signed fields
+  unsigned short ilist[kHCap];  // windowed cells: the staged entries within a batch's ball
   float4 home[kHome + 4];  // home particles (-x, -y, -z, sorted position), padded by far entries
   float4 own[kHome];       // the same with (x, y, z): the own cell's entries
   float hg[kHome][3];      // per home particle: sum of fsn r over its entries
@@ -1385,7 +1386,7 @@ struct HalfSmem {
   int oct[9];              // windowed cells: octant ranges of the cell's particles
   float bmin[kWarps][6];   // batch_ball: per-warp minima
   float wmax[kWarps];
-  int nf, nb, item, next;
+  int nf, nb, item, next, nl;
   unsigned long long ncand;
   double out[kWarps][16];
 };
@@ -1420,7 +1421,7 @@ __device__ __forceinline__ RowSeg half_segment(const SweepArgs& A, const HalfSme
       g.ebase = e0 - ox0 + tx * A.nx - cx;
       g.back = (tx | ty | tz) != 0 ? 1 : 0;
       g.valid = true;
-      image = (tx & 255) | ((ty & 255) << 8) | ((tz & 255) << 16);
+      image = (tx & 31) | ((ty & 31) << 5) | ((tz & 31) << 10);  // |t| <= 4: stencil reach <= 4
       break;
     }
     ox += len;
@@ -1495,7 +1496,7 @@ __device__ __forceinline__ void half_stage(const SweepArgs& A, HalfSmem& S, int 
             const bool keep = (mk[u] >> lane) & 1u;
             const int e = half_slot(keep, back, base + __popc(mk[u] & lt), lane);
             S.ent[e] = v[u];
-            if (back && e < kHCap) S.img[e] = im;
+            if (back && e < kHCap) S.img[e] = (unsigned short)im;
             base += __popc(mk[u]);
           }
         }
@@ -1530,12 +1531,22 @@ constexpr int kChunk = 32 * kEnt;   // entries per chunk
 struct SeqInfo {
   int nf, nb, nh;
   int obase;  // own pass of a windowed cell: position j is own particle j + obase of the batch
+  int wf;     // list pass of a windowed cell: the window's T = 0 entries (the others are T != 0)
 };
-template <bool OWNALL>
+// Kinds of sequence: the staged entries then the home particles (fast path),
+// a windowed cell's own particles (own pass), the entries of S.ilist (list
+// pass: a window's entries within a batch's ball; nf = list length).
+constexpr int kSeqPlain = 0, kSeqOwn = 1, kSeqList = 2;
+
+template <int SEQ>
 __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q, int j, int& own, bool far_up) {
   own = 0x7fffffff;
+  if (SEQ == kSeqList) {
+    if (j < q.nf) return S.ent[S.ilist[j]];
+    return far_up ? make_float4(kFar, kFar, kFar, 0.f) : make_float4(-kFar, -kFar, -kFar, 0.f);
+  }
   if (j < q.nf) {
-    if (OWNALL) own = j + q.obase;
+    if (SEQ == kSeqOwn) own = j + q.obase;
     return S.ent[j];
   }
   if (j < q.nf + q.nb) return S.ent[kHCap - q.nb + (j - q.nf)];
@@ -1552,13 +1563,14 @@ __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q,
 // when the entry comes after the home particle. The lane's entries' forces
 // (sum of fsn r, r = entry - home) accumulate in jx, jy, jz (pair k: positions
 // u = 2k, 2k + 1); each home particle's sum of fsn r over the chunk is
-// warp-summed per step into S.hg. OWNALL: the own pass of a windowed cell,
-// every entry an own-cell particle (index j + obase within the batch).
+// warp-summed per step into S.hg. SEQ: the kind of sequence (seq_entry); in
+// the own pass of a windowed cell every entry is an own-cell particle (index
+// j + obase within the batch).
 // Scalar modes (MODE 4 count, 5 sum 1/r) evaluate the same candidates with
 // the reduction of scalar_pair and no forces: the count in cnt, sum 1/r in e.
 // KB: the chunk's blocks of 64 positions that hold sequence positions (a last
 // chunk of at most 64 skips the second block's arithmetic).
-template <bool MASK, bool OWNALL = false, int MODE = 3, int KB = kEnt / 2>
+template <bool MASK, int SEQ = kSeqPlain, int MODE = 3, int KB = kEnt / 2>
 __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int base, int nh, float rc2, float irc,
                                            float irc2, float2 (&jx)[kEnt / 2], float2 (&jy)[kEnt / 2],
                                            float2 (&jz)[kEnt / 2], float2& e, unsigned& cnt, const ScalarRed& R) {
@@ -1570,8 +1582,8 @@ __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int b
   for (int k = 0; k < kEnt / 2; ++k) {
     jx[k] = jy[k] = jz[k] = f2(0.f);
     if (k >= KB) continue;
-    const float4 a = seq_entry<OWNALL>(S, sq, base + lane + 64 * k, own[2 * k], true);
-    const float4 b = seq_entry<OWNALL>(S, sq, base + lane + 64 * k + 32, own[2 * k + 1], false);
+    const float4 a = seq_entry<SEQ>(S, sq, base + lane + 64 * k, own[2 * k], true);
+    const float4 b = seq_entry<SEQ>(S, sq, base + lane + 64 * k + 32, own[2 * k + 1], false);
     qx[k] = make_float2(a.x, b.x);
     qy[k] = make_float2(a.y, b.y);
     qz[k] = make_float2(a.z, b.z);
@@ -1633,17 +1645,24 @@ __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int b
 // Adds the accumulated force of sequence position j to its particle (vector
 // atomic) and, for an entry across the boundary, the symmetric part of
 // (T.H) (x) f to the lane's virial sums.
+template <int SEQ = kSeqPlain>
 __device__ __forceinline__ void half_flush(const HoodArgs& H, const HalfSmem& S, const SeqInfo& q, int j, float fx,
                                            float fy, float fz, float* wv) {
   if (j >= q.nf + q.nb + q.nh || (fx == 0.f && fy == 0.f && fz == 0.f)) return;
-  const bool back = j >= q.nf && j < q.nf + q.nb;
-  const int idx = j < q.nf ? j : (back ? kHCap - q.nb + (j - q.nf) : -1);
+  bool back;
+  int idx;
+  if (SEQ == kSeqList) {
+    idx = S.ilist[j];
+    back = idx >= q.wf;
+  } else {
+    back = j >= q.nf && j < q.nf + q.nb;
+    idx = j < q.nf ? j : (back ? kHCap - q.nb + (j - q.nf) : -1);
+  }
   const int p = __float_as_int(idx >= 0 ? S.ent[idx].w : S.own[j - q.nf - q.nb].w);
   atomicAdd(&H.hforce[p], make_float4(fx, fy, fz, 0.f));
   if (back) {
     const int im = S.img[idx];
-    const float tx = (float)(signed char)(im & 255), ty = (float)(signed char)((im >> 8) & 255),
-                tz = (float)(signed char)((im >> 16) & 255);
+    const float tx = (float)((im << 27) >> 27), ty = (float)((im << 22) >> 27), tz = (float)((im << 17) >> 27);
     float t[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) t[a] = tx * H.hrow[a] + ty * H.hrow[3 + a] + tz * H.hrow[6 + a];
@@ -1764,7 +1783,7 @@ __device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w
       const bool keep = ((back ? mb[u] : mf[u]) >> lane) & 1u;
       const int e = half_slot(keep, back, back ? bb + __popc(mb[u] & lt) : bf + __popc(mf[u] & lt), lane);
       S.ent[e] = v[u];
-      if (back && e < kHCap) S.img[e] = meta[u] >> 1;
+      if (back && e < kHCap) S.img[e] = (unsigned short)(meta[u] >> 1);
       bf += __popc(mf[u]);
       bb += __popc(mb[u]);
     }
@@ -1774,8 +1793,9 @@ __device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w
 // One batch of at most kHome home particles (sorted positions hp ..) against
 // the staged sequence sq: the chunks of the sequence from a counter, the
 // entries' forces flushed per chunk, the home particles' forces at the end.
-// OWNALL: the own pass (every entry an own-cell particle, masked by index).
-template <bool OWNALL, int MODE>
+// SEQ: the kind of sequence (own pass: every entry an own-cell particle,
+// masked by index).
+template <int SEQ, int MODE>
 __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, const SeqInfo& sq, int hp, int nbh,
                            float2& e, float* wv, unsigned& cnt, const ScalarRed& R) {
   constexpr bool SCALAR = MODE >= 4;
@@ -1798,16 +1818,17 @@ __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, c
     if (c >= nch) break;
     float2 jx[kEnt / 2], jy[kEnt / 2], jz[kEnt / 2];
     const int base = c * kChunk;
+    constexpr bool MASK = SEQ == kSeqOwn;
     if (sq.nf + sq.nb - base > 64)
-      half_chunk<OWNALL, OWNALL, MODE, 2>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      half_chunk<MASK, SEQ, MODE, 2>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
     else
-      half_chunk<OWNALL, OWNALL, MODE, 1>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
+      half_chunk<MASK, SEQ, MODE, 1>(S, sq, base, nbh, A.rc2, A.irc, A.irc2, jx, jy, jz, e, cnt, R);
     if (!SCALAR) {
 #pragma unroll
       for (int k = 0; k < kEnt / 2; ++k) {
         const int j0 = base + lane + 64 * k;
-        half_flush(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
-        half_flush(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
+        half_flush<SEQ>(H, S, sq, j0, jx[k].x, jy[k].x, jz[k].x, wv);
+        half_flush<SEQ>(H, S, sq, j0 + 32, jx[k].y, jy[k].y, jz[k].y, wv);
       }
     }
   }
@@ -1901,29 +1922,67 @@ __device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, 
       for (int g = 1; g < 9; ++g) S.oct[g] = nh;  // one group
   }
   __syncthreads();
+  // the window's staging ball: the cell's particles' largest distance from
+  // the cell centre
+  {
+    float d = 0.f;
+    for (int t = tid; t < nh; t += kThreads) {
+      const float4 q = A.xs[hs + t];
+      d = fmaxf(d, fminf(sqrtf(fmaf(q.x, q.x, fmaf(q.y, q.y, q.z * q.z))), H.hd));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) d = fmaxf(d, __shfl_xor_sync(0xffffffffu, d, o));
+    if ((tid & 31) == 0) S.wmax[tid >> 5] = d;
+  }
+  __syncthreads();
+  float dcell = S.wmax[0];
+#pragma unroll
+  for (int w = 1; w < kWarps; ++w) dcell = fmaxf(dcell, S.wmax[w]);
+  const float tcell = H.rc + dcell + H.eps;
   const int C = S.ctot;
   unsigned long long cand = 0;
-  for (int g = 0; g < 8; ++g) {
-    const int g0 = S.oct[g], g1 = S.oct[g + 1];
-    for (int b0 = g0; b0 < g1; b0 += kHome) {
-      const int nbh = min(kHome, g1 - b0);
-      float bx, by, bz, top2;
-      batch_ball(A, H, S, hs + b0, nbh, bx, by, bz, top2);
-      for (int w0 = 0; w0 < C; w0 += kHCap) {
-        if (tid == 0) {
-          S.nf = 0;
-          S.nb = 0;
+  for (int w0 = 0; w0 < C; w0 += kHCap) {
+    if (tid == 0) {
+      S.nf = 0;
+      S.nb = 0;
+    }
+    __syncthreads();
+    half_stage_window(A, S, w0, min(C, w0 + kHCap), 0.f, 0.f, 0.f, tcell * tcell);
+    __syncthreads();
+    const int wf = min(S.nf, kHCap), wb = min(S.nb, kHCap - wf);
+    for (int g = 0; g < 8; ++g) {
+      const int g0 = S.oct[g], g1 = S.oct[g + 1];
+      for (int b0 = g0; b0 < g1; b0 += kHome) {
+        const int nbh = min(kHome, g1 - b0);
+        float bx, by, bz, top2;
+        batch_ball(A, H, S, hs + b0, nbh, bx, by, bz, top2);  // ends with a barrier
+        // the window's entries within the batch's ball
+        if (tid == 0) S.nl = 0;
+        __syncthreads();
+        for (int i0 = (tid >> 5) * 32; i0 < wf + wb; i0 += kThreads) {
+          const int i = i0 + (tid & 31);
+          const int idx = i < wf ? i : kHCap - wb + (i - wf);
+          bool keep = false;
+          if (i < wf + wb) {
+            const float4 q = S.ent[idx];
+            const float ex = q.x - bx, ey = q.y - by, ez = q.z - bz;
+            keep = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < top2;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          int at = 0;
+          if ((tid & 31) == 0 && m) at = atomicAdd(&S.nl, __popc(m));
+          at = __shfl_sync(0xffffffffu, at, 0);
+          if (keep) S.ilist[at + __popc(m & ((1u << (tid & 31)) - 1u))] = (unsigned short)idx;
         }
         __syncthreads();
-        half_stage_window(A, S, w0, min(C, w0 + kHCap), bx, by, bz, top2);
-        __syncthreads();
         SeqInfo sq;
-        sq.nf = min(S.nf, kHCap);
-        sq.nb = min(S.nb, kHCap - sq.nf);
+        sq.nf = S.nl;  // read by every thread before batch_ball's next barriers
+        sq.nb = 0;
         sq.nh = 0;
         sq.obase = 0;
-        half_batch<false, MODE>(A, H, S, sq, hs + b0, nbh, e, wv, cnt, R);
-        cand += (unsigned long long)nbh * (unsigned long long)(sq.nf + sq.nb);
+        sq.wf = wf;
+        half_batch<kSeqList, MODE>(A, H, S, sq, hs + b0, nbh, e, wv, cnt, R);
+        cand += (unsigned long long)nbh * (unsigned long long)sq.nf;
       }
     }
   }
@@ -1940,7 +1999,8 @@ __device__ __forceinline__ unsigned long long half_windowed(const SweepArgs& A, 
       sq.nb = 0;
       sq.nh = 0;
       sq.obase = o0 - b0;
-      half_batch<true, MODE>(A, H, S, sq, hs + b0, nbh, e, wv, cnt, R);  // its first barrier also covers the entries
+      sq.wf = 0;
+      half_batch<kSeqOwn, MODE>(A, H, S, sq, hs + b0, nbh, e, wv, cnt, R);  // its first barrier also covers the entries
       cand += (unsigned long long)nbh * (unsigned long long)no -
               (o0 == b0 ? (unsigned long long)nbh * (unsigned long long)(nbh + 1) / 2 : 0ull);
     }
@@ -2048,6 +2108,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     sq.nb = nb;
     sq.nh = nh;
     sq.obase = 0;
+    sq.wf = 0;
     const int nseq = nf + nb + nh;
     const int nch = (nseq + kChunk - 1) / kChunk;
     const int cmask = (nf + nb) / kChunk;  // the first chunk holding own-cell positions
