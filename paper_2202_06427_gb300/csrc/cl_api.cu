@@ -419,6 +419,9 @@ int cl_map(const cl_list* cc, cl_reduction red, const cl_params* params, cl_resu
       return clk::launch_scalar(*c->half, dim, 0, c->partials, c->sums, r->sum_inv_r, s);
     case CL_RED_SF_ENERGY:
       if (!r->energy) return CL_ERR_INVALID_ARG;
+      if (dim == 3 && c->n > 0 && clk::hood_half_fits(*c->half))
+        return clk::launch_hood_scalar(*c->half, *c->hood, c->work, 3, nullptr, c->partials, hood_cap(c), c->sums,
+                                       r->energy, 0, 0.f, nullptr, s, &c->lists_half);
       if (dim == 3 && c->n > 0)
         return clk::launch_hood(*c->half, nullptr, *c->hood, c->work, 2, c->geo.hinv, nullptr, nullptr, nullptr, nullptr,
                                 c->partials, hood_cap(c), c->sums, r->energy, nullptr, nullptr, s, &c->lists_half);

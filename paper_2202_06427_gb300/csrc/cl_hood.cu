@@ -239,6 +239,7 @@ __device__ __forceinline__ void hood_own(const float4* __restrict__ xy, const fl
 // copies are summed at the end.
 struct ScalarRed {
   float rc2, scale2, xlim;
+  float irc;       // MODE 2 (shifted-force energy): 1 / rc
   unsigned* hist;  // shared memory: this lane's copy
 };
 
@@ -257,6 +258,18 @@ __device__ __forceinline__ void scalar_pair(float2 qx, float2 qy, float2 qz, flo
   float2 d2 = __fmul2_rn(dz, dz);
   d2 = __ffma2_rn(dy, dy, d2);
   d2 = __ffma2_rn(dx, dx, d2);
+  if (MODE == 2) {  // shifted-force energy, the cutoff applied by clamping as in hood_pair
+    float2 y = rsqrt2(d2);
+    if (MASK) {
+      y.x = (m0 && d2.x < R.rc2) ? y.x : 0.f;
+      y.y = (m1 && d2.y < R.rc2) ? y.y : 0.f;
+    }
+    float2 t = __ffma2_rn(__fmul2_rn(d2, y), f2(-R.irc), f2(1.0f));
+    t.x = fmaxf(t.x, 0.f);
+    t.y = fmaxf(t.y, 0.f);
+    acc = __ffma2_rn(__fmul2_rn(t, t), y, acc);
+    return;
+  }
   bool h0 = false, h1 = false;
   if (MODE != 6) {
     h0 = d2.x < R.rc2 && (!MASK || m0);
@@ -1566,15 +1579,16 @@ __device__ __forceinline__ float4 seq_entry(const HalfSmem& S, const SeqInfo& q,
 // warp-summed per step into S.hg. SEQ: the kind of sequence (seq_entry); in
 // the own pass of a windowed cell every entry is an own-cell particle (index
 // j + obase within the batch).
-// Scalar modes (MODE 4 count, 5 sum 1/r) evaluate the same candidates with
-// the reduction of scalar_pair and no forces: the count in cnt, sum 1/r in e.
+// Scalar modes (MODE 2 energy, 4 count, 5 sum 1/r, 6 histogram) evaluate the
+// same candidates with the reduction of scalar_pair and no forces: the count
+// in cnt, the energy or sum 1/r in e, the bins in R.hist.
 // KB: the chunk's blocks of 64 positions that hold sequence positions (a last
 // chunk of at most 64 skips the second block's arithmetic).
 template <bool MASK, int SEQ = kSeqPlain, int MODE = 3, int KB = kEnt / 2>
 __device__ __forceinline__ void half_chunk(HalfSmem& S, const SeqInfo& sq, int base, int nh, float rc2, float irc,
                                            float irc2, float2 (&jx)[kEnt / 2], float2 (&jy)[kEnt / 2],
                                            float2 (&jz)[kEnt / 2], float2& e, unsigned& cnt, const ScalarRed& R) {
-  constexpr bool SCALAR = MODE >= 4;
+  constexpr bool SCALAR = MODE == 2 || MODE >= 4;
   const int lane = threadIdx.x & 31;
   float2 qx[kEnt / 2], qy[kEnt / 2], qz[kEnt / 2];
   int own[kEnt];
@@ -1798,7 +1812,7 @@ __device__ void half_stage_window(const SweepArgs& A, HalfSmem& S, int w0, int w
 template <int SEQ, int MODE>
 __device__ void half_batch(const SweepArgs& A, const HoodArgs& H, HalfSmem& S, const SeqInfo& sq, int hp, int nbh,
                            float2& e, float* wv, unsigned& cnt, const ScalarRed& R) {
-  constexpr bool SCALAR = MODE >= 4;
+  constexpr bool SCALAR = MODE == 2 || MODE >= 4;
   const int tid = threadIdx.x, lane = tid & 31;
   for (int t = tid; t < kHome + 4; t += kThreads) {
     if (t < nbh) {
@@ -2015,7 +2029,7 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
                                                            const __grid_constant__ HoodArgs H,
                                                            double* __restrict__ partials) {
   constexpr bool ENERGY = MODE != 1 && MODE != 4 && MODE != 6;  // MODE 5 sums 1/r where the energy goes
-  constexpr bool SCALAR = MODE >= 4;
+  constexpr bool SCALAR = MODE == 2 || MODE >= 4;
   extern __shared__ __align__(16) unsigned char smraw[];
   HalfSmem& S = *reinterpret_cast<HalfSmem*>(smraw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -2047,13 +2061,17 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     S.rowk[nr] = (unsigned short)(ne > 1 ? ne : 1);
     S.nrows = nr;
   }
-  // scalar modes (count, sum 1/r): the cutoff, the lane's count
-  static_assert(MODE != 6, "the histogram runs on k_hood<6>");
+  // scalar modes (energy, count, sum 1/r, histogram): the cutoff, the
+  // histogram's copies after HalfSmem (as in k_hood), the lane's count
   ScalarRed R;
   R.rc2 = A.rc2;
-  R.scale2 = 0.f;
-  R.xlim = 0.f;
-  R.hist = nullptr;
+  R.irc = A.irc;
+  R.scale2 = H.hscale * H.hscale;
+  R.xlim = H.hxlim;
+  unsigned* const hist_all = reinterpret_cast<unsigned*>(smraw + sizeof(HalfSmem));
+  R.hist = hist_all + (lane & (H.hcopies - 1)) * H.hstride;
+  if (MODE == 6)
+    for (int b = tid; b < H.hcopies * H.hstride; b += kThreads) hist_all[b] = 0u;
   unsigned cnt = 0;
   float wv[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // lane's sum of (T.H) (x) f over its entries across the boundary
   float2 e = f2(0.f);
@@ -2168,9 +2186,15 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0 && c) atomicAdd(H.count, c);
   }
+  if (MODE == 6)
+    for (int b = tid; b < H.nbins; b += kThreads) {
+      unsigned c = 0;
+      for (int q = 0; q < H.hcopies; ++q) c += hist_all[q * H.hstride + b];
+      if (c) atomicAdd(&H.hist[b], (unsigned long long)c);
+    }
   if (tid < NV) {
     int src;
-    if (MODE == 2 || SCALAR) src = 15;
+    if (SCALAR) src = 15;
     else if (tid < kVirN3) src = tid;
     else if (MODE == 0) src = 15;
     else if (tid < kVirN3 + 9) src = -1;  // X: from k_half_finish
@@ -2315,9 +2339,11 @@ int hood_grid(int mode) {
 size_t hood_smem_bytes() { return sizeof(Smem); }
 
 // Persistent CTAs of the half-shell sweep, per mode (0, 1, 3).
-// Shared memory of k_hood_half<mode> (the histogram mode, whose copies would
-// follow HalfSmem, is not launched: k_hood<6> is faster).
-size_t half_mode_smem(int) { return sizeof(HalfSmem); }
+// Shared memory of k_hood_half<mode>: HalfSmem, and for the histogram its
+// largest set of copies.
+size_t half_mode_smem(int mode) {
+  return sizeof(HalfSmem) + (mode == 6 ? sizeof(unsigned) * (size_t)hist_stride(kMaxBins) : 0);
+}
 
 template <int M>
 cudaError_t half_setup(int bytes, int* per) {
@@ -2327,11 +2353,11 @@ cudaError_t half_setup(int bytes, int* per) {
   return e;
 }
 
-// Persistent CTAs of the half-shell sweep, per mode (0, 1, 3; scalar 4, 5);
-// also raises the kernels' shared-memory limit on the current device.
+// Persistent CTAs of the half-shell sweep, per mode (0, 1, 3; scalar 2, 4,
+// 5, 6); also raises the kernels' shared-memory limit on the current device.
 int half_grid(int mode) {
-  static DevCache cached[6];
-  if (mode < 0 || mode > 5 || mode == 2) return 0;
+  static DevCache cached[7];
+  if (mode < 0 || mode > 6) return 0;
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (const int c = cached[mode].get(dev)) return c;
@@ -2342,8 +2368,10 @@ int half_grid(int mode) {
     case 0: e = half_setup<0>(bytes, &per); break;
     case 1: e = half_setup<1>(bytes, &per); break;
     case 3: e = half_setup<3>(bytes, &per); break;
+    case 2: e = half_setup<2>(bytes, &per); break;
     case 4: e = half_setup<4>(bytes, &per); break;
-    default: e = half_setup<5>(bytes, &per); break;
+    case 5: e = half_setup<5>(bytes, &per); break;
+    default: e = half_setup<6>(bytes, &per); break;
   }
   if (e != cudaSuccess || per < 1) return 0;
   cached[mode].put(dev, sms * per);
@@ -2379,32 +2407,41 @@ int dense_grid(int mode) {
   return sms * per;
 }
 
-// Count and sum 1/r on the half-shell sweep (entry-major, every cell,
-// windowed where the buffers do not fit) rather than on the home-major
-// k_hood<4, 5> with the per-particle sweep for the cells it leaves. Measured
-// (CUDA events, one cl_map call): 16M clustered count 11.2 against 13.2 ms,
-// sum 1/r 12.3 against 16.7 ms; 1M lattice count 0.60 against 0.57 ms. The
-// histogram stays on k_hood<6> (1M lattice 0.93 against 1.05 ms, 16M
-// clustered 19.0 against 21.8 ms).
-inline bool scalar_half(int kind) { return kind != 2; }
+// Occupancy grid of a kernel with `smem` bytes of dynamic shared memory.
+template <class K>
+int grid_for(K kernel, size_t smem) {
+  int per = 0, sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kThreads, smem) != cudaSuccess || per < 1)
+    return 0;
+  return sms * per;
+}
 
+bool hood_half_fits(const SweepArgs& A) { return A.noff <= kTab; }
+
+// Scalar reductions over the half stencil. When the stencil fits the table,
+// the work lists of the half-shell sweep split the cells: the fast-path cells
+// (at most kHome particles, at most kHCap in the half neighbourhood) go to the
+// home-major k_hood<mode>, the others to the windowed k_hood_half<mode, true>
+// (octant batches, index lists); otherwise k_hood<mode> takes the cells it can
+// and the per-particle sweep the rest. Measured with the half-shell kernel
+// alone for every cell: 1M lattice count 0.60 against 0.57 ms, histogram 1.05
+// against 0.93 ms (the home-major kernel is faster on small cells).
 int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int kind, unsigned long long* count,
-                       double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
+                       double* partials, long long partials_cap, double* sums, double* scalar_out, int nbins,
                        float rmax, unsigned long long* hist, cudaStream_t s, int* lists_half) {
-  const int mode = 4 + kind;
-  if (kind < 0 || kind > 2) return CL_ERR_INVALID_ARG;
+  if (kind < 0 || kind > 3) return CL_ERR_INVALID_ARG;
+  const int mode = kind == 3 ? 2 : 4 + kind;
+  const bool scalar = kind == 1 || kind == 3;  // FP64 partials and a final reduction
+  const int final_mode = kind == 3 ? 1 : 0;
   if (kind == 2 && (nbins < 1 || nbins > kMaxBins || !(rmax > 0.f))) return CL_ERR_INVALID_ARG;
-  const int nrest = flagged_blocks(A.n);
-  int nb = hood_grid(mode);
-  if (nb <= 0) return CL_ERR_CUDA;
-  if (nb > Hin.ncells) nb = Hin.ncells;
-  if (kind == 1 && nb + nrest > partials_cap) nb = (int)(partials_cap - nrest);
-  if (nb < 1) return CL_ERR_INVALID_ARG;
+  const bool half = hood_half_fits(A);
+  if (kind == 3 && !half) return CL_ERR_UNSUPPORTED;  // the caller takes launch_hood's mode 2
   HoodArgs H = Hin;
   H.work = work;
   H.cand = reinterpret_cast<unsigned long long*>(work + 2);
   H.ndense = work + 7;
-  H.half = 0;
+  H.half = half ? 1 : 0;
   H.count = count;
   H.hist = hist;
   H.nbins = kind == 2 ? nbins : 0;
@@ -2413,73 +2450,69 @@ int launch_hood_scalar(const SweepArgs& A, const HoodArgs& Hin, int* work, int k
   H.hxlim = kind == 2 ? (float)std::min((double)nbins, (double)Hin.rc * ((double)nbins / rmax)) : 0.f;
   H.hcopies = kind == 2 ? hist_copies(nbins) : 1;
   H.hstride = kind == 2 ? hist_stride(nbins) : 0;
-  const bool half = scalar_half(kind) && A.noff <= kTab;
   const bool reuse = half && lists_half && *lists_half;  // the half-shell work lists of this cell list are built
   if (cudaMemsetAsync(work, 0, (reuse ? 6 : 8) * sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
   if (kind == 0 && cudaMemsetAsync(count, 0, sizeof(unsigned long long), s) != cudaSuccess) return CL_ERR_CUDA;
   if (kind == 2 && cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * nbins, s) != cudaSuccess) return CL_ERR_CUDA;
   if (A.n <= 0) {
-    if (kind != 1) return CL_OK;
+    if (!scalar) return CL_OK;
     if (cudaMemsetAsync(partials, 0, sizeof(double), s) != cudaSuccess) return CL_ERR_CUDA;
-    return finish_reduction(0, 3, nullptr, 1, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
+    return finish_reduction(final_mode, 3, nullptr, 1, 1, partials, sums, scalar_out, nullptr, nullptr, nullptr, s);
   }
   if (lists_half) *lists_half = half ? 1 : 0;
-  if (half) {
-    // the half-shell sweep (fast-path and windowed cells) takes every cell
-    H.half = 1;
-    if (!reuse) {
-      k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag,
-                                                         H.dense, H.ndense, H, A.noff, A.nx, A.ny, A.nz);
-      if (launch_octsort(H.dense, H.ndense, A.cell_start, const_cast<float4*>(A.xs), const_cast<int*>(H.slot), s) !=
-          CL_OK)
-        return CL_ERR_CUDA;
-    }
-    int nhb = half_grid(mode);
-    if (nhb <= 0) return CL_ERR_CUDA;
-    const size_t hsm = half_mode_smem(mode);
-    if (nhb > Hin.ncells) nhb = Hin.ncells;
-    if (kind == 1 && 2 * nhb > partials_cap) nhb = (int)(partials_cap / 2);
-    if (nhb < 1) return CL_ERR_INVALID_ARG;
-    if (kind == 0) {
-      k_hood_half<4, false><<<nhb, kThreads, hsm, s>>>(A, H, partials);
-      k_hood_half<4, true><<<nhb, kThreads, hsm, s>>>(A, H, partials + nhb);
-    } else {
-      k_hood_half<5, false><<<nhb, kThreads, hsm, s>>>(A, H, partials);
-      k_hood_half<5, true><<<nhb, kThreads, hsm, s>>>(A, H, partials + nhb);
-    }
-    if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
-    if (kind != 1) return CL_OK;
-    return finish_reduction(0, 3, nullptr, 2 * nhb, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
+  // grids: the home-major kernel, and (half) the windowed kernel
+  const size_t hist_bytes = kind == 2 ? sizeof(unsigned) * (size_t)H.hcopies * H.hstride : 0;
+  const size_t smem = sizeof(Smem) + hist_bytes, hsmem = sizeof(HalfSmem) + hist_bytes;
+  if (hood_grid(mode) <= 0 || (half && half_grid(mode) <= 0)) return CL_ERR_CUDA;  // also raise the smem limits
+  int nb = 0, nhb = 0;
+  switch (mode) {
+    case 2: nb = grid_for(k_hood<2>, smem); nhb = grid_for(k_hood_half<2, true>, hsmem); break;
+    case 4: nb = grid_for(k_hood<4>, smem); nhb = grid_for(k_hood_half<4, true>, hsmem); break;
+    case 5: nb = grid_for(k_hood<5>, smem); nhb = grid_for(k_hood_half<5, true>, hsmem); break;
+    default: nb = grid_for(k_hood<6>, smem); nhb = grid_for(k_hood_half<6, true>, hsmem); break;
   }
-  k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
-                                                     H.ndense, H, 0, A.nx, A.ny, A.nz);
-  size_t smem = hood_mode_smem(mode);
-  if (kind == 2) {  // the grid for this launch's histogram size
-    smem = sizeof(Smem) + sizeof(unsigned) * (size_t)H.hcopies * H.hstride;
-    int per = 0, sms = 0, dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_hood<6>, kThreads, smem) != cudaSuccess || per < 1)
+  if (nb <= 0 || nhb <= 0) return CL_ERR_CUDA;
+  nb = std::min(nb, Hin.ncells);
+  nhb = half ? std::min(nhb, Hin.ncells) : 0;
+  const int nrest = half ? 0 : flagged_blocks(A.n);
+  if (scalar && nb + nhb + nrest > partials_cap) return CL_ERR_INVALID_ARG;
+  if (!reuse) {
+    k_hood_list<<<(H.ncells + 255) / 256, 256, 0, s>>>(A.cell_start, H.ncells, A.noff, work, H.list, H.flag, H.dense,
+                                                       H.ndense, H, half ? A.noff : 0, A.nx, A.ny, A.nz);
+    if (half && launch_octsort(H.dense, H.ndense, A.cell_start, const_cast<float4*>(A.xs), const_cast<int*>(H.slot),
+                               s) != CL_OK)
       return CL_ERR_CUDA;
-    nb = std::min(sms * per, Hin.ncells);
   }
-  // the staged sweep, then one thread per particle for the cells it left
-  // (flag != 0: few particles, more than kHome, or an overflowing ball)
-  if (kind == 0) {
-    k_hood<4><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
-    if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
-    return launch_count_flagged(A, H.flag, count, s);
+  double* p2 = partials + nb;
+  switch (mode) {
+    case 2:
+      k_hood<2><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+      k_hood_half<2, true><<<nhb, kThreads, hsmem, s>>>(A, H, p2);
+      break;
+    case 4:
+      k_hood<4><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+      if (half) k_hood_half<4, true><<<nhb, kThreads, hsmem, s>>>(A, H, p2);
+      break;
+    case 5:
+      k_hood<5><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+      if (half) k_hood_half<5, true><<<nhb, kThreads, hsmem, s>>>(A, H, p2);
+      break;
+    default:
+      k_hood<6><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
+      if (half) k_hood_half<6, true><<<nhb, kThreads, hsmem, s>>>(A, H, p2);
+      break;
   }
-  if (kind == 2) {
-    k_hood<6><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
-    if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
-    return launch_hist_flagged(A, H.flag, nbins, rmax, hist, s);
-  }
-  k_hood<5><<<nb, kThreads, smem, s>>>(A, H, nullptr, nullptr, nullptr, nullptr, partials);
   if (cudaGetLastError() != cudaSuccess) return CL_ERR_CUDA;
-  const int e = launch_suminvr_flagged(A, H.flag, partials + nb, s);
-  if (e != CL_OK) return e;
-  return finish_reduction(0, 3, nullptr, nb + nrest, 1, partials, sums, sum_inv_r, nullptr, nullptr, nullptr, s);
+  if (!half) {  // one thread per particle for the cells the staged sweep left (flag != 0)
+    int e = CL_OK;
+    if (kind == 0) e = launch_count_flagged(A, H.flag, count, s);
+    else if (kind == 2) e = launch_hist_flagged(A, H.flag, nbins, rmax, hist, s);
+    else e = launch_suminvr_flagged(A, H.flag, partials + nb, s);
+    if (e != CL_OK) return e;
+  }
+  if (!scalar) return CL_OK;
+  return finish_reduction(final_mode, 3, nullptr, nb + nhb + nrest, 1, partials, sums, scalar_out, nullptr, nullptr,
+                          nullptr, s);
 }
 
 int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int* opk_half, int noff_half,

@@ -203,12 +203,17 @@ int launch_hood(const SweepArgs& A, const SweepArgs* Ahalf, const HoodArgs& H, i
                 double* sums, double* energy, double* virial, double* gradbox, cudaStream_t s,
                 int* lists_half = nullptr);
 
-// Count (kind 0), sum 1/r (1) or distance histogram (2) over the half
-// stencil (A = half stencil, 3D): the staged neighbourhood sweep for the
-// cells that fit it, then the per-particle sweep for the others. The outputs
-// (count: 1 value, sum_inv_r: 1 value, hist: nbins values) are overwritten.
+// Count (kind 0), sum 1/r (1), distance histogram (2) or shifted-force
+// energy (3) over the half stencil (A = half stencil, 3D): the staged sweeps
+// (home-major for the fast-path cells, the windowed half-shell sweep for the
+// others), or, when the stencil does not fit the kernels' table, the staged
+// sweep for the cells that fit it and the per-particle sweep for the rest
+// (the energy then returns CL_ERR_UNSUPPORTED: launch_hood's mode 2 takes it).
+// The outputs (count: 1 value, scalar_out: 1 value, hist: nbins values) are
+// overwritten.
+bool hood_half_fits(const SweepArgs& A);
 int launch_hood_scalar(const SweepArgs& A, const HoodArgs& H, int* work, int kind, unsigned long long* count,
-                       double* partials, long long partials_cap, double* sums, double* sum_inv_r, int nbins,
+                       double* partials, long long partials_cap, double* sums, double* scalar_out, int nbins,
                        float rmax, unsigned long long* hist, cudaStream_t s, int* lists_half = nullptr);
 
 // Two sets (cl_cross.cu): what 0 counts per query (count may be null) and their
