@@ -523,7 +523,11 @@ def clustered_leg(dev, steps, warmup):
     avg = lambda a, b: sum(e[a].elapsed_time(e[b]) for e in ev) / steps
     ms, bms, kms = avg(0, 3), avg(0, 1), avg(1, 2)
     peaks, basis = load_peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    red = reduction_times(P, cl, dev, flush, reps=5)
+    del flush
     return {"workload": "w4_clustered_16m", "n": n, "cutoff": rc, "lcell": lcell, "pairs_per_step": pairs,
+            "reductions": red,
             "steps": steps, "ms_per_step": ms, "pairs_per_s": pairs / (ms / 1e3),
             "step": "binning + fused energy/forces/box-gradient sweep + chain rule",
             "l2": "inputs (384 MB positions) larger than L2",
