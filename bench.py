@@ -64,17 +64,18 @@ FLOP_PER_HIT_HALF = 22
 # original index (4 B); the per-cell counts and offsets add 8 B per cell.
 BIN_BYTES_PER_PARTICLE = 44
 BIN_BYTES_PER_CELL = 8
-# DRAM bytes per launch of the dominant kernel (k_hood_half<3> on the 1M
+# DRAM bytes per launch of the dominant kernel (k_hood_half<3, 0> on the 1M
 # lattice) from one ncu capture of its current version (dram__bytes_read.sum +
-# dram__bytes_write.sum = 36.39 + 0.03 MB), or None when the kernel has changed
+# dram__bytes_write.sum = 36.40 + 0.00 MB), or None when the kernel has changed
 # since the counters were taken.
-SWEEP_DRAM_BYTES = 36_416_000
+SWEEP_DRAM_BYTES = 36_400_384
 FP32_LANES_PER_SM = 128
 # kernels of one headline step: bin, 2 scan, scatter, packed cells (binning);
-# cell list, half-shell sweep of the fast-path cells, of the windowed cells
-# (exits at once when there are none), per-particle finish, 2 reduce
-# (cl_energy_grad); 2 scale (chain rule for positions and box)
-STEP_LAUNCHES = 13
+# cell list, octant order of the windowed cells, half-shell sweep of the
+# fast-path cells, of the windowed cells (both exit at once when there are
+# none), per-particle finish, 2 reduce (cl_energy_grad); 2 scale (chain rule
+# for positions and box)
+STEP_LAUNCHES = 14
 
 
 def parse():
