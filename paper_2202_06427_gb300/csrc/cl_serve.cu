@@ -48,49 +48,87 @@ struct ReqDesc {
 
 constexpr int kServeThreads = 256;
 
+// One tile of a request: one thread per cell-sorted particle over the
+// stencil, the packed (f32x2) sweep in 3D as in the library's per-particle
+// kernels, the scalar one in 2D.
 template <int DIM>
 __device__ void serve_tile(const ReqDesc& R, int blk, unsigned* shist) {
   const int p = blk * kServeThreads + threadIdx.x;
   float4 pi;
   if (R.task == CL_TASK_ENERGY) {
-    RedEnergy red;
-    red.irc = R.irc;
-    RedEnergy::Acc acc;
-    red.init(acc);
-    sweep_particle<DIM>(R, red, acc, p, pi);
-    double v[1] = {(double)acc.e};
+    double v[1];
+    if (DIM == 3) {
+      Red2Energy red;
+      red.irc = R.irc;
+      Red2Energy::Acc acc;
+      red.init(acc);
+      sweep_particle2(R, red, acc, p, pi);
+      v[0] = (double)acc.e.x + (double)acc.e.y;
+    } else {
+      RedEnergy red;
+      red.irc = R.irc;
+      RedEnergy::Acc acc;
+      red.init(acc);
+      sweep_particle<DIM>(R, red, acc, p, pi);
+      v[0] = (double)acc.e;
+    }
     block_sum_store<1>(v, R.partials + blk);
   } else if (R.task == CL_TASK_FORCES) {
-    RedForce<DIM, true> red;
-    red.irc = R.irc;
-    red.irc2 = R.irc2;
-    typename RedForce<DIM, true>::Acc acc;
-    red.init(acc);
-    const bool live = sweep_particle<DIM>(R, red, acc, p, pi);
-    if (live) {
-      const int i = __float_as_int(pi.w);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) R.forces[(size_t)i * DIM + a] = acc.f[a];
-    }
     constexpr int NW = DIM == 3 ? 6 : 3;
     double v[NW + 1];
     if (DIM == 3) {
-      for (int k = 0; k < 6; ++k) v[k] = acc.w[k];
+      Red2Force<true> red;
+      red.irc = R.irc;
+      red.irc2 = R.irc2;
+      Red2Force<true>::Acc acc;
+      red.init(acc);
+      const bool live = sweep_particle2(R, red, acc, p, pi);
+      float v6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      if (live) {
+        const int i = __float_as_int(pi.w);
+        R.forces[(size_t)i * 3 + 0] = -acc.tx;
+        R.forces[(size_t)i * 3 + 1] = -acc.ty;
+        R.forces[(size_t)i * 3 + 2] = -acc.tz;
+        red.virial(acc, pi.x, pi.y, pi.z, v6);
+      }
+      // the scalar sweep's accumulator is sum fs r (x) r = -(sum fsn r (x) r)
+      for (int k = 0; k < 6; ++k) v[k] = -(double)v6[k];
+      v[NW] = 0.5 * ((double)acc.e.x + (double)acc.e.y);
     } else {
+      RedForce<DIM, true> red;
+      red.irc = R.irc;
+      red.irc2 = R.irc2;
+      typename RedForce<DIM, true>::Acc acc;
+      red.init(acc);
+      const bool live = sweep_particle<DIM>(R, red, acc, p, pi);
+      if (live) {
+        const int i = __float_as_int(pi.w);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) R.forces[(size_t)i * DIM + a] = acc.f[a];
+      }
       v[0] = acc.w[0]; v[1] = acc.w[1]; v[2] = acc.w[3];
+      v[NW] = 0.5 * (double)acc.e;
     }
-    v[NW] = 0.5 * (double)acc.e;
     block_sum_store<NW + 1>(v, R.partials + (size_t)blk * (NW + 1));
   } else {
     for (int b = threadIdx.x; b < R.nbins; b += blockDim.x) shist[b] = 0u;
     __syncthreads();
-    RedHist red;
-    red.nbins = R.nbins;
-    red.rmax = R.rmax;
-    red.scale = R.hscale;
-    red.sh = shist;
-    RedHist::Acc acc;
-    sweep_particle<DIM>(R, red, acc, p, pi);
+    if (DIM == 3) {
+      Red2Hist red;
+      red.scale2 = R.hscale * R.hscale;
+      red.xlim = fminf((float)R.nbins, sqrtf(R.rc2) * R.hscale);
+      red.sh = shist;
+      Red2Hist::Acc acc;
+      sweep_particle2(R, red, acc, p, pi);
+    } else {
+      RedHist red;
+      red.nbins = R.nbins;
+      red.rmax = R.rmax;
+      red.scale = R.hscale;
+      red.sh = shist;
+      RedHist::Acc acc;
+      sweep_particle<DIM>(R, red, acc, p, pi);
+    }
     __syncthreads();
     for (int b = threadIdx.x; b < R.nbins; b += blockDim.x)
       if (shist[b]) atomicAdd(&R.hist[b], (unsigned long long)shist[b]);

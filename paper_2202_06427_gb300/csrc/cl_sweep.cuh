@@ -364,7 +364,8 @@ __device__ __forceinline__ void scan_pairs(const float4* __restrict__ xs, int j0
 }
 
 // Neighbour cell of stencil entry k for the cell (cx, cy, cz).
-__device__ __forceinline__ int stencil_cell(const SweepArgs& A, int k, int cx, int cy, int cz) {
+template <class ARGS>
+__device__ __forceinline__ int stencil_cell(const ARGS& A, int k, int cx, int cy, int cz) {
   const Off& o = A.off[k];
   int x2 = cx + o.dx;
   x2 -= (x2 >= A.nx) ? A.nx : 0;
@@ -376,8 +377,8 @@ __device__ __forceinline__ int stencil_cell(const SweepArgs& A, int k, int cx, i
 }
 
 // Packed counterpart of sweep_particle (3D only).
-template <class R>
-__device__ __forceinline__ bool sweep_particle2(const SweepArgs& A, const R& red, typename R::Acc& acc, int p,
+template <class R, class ARGS = SweepArgs>
+__device__ __forceinline__ bool sweep_particle2(const ARGS& A, const R& red, typename R::Acc& acc, int p,
                                                 float4& pi) {
   if (p >= A.n) return false;
   pi = A.xs[p];
