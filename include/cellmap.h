@@ -294,6 +294,13 @@ void cl_free(cl_list* cl);
 /* Static description of an error code. */
 const char* cl_error_string(int code);
 
+/* The guard the pair-list calls (CL_RED_PAIRLIST, cl_cross_pairlist) apply
+ * to the 64-bit total of their count pass before any pair is written: CL_OK
+ * when 0 <= npairs <= capacity, CL_ERR_CAPACITY when npairs > capacity (the
+ * call then returns with *npairs set and writes nothing), CL_ERR_INVALID_ARG
+ * for a negative total. Host-only, no device work. */
+int cl_pairlist_fits(long long npairs, long long capacity);
+
 /* One neighbour-cell offset o of the stencil: its periodic cell step
  * (o_k mod n_k, in [0, n_k)) and the Cartesian shift S_o = sum_k (o_k/n_k) H_k
  * between the centres of a cell and of its neighbour o, unwrapped. */

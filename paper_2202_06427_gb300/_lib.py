@@ -62,6 +62,7 @@ def lib():
         L.cl_backward.argtypes = [P, P, P, P, P, P]
         L.cl_energy_grad.argtypes = [P, P, P, P, P, P, P]
         L.cl_scale.argtypes = [P, P, P, ll, P]
+        L.cl_pairlist_fits.argtypes = [ll, ll]
         L.cl_map_mass.argtypes = [P, P, P, P]
         L.cl_map_lj.argtypes = [P, ctypes.c_double, ctypes.c_double, P, P, P]
         L.cl_map_velocity_hist.argtypes = [P, P, ctypes.c_double, i32, P, P, P]

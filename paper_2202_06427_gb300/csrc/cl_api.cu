@@ -289,7 +289,7 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
       cudaStreamSynchronize(s) != cudaSuccess)
     return CL_ERR_CUDA;
   *r->npairs = total;
-  if (total > r->capacity) return CL_ERR_CAPACITY;
+  if ((e = cl_pairlist_fits(total, r->capacity))) return e;
   if (total == 0) return CL_OK;
   if (!r->pair_i || !r->pair_j || !r->pair_d) return CL_ERR_INVALID_ARG;
   return clk::launch_pairs_fill(*c->full, dim, ball2, cap, c->hflag, c->hlist, c->pl_meta + 4, c->pl_count, c->pl_start,
@@ -299,6 +299,11 @@ int map_pairlist(cl_list* c, cl_result* r, cudaStream_t s) {
 }  // namespace
 
 extern "C" {
+
+int cl_pairlist_fits(long long npairs, long long capacity) {
+  if (npairs < 0) return CL_ERR_INVALID_ARG;  // a total read back from the 64-bit scan is never negative
+  return npairs > capacity ? CL_ERR_CAPACITY : CL_OK;
+}
 
 const char* cl_error_string(int code) {
   switch (code) {
@@ -570,7 +575,7 @@ int cl_cross_pairlist(const cl_list* cc, const double* posb_dev, long long nb, l
     return CL_ERR_CUDA;
   if ((e = read_err(w.err, s))) return e;
   *npairs = total;
-  if (total > capacity) return CL_ERR_CAPACITY;
+  if ((e = cl_pairlist_fits(total, capacity))) return e;
   if (total == 0) return CL_OK;
   if (!pa_dev || !pb_dev || !pd_dev) return CL_ERR_INVALID_ARG;
   if ((e = clk::launch_cross(1, *c->full, c->geo, posb_dev, nb, 0, nullptr, nullptr, w.start, pa_dev, pb_dev, pd_dev,

@@ -40,6 +40,23 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_pairlist_capacity_guard(lib):
+    """The guard applied to the 64-bit pair total before a pair list is
+    written: totals past 2^31 (the 16M clustered set has 5.2e9 pairs) are
+    compared in 64 bits, never wrapped."""
+    from paper_2202_06427_gb300 import _lib as L
+    L.lib()
+    fits = lib.cl_pairlist_fits
+    assert fits(0, 0) == L.CL_OK
+    assert fits(16, 16) == L.CL_OK
+    assert fits(17, 16) == L.CL_ERR_CAPACITY
+    assert fits(5_209_002_118, 16) == L.CL_ERR_CAPACITY
+    assert fits(5_209_002_118, 5_209_002_118) == L.CL_OK
+    assert fits((1 << 31) + 5, (1 << 31) + 4) == L.CL_ERR_CAPACITY
+    assert fits((1 << 32) + 1, 2) == L.CL_ERR_CAPACITY  # wraps to 1 in 32 bits
+    assert fits(-1, 10) == -1  # CL_ERR_INVALID_ARG
+
+
 def test_error_strings(lib):
     from paper_2202_06427_gb300 import cl_error_string
     assert cl_error_string(0) == "ok"
