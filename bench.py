@@ -73,9 +73,9 @@ FP32_LANES_PER_SM = 128
 # kernels of one headline step: bin, 2 scan, scatter, packed cells (binning);
 # cell list, octant order of the windowed cells, half-shell sweep of the
 # fast-path cells, of the windowed cells (both exit at once when there are
-# none), per-particle finish, 2 reduce (cl_energy_grad); 2 scale (chain rule
-# for positions and box)
-STEP_LAUNCHES = 14
+# none), per-particle finish, final reduction (cl_energy_grad); 2 scale
+# (chain rule for positions and box)
+STEP_LAUNCHES = 13
 
 
 def parse():

@@ -384,6 +384,8 @@ int cl_build(const double* pos_dev, long long n, const cl_box* box, void* stream
   if (!e) e = set_geometry(c, box);
   cudaStream_t s = (cudaStream_t)stream;
   if (!e && cudaMemsetAsync(c->meta, 0, sizeof(int) * 4, s) != cudaSuccess) e = CL_ERR_CUDA;
+  // sums[31]: the final reduction's completion counter, zero between launches
+  if (!e && cudaMemsetAsync(c->sums, 0, sizeof(double) * 32, s) != cudaSuccess) e = CL_ERR_CUDA;
   if (!e) e = run_build(c, s);
   if (e) {
     free_all(c);

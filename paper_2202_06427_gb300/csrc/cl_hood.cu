@@ -719,7 +719,9 @@ __device__ unsigned long long particle_sweep(const SweepArgs& A, const HoodArgs&
 // (wrapped): one contiguous range unless the run crosses the box edge in x.
 __device__ __forceinline__ int run_count(const int* __restrict__ cell_start, int nx, int ny, int nz, int cx, int cy,
                                          int cz, int ox0, int ox1, int oy, int oz) {
-  const int y2 = ((cy + oy) % ny + ny) % ny, z2 = ((cz + oz) % nz + nz) % nz;
+  int y2 = cy + oy, z2 = cz + oz;
+  if ((unsigned)y2 >= (unsigned)ny) y2 = (y2 % ny + ny) % ny;  // wrap only off the box: no division inside it
+  if ((unsigned)z2 >= (unsigned)nz) z2 = (z2 % nz + nz) % nz;
   const int row = nx * (y2 + ny * z2);
   const int xa = cx + ox0, xb = cx + ox1;
   if (xa >= 0 && xb < nx) return cell_start[row + xb + 1] - cell_start[row + xa];
@@ -758,18 +760,26 @@ __global__ void __launch_bounds__(256) k_hood_list(const int* __restrict__ cell_
     flag[h] = (nh > 0 && !take) ? (big ? 2 : 1) : 0;
     if (half && take) {
       const int cx = h % nx, cy = (h / nx) % ny, cz = h / (nx * ny);
-      int cnt = 0, r0 = 0, px = 0, py = 0, pz = 0;
-      for (int k = 1; k <= noff_half; ++k) {
-        int ox = 0, oy = 0, oz = 0;
-        if (k < noff_half) unpack_off(opk_half[k], ox, oy, oz);
-        if (k > 1 && (k == noff_half || oy != py || oz != pz || ox != px + 1)) {
-          cnt += run_count(cell_start, nx, ny, nz, cx, cy, cz, r0, px, py, pz);
-          r0 = ox;
+      int cnt = 0;
+      if (H.nrows_half > 0) {  // the rows from the host: independent loads
+#pragma unroll 4
+        for (int r = 0; r < H.nrows_half; ++r)
+          cnt += run_count(cell_start, nx, ny, nz, cx, cy, cz, H.rows_half[r][0], H.rows_half[r][1],
+                           H.rows_half[r][2], H.rows_half[r][3]);
+      } else {
+        int r0 = 0, px = 0, py = 0, pz = 0;
+        for (int k = 1; k <= noff_half; ++k) {
+          int ox = 0, oy = 0, oz = 0;
+          if (k < noff_half) unpack_off(opk_half[k], ox, oy, oz);
+          if (k > 1 && (k == noff_half || oy != py || oz != pz || ox != px + 1)) {
+            cnt += run_count(cell_start, nx, ny, nz, cx, cy, cz, r0, px, py, pz);
+            r0 = ox;
+          }
+          if (k == 1) r0 = ox;
+          px = ox;
+          py = oy;
+          pz = oz;
         }
-        if (k == 1) r0 = ox;
-        px = ox;
-        py = oy;
-        pz = oz;
       }
       if (cnt > kHCap) {
         take = false;
@@ -2520,6 +2530,27 @@ int fill_hood_args(const Geo& geo, const int* opk_full, int noff_full, const int
   std::memset(H, 0, sizeof(*H));
   for (int k = 0; k < noff_full && k < kMaxOff; ++k) H->opk[0][k] = opk_full[k];
   for (int k = 0; k < noff_half && k < kMaxOff; ++k) H->opk[1][k] = opk_half[k];
+  {  // rows of the half stencil, for the work lists' neighbourhood counts
+    int nr = 0;
+    bool fits = true;
+    for (int k = 1; k < noff_half && k < kMaxOff; ++k) {
+      const int v = opk_half[k];
+      const int ox = (signed char)(v & 0xff), oy = (signed char)((v >> 8) & 0xff), oz = (signed char)((v >> 16) & 0xff);
+      if (nr > 0 && H->rows_half[nr - 1][2] == oy && H->rows_half[nr - 1][3] == oz && H->rows_half[nr - 1][1] + 1 == ox) {
+        H->rows_half[nr - 1][1] = (signed char)ox;
+        continue;
+      }
+      if (nr == 128) {
+        fits = false;
+        break;
+      }
+      H->rows_half[nr][0] = H->rows_half[nr][1] = (signed char)ox;
+      H->rows_half[nr][2] = (signed char)oy;
+      H->rows_half[nr][3] = (signed char)oz;
+      ++nr;
+    }
+    H->nrows_half = fits ? nr : 0;
+  }
   double hd = 0.0;
   for (int s = 0; s < 8; ++s) {
     double v[3] = {0, 0, 0};

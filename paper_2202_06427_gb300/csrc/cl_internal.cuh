@@ -158,6 +158,10 @@ int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, i
 // Neighbourhood sweep of the 3D shifted-force energy (cl_hood.cu).
 struct HoodArgs {
   int opk[2][kMaxOff];  // unwrapped stencil offsets (see build_stencil): [0] full, [1] half stencil
+  // rows of the half stencil (entries 1..: runs of consecutive ox with one
+  // (oy, oz)) as (ox0, ox1, oy, oz); nrows_half of them, 0 when more than 128
+  signed char rows_half[128][4];
+  int nrows_half;
   double g[9];        // cell edge vectors G_k = H_k / n_k (rows), FP64
   float gf[9];        // the same, FP32
   float rc;

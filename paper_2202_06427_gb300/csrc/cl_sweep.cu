@@ -255,23 +255,6 @@ __global__ void __launch_bounds__(256) k_sweep2_force(const __grid_constant__ Sw
 
 // ----------------------------------------------------------- final reduce
 
-// Sums partials[nblocks][nv] in a fixed order into sums[nv]: CTA k sums
-// component k (strided per thread, then a fixed tree).
-__global__ void __launch_bounds__(256) k_final_sum(const double* __restrict__ partials, int nblocks, int nv,
-                                                   double* __restrict__ sums) {
-  __shared__ double sm[256];
-  const int k = blockIdx.x;
-  double s = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * nv + k];
-  sm[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) sums[k] = sm[0];
-}
-
 struct FinalArgs {
   int mode;          // 0 sum 1/r, 1 energy, 2 forward forces (energy + virial), 3 backward, 4 energy + backward
   int dim;
@@ -283,8 +266,7 @@ struct FinalArgs {
 };
 
 // Turns the summed partials into the caller's outputs (one thread).
-__global__ void k_final_assemble(const __grid_constant__ FinalArgs F, const double* __restrict__ sums) {
-  if (threadIdx.x != 0) return;
+__device__ void final_assemble(const FinalArgs& F, const double* sums) {
   const int d = F.dim;
   if (F.mode <= 1) {
     *F.out_scalar = sums[0];
@@ -322,10 +304,41 @@ __global__ void k_final_assemble(const __grid_constant__ FinalArgs F, const doub
   }
 }
 
+// Sums partials[nblocks][nv] in a fixed order into sums[nv]: CTA k sums
+// component k (strided per thread, then a fixed tree). The last CTA to finish
+// (a completion counter in the last word of sums, which holds 32 doubles,
+// zero between launches and reset by that CTA) turns the sums into the
+// caller's outputs, so the final step takes one launch.
+__global__ void __launch_bounds__(256) k_final_sum(const double* __restrict__ partials, int nblocks, int nv,
+                                                   double* __restrict__ sums, const __grid_constant__ FinalArgs F) {
+  __shared__ double sm[256];
+  __shared__ bool last;
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 256) s += partials[(size_t)b * nv + k];
+  sm[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[k] = sm[0];
+    __threadfence();
+    unsigned long long* done = reinterpret_cast<unsigned long long*>(sums + 31);
+    last = atomicAdd(done, 1ull) == (unsigned long long)(nv - 1);
+    if (last) {
+      *done = 0ull;
+      double tot[32];  // the other CTAs' sums, past L1
+      for (int q = 0; q < nv; ++q) tot[q] = __ldcg(sums + q);
+      final_assemble(F, tot);
+    }
+  }
+}
+
 int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, int nv, const double* partials,
                      double* sums, double* scalar, double* virial, double* gradbox, const double* gE,
                      cudaStream_t s) {
-  k_final_sum<<<nv, 256, 0, s>>>(partials, nblocks, nv, sums);
   FinalArgs F;
   memset(&F, 0, sizeof(F));
   F.mode = final_mode;
@@ -336,7 +349,8 @@ int finish_reduction(int final_mode, int dim, const double* hinv, int nblocks, i
   F.out_virial = virial;
   F.out_gradbox = gradbox;
   F.gE = gE;
-  k_final_assemble<<<1, 32, 0, s>>>(F, sums);
+  if (nv < 1 || nv > 31) return CL_ERR_INVALID_ARG;  // sums[31] is the completion counter
+  k_final_sum<<<nv, 256, 0, s>>>(partials, nblocks, nv, sums, F);
   return cudaGetLastError() == cudaSuccess ? CL_OK : CL_ERR_CUDA;
 }
 
