@@ -2220,6 +2220,37 @@ __global__ void __launch_bounds__(kThreads, 5) k_hood_half(const __grid_constant
 // accumulated buffer, which it clears for the next launch), the outputs
 // (MODE 0: forces; 1, 3: grad = -g F) and the per-CTA sums of -2 X (x) F
 // (symmetric part) and, for the gradient modes, x_raw (x) F.
+// FP32 <-> FP64 conversions from the IEEE bit layouts, on the integer pipes
+// (this GPU issues FP64 conversions at a small fraction of the FP32 rate):
+// f2d_bits is exact for finite values (FP32 subnormals, which the FTZ
+// arithmetic producing them never yields, go to zero); d2f_bits rounds to
+// nearest even, out of range to zero or infinity.
+__device__ __forceinline__ double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0) return (u >> 31) ? -0.0 : 0.0;
+  const unsigned long long d = ((unsigned long long)(u >> 31) << 63) |
+                               ((unsigned long long)(e == 255 ? 2047 : e + 896) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ float d2f_bits(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned s = (unsigned)(b >> 63) << 31;
+  int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(s);
+  unsigned m = (unsigned)((b >> 29) & 0x7fffffu);
+  const unsigned long long rem = b & ((1ull << 29) - 1), half = 1ull << 28;
+  if (rem > half || (rem == half && (m & 1u))) {
+    if (++m == 0x800000u) {
+      m = 0;
+      ++e;
+    }
+  }
+  if (e >= 255) return __uint_as_float(s | 0x7f800000u);
+  return __uint_as_float(s | ((unsigned)e << 23) | m);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(256) k_half_finish(const __grid_constant__ SweepArgs A,
                                                      const __grid_constant__ HoodArgs H, float* __restrict__ forces,
@@ -2278,10 +2309,10 @@ __global__ void __launch_bounds__(256) k_half_finish(const __grid_constant__ Swe
         for (int a = 0; a < 3; ++a) forces[(size_t)i * 3 + a] = F[a];
       } else {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = (double)(-g * F[a]);
+        for (int a = 0; a < 3; ++a) grad[(size_t)i * 3 + a] = f2d_bits(-g * F[a]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          const float xa = (float)pos[(size_t)i * 3 + a];
+          const float xa = d2f_bits(pos[(size_t)i * 3 + a]);
 #pragma unroll
           for (int b = 0; b < 3; ++b) o[6 + a * 3 + b] = fmaf(xa, F[b], o[6 + a * 3 + b]);
         }
