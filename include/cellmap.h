@@ -151,7 +151,9 @@ int cl_backward(const cl_list* cl, const double* grad_energy_dev, double* grad_p
  * ((n, dim) FP64, original order) and, when grad_box_dev is not NULL,
  * grad_box_dev = s dE/dH (dim*dim); virial_dev (optional) receives W. The
  * same outputs as cl_map(CL_RED_SF_ENERGY) plus cl_backward(scale_dev), at the
- * cost of one full-shell sweep. Errors as cl_backward. */
+ * cost of one sweep (in 3D the half-shell sweep with forces on both particles
+ * of each pair-image, then one pass over the particles). Errors as
+ * cl_backward. */
 int cl_energy_grad(const cl_list* cl, const double* scale_dev, double* energy_dev, double* grad_pos_dev,
                    double* grad_box_dev, double* virial_dev, void* stream);
 
