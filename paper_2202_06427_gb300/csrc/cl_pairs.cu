@@ -560,6 +560,23 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
 // by original index (radix sort of its indices), so a particle's pairs with
 // j > a come from a suffix of that order in ascending j and are written in
 // order, coalesced, as the ballot finds them.
+// Squared distances of a staged entry q to two home particles (nx, ny, nz:
+// their negated coordinates), both in packed FP32: per lane the same rounding
+// as fmaf(dx, dx, fmaf(dy, dy, dz * dz)) with dx = q.x - x. The count and the
+// fill pass both decide j within rc from this one expression.
+template <int DIM>
+__device__ __forceinline__ float2 pair_d2(const float4& q, float2 nx, float2 ny, float2 nz, float2& dx, float2& dy,
+                                          float2& dz) {
+  dx = __fadd2_rn(make_float2(q.x, q.x), nx);
+  dy = __fadd2_rn(make_float2(q.y, q.y), ny);
+  if (DIM == 3) {
+    dz = __fadd2_rn(make_float2(q.z, q.z), nz);
+    return __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+  }
+  dz = make_float2(0.f, 0.f);
+  return __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+}
+
 template <int DIM, bool FILL>
 __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ SweepArgs A,
                                                                                float ball2, int cap,
@@ -630,26 +647,20 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
           const float4 pa = A.xs[p];
           const float4 pb = two ? A.xs[p + 1] : pa;
           const int a0 = __float_as_int(pa.w), a1 = two ? __float_as_int(pb.w) : INT_MAX;
-          int L0 = 0, L1 = 0;
+          const float2 nx = make_float2(-pa.x, -pb.x), ny = make_float2(-pa.y, -pb.y),
+                       nz = make_float2(-pa.z, -pb.z);
+          int L0 = 0, L1 = 0;  // per lane, summed over the warp at the end
 #pragma unroll 2
-          for (int t0 = 0; t0 < S; t0 += 32) {
-            const int t = t0 + lane;
-            bool k0 = false, k1 = false;
-            if (t < S) {
-              const float4 q = st[t];
-              const int jo = __float_as_int(q.w);
-              const float dx0 = q.x - pa.x, dy0 = q.y - pa.y;
-              const float dz0 = DIM == 3 ? q.z - pa.z : 0.f;
-              const float d20 = DIM == 3 ? fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0)) : fmaf(dx0, dx0, dy0 * dy0);
-              const float dx1 = q.x - pb.x, dy1 = q.y - pb.y;
-              const float dz1 = DIM == 3 ? q.z - pb.z : 0.f;
-              const float d21 = DIM == 3 ? fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1)) : fmaf(dx1, dx1, dy1 * dy1);
-              k0 = jo > a0 && d20 < A.rc2;
-              k1 = jo > a1 && d21 < A.rc2;
-            }
-            L0 += __popc(__ballot_sync(0xffffffffu, k0));
-            L1 += __popc(__ballot_sync(0xffffffffu, k1));
+          for (int t = lane; t < S; t += 32) {
+            const float4 q = st[t];
+            const int jo = __float_as_int(q.w);
+            float2 dx, dy, dz;
+            const float2 d2 = pair_d2<DIM>(q, nx, ny, nz, dx, dy, dz);
+            L0 += (jo > a0 && d2.x < A.rc2) ? 1 : 0;
+            L1 += (jo > a1 && d2.y < A.rc2) ? 1 : 0;
           }
+          L0 = __reduce_add_sync(0xffffffffu, L0);
+          L1 = __reduce_add_sync(0xffffffffu, L1);
           if (lane == 0) {
             count[a0] = L0;
             if (two) count[a1] = L1;
@@ -688,6 +699,8 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
           }
           const int c0 = __ldg(count + a0), c1 = two ? __ldg(count + a1) : 0;
           const long long b0 = __ldg(start + a0), b1 = two ? __ldg(start + a1) : 0;
+          const float2 nx = make_float2(-pa.x, -pb.x), ny = make_float2(-pa.y, -pb.y),
+                       nz = make_float2(-pa.z, -pb.z);
           int L0 = 0, L1 = 0;
 #pragma unroll 2
           for (int t0 = min(f0, f1); t0 < S; t0 += 32) {
@@ -698,12 +711,10 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
             if (t < S) {
               const float4 q = st[(int)slots[t]];
               jo = __float_as_int(q.w);
-              const float dx0 = q.x - pa.x, dy0 = q.y - pa.y;
-              const float dz0 = DIM == 3 ? q.z - pa.z : 0.f;
-              d20 = DIM == 3 ? fmaf(dx0, dx0, fmaf(dy0, dy0, dz0 * dz0)) : fmaf(dx0, dx0, dy0 * dy0);
-              const float dx1 = q.x - pb.x, dy1 = q.y - pb.y;
-              const float dz1 = DIM == 3 ? q.z - pb.z : 0.f;
-              d21 = DIM == 3 ? fmaf(dx1, dx1, fmaf(dy1, dy1, dz1 * dz1)) : fmaf(dx1, dx1, dy1 * dy1);
+              float2 dx, dy, dz;
+              const float2 d2 = pair_d2<DIM>(q, nx, ny, nz, dx, dy, dz);
+              d20 = d2.x;
+              d21 = d2.y;
               k0 = jo > a0 && d20 < A.rc2;
               k1 = jo > a1 && d21 < A.rc2;
             }
