@@ -687,6 +687,36 @@ def reduction_times(P, cl, dev, flush, reps=20):
     return out
 
 
+def serve_trace(times, span):
+    """Where a served stream's time goes, from the server's own host
+    timestamps (submitted, admitted, batch launched, completed): the host
+    time between consecutive admissions, the batches (grouped by launch time)
+    and the part of the span with at least one batch in flight."""
+    if len(times) == 0:
+        return None
+    t0 = times[:, 0].min()
+    t1 = np.sort(times[:, 1])
+    launch, inv = np.unique(times[:, 2], return_inverse=True)
+    sizes = np.bincount(inv)
+    end = np.array([times[inv == k, 3].max() for k in range(len(launch))])
+    busy, cur0, cur1 = 0.0, None, None  # union of the batches' [launch, last completion] intervals
+    for a, b in sorted(zip(launch, end)):
+        if cur1 is None or a > cur1:
+            if cur1 is not None:
+                busy += cur1 - cur0
+            cur0, cur1 = a, b
+        else:
+            cur1 = max(cur1, b)
+    busy += cur1 - cur0
+    gaps = np.diff(t1)
+    return {"admit_us_per_request": float(np.median(gaps)) * 1e6 if len(gaps) else 0.0,
+            "admission_span_ms": float(t1[-1] - t1[0]) * 1e3,
+            "first_launch_ms": float(launch[0] - t0) * 1e3,
+            "batches": int(len(sizes)), "mean_batch": float(sizes.mean()), "largest_batch": int(sizes.max()),
+            "mean_batch_ms": float(np.mean(end - launch)) * 1e3,
+            "batch_in_flight_frac": float(busy / span) if span > 0 else 0.0}
+
+
 def serve_leg(dev):
     """Serving stream (512 seeded requests, Poisson arrivals with 2 ms mean
     gap, 2D/3D, 1e3..2e5 particles, ortho/triclinic, energy/forces/histogram)
@@ -730,7 +760,8 @@ def serve_leg(dev):
         span = times[:, 3].max() - times[:, 0].min()
         return {"req_per_s": len(reqs) / span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "batches": st["batches"] - b0,
-                "largest_batch": st["largest_batch"], "failed": int(sum(1 for x in status if x != 0))}
+                "largest_batch": st["largest_batch"], "failed": int(sum(1 for x in status if x != 0)),
+                "trace": serve_trace(times[np.array(status) == 0], span)}
 
     def plain(k_max=None):
         """one request at a time through cl_build + cl_map, H2D and D2H included"""

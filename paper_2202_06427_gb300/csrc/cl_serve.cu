@@ -204,6 +204,11 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int kBuildStreams = 4;
 constexpr size_t kAlign = 256;
+// Requests admitted per pass of the scheduling loop before it looks for a free
+// batch slot: admission (copies and binning launches, about a dozen runtime
+// calls per request) is host work, and a burst of hundreds of requests
+// admitted in one pass would keep the GPU waiting for the first batch.
+constexpr int kAdmitPerPass = 32;
 
 size_t up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -539,7 +544,7 @@ void cl_server::loop() {
         complete(b);
         progressed = true;
       }
-    while (!queue.empty() && resident < max_inflight) {
+    for (int k = 0; k < kAdmitPerPass && !queue.empty() && resident < max_inflight; ++k) {
       Req* q = queue.front();
       if (!admit_one(q)) break;
       queue.pop_front();
