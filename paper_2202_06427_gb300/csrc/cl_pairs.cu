@@ -550,16 +550,6 @@ __device__ __forceinline__ void stage_radix(const float4* st, int S, unsigned sh
   slots = s0;
 }
 
-// One CTA of W warps per cell (grid-stride over the cells). The stencil
-// entries are shared among the warps 32 at a time; each warp appends the
-// particles of its entries that lie within sqrt(ball2) of the cell centre,
-// shifted to the cell's frame (x_j + s_o), to the staged list. Then warp w
-// sweeps home particles w, w + W, ... against it (distance (x_j + s_o) - x_i).
-// COUNT: count[a] = pairs with j > a; a cell whose list does not fit gets
-// flag 1 (else 0) and is listed in fcells. FILL: flagged cells are skipped; the staged list is ordered
-// by original index (radix sort of its indices), so a particle's pairs with
-// j > a come from a suffix of that order in ascending j and are written in
-// order, coalesced, as the ballot finds them.
 // Squared distances of a staged entry q to two home particles (nx, ny, nz:
 // their negated coordinates), both in packed FP32: per lane the same rounding
 // as fmaf(dx, dx, fmaf(dy, dy, dz * dz)) with dx = q.x - x. The count and the
@@ -577,6 +567,18 @@ __device__ __forceinline__ float2 pair_d2(const float4& q, float2 nx, float2 ny,
   return __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
 }
 
+// One CTA of W warps per cell (grid-stride over the cells). The stencil
+// entries are shared among the warps 32 at a time; each warp appends the
+// particles of its entries that lie within sqrt(ball2) of the cell centre,
+// shifted to the cell's frame (x_j + s_o), to the staged list. Then warp w
+// sweeps home particles w, w + W, ... against it (distance (x_j + s_o) - x_i).
+// Particles whose original index is not above the smallest of the cell's own
+// are not staged: no pair with j > i of this cell needs them.
+// COUNT: count[a] = pairs with j > a; a cell whose list does not fit gets
+// flag 1 (else 0) and is listed in fcells. FILL: flagged cells are skipped; the staged list is ordered
+// by original index (radix sort of its indices), so a particle's pairs with
+// j > a come from a suffix of that order in ascending j and are written in
+// order, coalesced, as the ballot finds them.
 template <int DIM, bool FILL>
 __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ SweepArgs A,
                                                                                float ball2, int cap,
@@ -606,6 +608,12 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
     if (FILL && flag[c]) continue;
     const int cx = c % A.nx, cy = (c / A.nx) % A.ny, cz = c / (A.nx * A.ny);
     if (threadIdx.x == 0) scal[0] = 0;
+    // the smallest original index among the cell's particles (each warp on
+    // its own): a staged particle of index <= amin pairs with none of them
+    // under j > i, so neither pass stages it
+    int amin = INT_MAX;
+    for (int p = h0 + lane; p < h1; p += 32) amin = min(amin, __float_as_int(__ldg(&A.xs[p].w)));
+    amin = __reduce_min_sync(0xffffffffu, amin);
     __syncthreads();
     for (int k0 = warp * 32; k0 < A.noff; k0 += 32 * W) {
       const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, 0.f, 0.f, 0.f);
@@ -621,7 +629,7 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
           v.y = q.y + ay;
           v.z = DIM == 3 ? q.z + az : 0.f;
           v.w = q.w;
-          keep = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)) < ball2;
+          keep = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z)) < ball2 && __float_as_int(q.w) > amin;
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         int base = 0;
