@@ -140,6 +140,11 @@ void fill_sweep_args(cl_list* c, clk::SweepArgs* A) {
   A->rc2 = (float)(c->geo.rc * c->geo.rc);
   A->irc = (float)(1.0 / c->geo.rc);
   A->irc2 = (float)(1.0 / (c->geo.rc * c->geo.rc));
+  float e[3];
+  clk::cell_halfwidths(c->geo, e);
+  A->ex = e[0];
+  A->ey = e[1];
+  A->ez = e[2];
 }
 
 int set_geometry(cl_list* c, const cl_box* box) {

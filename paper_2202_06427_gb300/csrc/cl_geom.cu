@@ -161,6 +161,14 @@ static double min_dist2(const Geo& geo, const int* o) {
   return best;
 }
 
+void cell_halfwidths(const Geo& geo, float* e) {
+  for (int a = 0; a < 3; ++a) {
+    double s = 0.0;
+    for (int k = 0; k < geo.dim; ++k) s += std::fabs(geo.h[k * 3 + a]) / geo.n[k];
+    e[a] = (float)(0.5 * s + 1e-3 * geo.rc);
+  }
+}
+
 int build_stencil(const Geo& geo, int half, Off* out, int cap, int* opk) {
   const int dim = geo.dim;
   int m[3] = {0, 0, 0};

@@ -92,6 +92,10 @@ struct SweepArgs {
   int n;
   int nx, ny, nz;
   float rc2, irc, irc2;
+  // Half-widths of one cell's Cartesian bounding box, padded by 1e-3 rc (3D
+  // packed per-particle sweep: a neighbour cell whose box lies at least rc
+  // from the particle is skipped); 0 turns the test off.
+  float ex, ey, ez;
   int noff;             // entries in off[]; off[0] is the own cell
   Off off[kMaxOff];
 };
@@ -102,6 +106,9 @@ int prepare_geometry(const cl_box* box, Geo* geo);
 // negative error. opk (optional) receives each entry's unwrapped offset packed
 // as bytes: (ox & 255) | (oy & 255) << 8 | (oz & 255) << 16.
 int build_stencil(const Geo& geo, int half, Off* out, int cap, int* opk = nullptr);
+// Half-widths of one cell's Cartesian bounding box (sum over the cell edge
+// vectors of |G_k,a| / 2 per axis a), each padded by 1e-3 rc.
+void cell_halfwidths(const Geo& geo, float* e);
 
 }  // namespace clk
 

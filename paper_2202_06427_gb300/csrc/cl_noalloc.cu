@@ -137,6 +137,7 @@ extern "C" int cl_energy_noalloc(const double* pos_dev, long long n, const cl_bo
   A.rc2 = (float)(g.rc * g.rc);
   A.irc = (float)(1.0 / g.rc);
   A.irc2 = (float)(1.0 / (g.rc * g.rc));
+  A.ex = A.ey = A.ez = 0.f;  // the scalar sweep tests every stencil cell
   A.noff = noff;
   return clk::launch_scalar(A, g.dim, 1, reinterpret_cast<double*>(base + kOffPartials),
                             reinterpret_cast<double*>(base + kOffSums), energy_dev, s);

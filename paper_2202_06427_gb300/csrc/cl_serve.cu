@@ -34,6 +34,7 @@ struct ReqDesc {
   int dim, task, n, noff;
   int nx, ny, nz, nbins;
   float rc2, irc, irc2, hscale, rmax;
+  float ex, ey, ez;  // a cell's bounding-box half-widths (as in SweepArgs)
   int item_base, nitems;
   const float4* xs;
   const unsigned* cellc;
@@ -449,6 +450,13 @@ void cl_server::launch_batch(Batch& b) {
     D.rc2 = (float)(q->geo.rc * q->geo.rc);
     D.irc = (float)(1.0 / q->geo.rc);
     D.irc2 = (float)(1.0 / (q->geo.rc * q->geo.rc));
+    {
+      float e[3];
+      clk::cell_halfwidths(q->geo, e);
+      D.ex = e[0];
+      D.ey = e[1];
+      D.ez = e[2];
+    }
     const double rmax = q->r.rmax > 0 ? q->r.rmax : q->geo.rc;
     D.rmax = (float)rmax;
     D.hscale = q->r.task == CL_TASK_HIST ? (float)(q->r.nbins / rmax) : 0.f;

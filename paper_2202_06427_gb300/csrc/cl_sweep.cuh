@@ -197,6 +197,7 @@ __device__ __forceinline__ float2 rsqrt2(float2 d2) { return make_float2(rsqrtf(
 // Shifted-force energy (1 - r/rc)^2 / r of the pairs in the cutoff.
 struct Red2Energy {
   static constexpr bool kFull = false;
+  static constexpr bool kCull = true;  // skip cells beyond rc (sweep_particle2)
   float irc;
   struct Acc { float2 e; };
   __device__ void init(Acc& a) const { a.e = f2(0.f); }
@@ -224,6 +225,7 @@ __device__ __forceinline__ float sqrt_approx(float v) {
 
 struct Red2Count {
   static constexpr bool kFull = false;
+  static constexpr bool kCull = true;
   struct Acc { unsigned n; };
   __device__ void init(Acc& a) const { a.n = 0; }
   __device__ void hit2(Acc& a, float2, float2, float2, float2, bool h0, bool h1) const {
@@ -233,6 +235,7 @@ struct Red2Count {
 
 struct Red2SumInvR {
   static constexpr bool kFull = false;
+  static constexpr bool kCull = true;
   struct Acc { float2 s; };
   __device__ void init(Acc& a) const { a.s = f2(0.f); }
   __device__ void hit2(Acc& a, float2, float2, float2, float2 d2, bool h0, bool h1) const {
@@ -245,6 +248,7 @@ struct Red2SumInvR {
 
 struct Red2Hist {
   static constexpr bool kFull = false;
+  static constexpr bool kCull = false;  // measured slower with the cell test (0.853 against 0.832 ms, 1M triclinic)
   float scale2, xlim;
   unsigned* sh;  // shared-memory histogram
   struct Acc {};
@@ -271,6 +275,7 @@ struct Red2Hist {
 template <bool ENERGY>
 struct Red2Force {
   static constexpr bool kFull = true;
+  static constexpr bool kCull = true;
   float irc, irc2;
   struct Acc {
     float2 gx, gy, gz;  // partial Gn of the current neighbour cell
@@ -376,7 +381,10 @@ __device__ __forceinline__ int stencil_cell(const ARGS& A, int k, int cx, int cy
   return x2 + A.nx * (y2 + A.ny * z2);
 }
 
-// Packed counterpart of sweep_particle (3D only).
+// Packed counterpart of sweep_particle (3D only). A neighbour cell whose
+// Cartesian bounding box (centre S_o, half-widths ex, ey, ez, padded by 1e-3
+// rc) lies at least rc from the particle holds no pair within the cutoff and
+// is skipped (reducers with kCull).
 template <class R, class ARGS = SweepArgs>
 __device__ __forceinline__ bool sweep_particle2(const ARGS& A, const R& red, typename R::Acc& acc, int p,
                                                 float4& pi) {
@@ -391,9 +399,15 @@ __device__ __forceinline__ bool sweep_particle2(const ARGS& A, const R& red, typ
     scan_pairs(A.xs, p + 1, s1, -pi.x, -pi.y, -pi.z, A.rc2, red, acc);
     cell_done_of(red, acc, 0.f, 0.f, 0.f);
   }
+  const bool cull = R::kCull && A.ex > 0.f;
   for (int k = 1; k < A.noff; ++k) {
-    const int c = stencil_cell(A, k, cx, cy, cz);
     const Off& o = A.off[k];
+    if (cull) {
+      const float bx = fmaxf(fabsf(pi.x - o.sx) - A.ex, 0.f), by = fmaxf(fabsf(pi.y - o.sy) - A.ey, 0.f),
+                  bz = fmaxf(fabsf(pi.z - o.sz) - A.ez, 0.f);
+      if (fmaf(bx, bx, fmaf(by, by, bz * bz)) >= A.rc2) continue;
+    }
+    const int c = stencil_cell(A, k, cx, cy, cz);
     scan_pairs(A.xs, A.cell_start[c], A.cell_start[c + 1], o.sx - pi.x, o.sy - pi.y, o.sz - pi.z, A.rc2,
                red, acc);
     cell_done_of(red, acc, o.sx, o.sy, o.sz);
