@@ -3,7 +3,8 @@
 //
 //   k_pairs_cell<COUNT>  one CTA per cell stages the cell's neighbourhood
 //                  (the particles of its full stencil that lie within
-//                  rc + half a cell diagonal of its centre) in shared memory;
+//                  rc + half a cell diagonal of its centre and whose index is
+//                  above the smallest of the cell's own) in shared memory;
 //                  one warp per home particle sweeps it and counts the pairs
 //                  with j > i (original indices), so every pair is counted
 //                  once, by its smaller index, without atomics. A cell whose
