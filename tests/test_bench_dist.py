@@ -56,3 +56,30 @@ def test_reference_arm_line_shape(monkeypatch):
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0
     assert bench.run_reference(A, 1, 2) is None
+
+
+def test_serve_trace_from_timestamps():
+    """The serving record's trace: admission spacing, batches grouped by launch
+    time, and the part of the span with a batch in flight (a union of the
+    batches' intervals, overlapping ones counted once)."""
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import bench
+    # (submitted, admitted, launched, completed) in seconds; three batches:
+    # launched at 2 ms (two requests, done by 6 ms), at 4 ms (overlapping the
+    # first, done at 8 ms) and at 9 ms (done at 10 ms)
+    t = np.array([[0.000, 0.001, 0.002, 0.005],
+                  [0.000, 0.0015, 0.002, 0.006],
+                  [0.000, 0.003, 0.004, 0.008],
+                  [0.001, 0.004, 0.009, 0.010]])
+    tr = bench.serve_trace(t, 0.010)
+    assert tr["batches"] == 3 and tr["largest_batch"] == 2
+    assert abs(tr["mean_batch"] - 4 / 3) < 1e-12
+    assert abs(tr["first_launch_ms"] - 2.0) < 1e-9
+    assert abs(tr["admission_span_ms"] - 3.0) < 1e-9
+    assert abs(tr["admit_us_per_request"] - 1000.0) < 1e-6  # median of 0.5, 1.5, 1 ms gaps
+    # in flight: [2, 8] ms and [9, 10] ms -> 7 ms of the 10 ms span
+    assert abs(tr["batch_in_flight_frac"] - 0.7) < 1e-12
+    # per batch, launch to last completion: 4, 4 and 1 ms
+    assert abs(tr["mean_batch_ms"] - 3.0) < 1e-9
+    assert bench.serve_trace(t[:0], 0.0) is None
