@@ -83,3 +83,25 @@ def test_serve_trace_from_timestamps():
     # per batch, launch to last completion: 4, 4 and 1 ms
     assert abs(tr["mean_batch_ms"] - 3.0) < 1e-9
     assert bench.serve_trace(t[:0], 0.0) is None
+
+
+def test_roofline_records_follow_the_scope_counts(monkeypatch):
+    """Sweep: half-shell stencil candidates x 8 + pair-images x 26 FLOP per
+    launch over the CUDA-event time, against 152 SMs x 128 lanes x 2 x 2.07
+    GHz; binning: 44 B per particle + 8 B per cell over the measured copy
+    bandwidth. Figures of the 1M lattice step."""
+    sys.path.insert(0, ROOT)
+    import bench
+    peak = 152 * 128 * 2 * 2070e6 / 1e12
+    monkeypatch.setattr(bench, "fp32_peak", lambda dev, clocks: (peak, "test"))
+    cand, pairs, kms = 1_457_508_307, 361_637_312, 1.2142307305335998
+    r = bench.sweep_roofline(None, None, cand, pairs, kms, 911_427_599, "k", True)
+    flop = cand * 8 + pairs * 26
+    assert r["flop_per_launch"] == flop == 21_062_636_568
+    assert abs(r["achieved"] - flop / (kms * 1e-3) / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 80.54784) < 1e-12 and 0.21 < r["frac"] < 0.22
+    assert r["evaluated"]["flop"] == 911_427_599 * 8 + pairs * 22
+    b = bench.binning_record(1_000_000, 42_875, 0.05, {"hbm_gbs": 6782.8}, "test")
+    assert b["bytes"] == 44 * 1_000_000 + 8 * 42_875
+    assert abs(b["achieved"] - b["bytes"] / 0.05e-3 / 1e9) < 1e-9
+    assert abs(b["frac"] - b["achieved"] / 6782.8) < 1e-12
