@@ -294,13 +294,13 @@ struct Chunk {
 
 template <int DIM>
 __device__ __forceinline__ Chunk chunk_ranges(const SweepArgs& A, const float4* stab, int k0, int lane, int cx,
-                                              int cy, int cz, float bx, float by, float bz) {
+                                              int cy, int cz, float bx, float by, float bz, int lim = 32) {
   Chunk ch;
   ch.j0 = 0;
   ch.len = 0;
   ch.sx = ch.sy = ch.sz = 0.f;
   const int k = k0 + lane;
-  if (k < A.noff) {
+  if (lane < lim && k < A.noff) {  // lim: the entries this warp takes (lanes 0..lim-1)
     const float4 e = stab[k];
     const unsigned d = __float_as_uint(e.w);
     int x2 = cx + (int)(d & 1023u);
@@ -616,8 +616,12 @@ __global__ void __launch_bounds__(256, 5) k_pairs_cell(const __grid_constant__ S
     for (int p = h0 + lane; p < h1; p += 32) amin = min(amin, __float_as_int(__ldg(&A.xs[p].w)));
     amin = __reduce_min_sync(0xffffffffu, amin);
     __syncthreads();
-    for (int k0 = warp * 32; k0 < A.noff; k0 += 32 * W) {
-      const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, 0.f, 0.f, 0.f);
+    // the stencil dealt evenly to the warps (E entries each per round, at most
+    // 32): at 32 per warp the 125 entries of a full stencil at lcell 2 would
+    // keep four of the eight warps waiting while the others stage
+    const int E = min(32, (A.noff + W - 1) / W);
+    for (int k0 = warp * E; k0 < A.noff; k0 += E * W) {
+      const Chunk ch = chunk_ranges<DIM>(A, stab, k0, lane, cx, cy, cz, 0.f, 0.f, 0.f, E);
       for (int t0 = 0; t0 < ch.total; t0 += 32) {
         const int t = t0 + lane;
         float ax, ay, az;
